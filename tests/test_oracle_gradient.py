@@ -1,0 +1,63 @@
+"""Pins of the oracle's reference gradients against central finite differences (CPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bldtt, gradient, physics
+from paper_2302_07567_gb300.workloads import make_weights, random_beam
+
+
+def _fd(fun, arr, idx, h):
+    a1 = arr.copy()
+    a2 = arr.copy()
+    a1[idx] += h
+    a2[idx] -= h
+    return (fun(a1) - fun(a2)) / (2.0 * h)
+
+
+@pytest.mark.parametrize("which", ["fmm", "direct"])
+def test_gradient_matches_central_differences(which):
+    N = 96
+    x, p, q = random_beam(N, seed=12, gamma=6.0, spread=0.05, angle=0.05)
+    wE, wB = make_weights(N)
+    plan = bldtt.build_plan(x, p, 4, 8, 0.6)
+    gb = plan.tree.gbar
+    assert len(plan.m2l) > 0
+    if which == "fmm":
+        L0, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+
+        def loss(xx, pp, qq):
+            E, B = bldtt.fmm_fields(xx, pp, qq, 4, 8, 0.6, plan=plan)
+            return gradient.loss_value(E, B, wE, wB)
+    else:
+        L0, gx, gp, gq = gradient.direct_gradient(x, p, q, wE, wB, gbar=gb)
+
+        def loss(xx, pp, qq):
+            E, B = physics.direct_fields(xx, pp, qq, gbar=gb)
+            return gradient.loss_value(E, B, wE, wB)
+
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        j, k = int(rng.integers(N)), int(rng.integers(3))
+        h = 1e-6 * max(abs(x[j, k]), 1e-4)
+        fd = _fd(lambda a: loss(a, p, q), x, (j, k), h)
+        assert abs(fd - float(gx[j, k])) <= 2e-5 * abs(fd) + 2e-8 * float(gx.abs().max())
+        h = 1e-6 * max(abs(p[j, k]), 1e-2)
+        fd = _fd(lambda a: loss(x, a, q), p, (j, k), h)
+        assert abs(fd - float(gp[j, k])) <= 2e-5 * abs(fd) + 2e-8 * float(gp.abs().max())
+        h = 1e-6 * abs(q[j])
+        fd = _fd(lambda a: loss(x, p, a), q, (j,), h)
+        assert abs(fd - float(gq[j])) <= 2e-5 * abs(fd) + 2e-8 * float(gq.abs().max())
+
+
+def test_fmm_gradient_approaches_direct_gradient():
+    N = 256
+    x, p, q = random_beam(N, seed=13, gamma=8.0)
+    wE, wB = make_weights(N)
+    errs = []
+    for n in (2, 5):
+        plan = bldtt.build_plan(x, p, n, 16, 0.5)
+        _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+        _, dx, dp, dq = gradient.direct_gradient(x, p, q, wE, wB, gbar=plan.tree.gbar)
+        errs.append(max(float((gx - dx).norm() / dx.norm()), float((gq - dq).norm() / dq.norm())))
+    assert errs[1] < errs[0] < 0.1
