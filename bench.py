@@ -1,0 +1,361 @@
+"""Benchmark of the GB300 relativistic space-charge FMM.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--passes fwd|fwd+adj]
+                [--impl ours|reference]
+
+A step is one pass of the whole hot path on one batch of synthetic input:
+setup (gbar), tree build, upward pass, dual tree traversal, list sort, M2L,
+L2L, P2P + L2P (the forward field), and with --passes fwd+adj the adjoint
+(the gradients of sum wE.E + wB.B with respect to x, p and q).  The metric
+is particles per second of that step.  Inputs are resident on the GPU when
+the timed region starts; L2 is flushed (a 512 MiB write) before every timed
+step because one batch is smaller than L2.  Under torchrun every rank runs
+its own replica of the workload (the problems are independent, no data-path
+collective) and the reported value is the sum over ranks of particles per
+second at the slowest rank's time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle (serial BLDTT + autograd adjoint)
+on the host cores on a bounded sample of the same workload; it is a
+deliberately plain program, reported as a baseline, not a target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2302_07567_gb300.workloads import WORKLOADS, make_beam, make_weights, sample_targets  # noqa: E402
+
+METRIC = "particles/s (E,B on all N; fwd and fwd+adjoint) at fixed rel. L2 error vs FP64"
+SMS = 152          # GB300 streaming multiprocessors
+FP32_LANES = 128   # FP32 FMA lanes per SM
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="cylinder64k", choices=sorted(WORKLOADS))
+    ap.add_argument("--passes", default="fwd+adj", choices=["fwd", "fwd+adj"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 GPU FMM side measurement")
+    ap.add_argument("--profile", action="store_true",
+                    help="run only the warm-up and the timed steps, print nothing (for profiler captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [c.strip() for c in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * (max(smax) if smax else 1)]
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2302_07567_gb300 import fmm
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    N = w.N
+    x, p, q = make_beam(args.workload)
+    wE, wB = make_weights(N)
+    out_dt = torch.float32 if args.precision == "fp32" else torch.float64
+    X, Pm, Q = (torch.as_tensor(a, device=dev) for a in (x, p, q))
+    WE, WB = torch.as_tensor(wE, device=dev, dtype=out_dt), torch.as_tensor(wB, device=dev, dtype=out_dt)
+    adj = args.passes == "fwd+adj"
+    plan = fmm.Plan(N, w.n, w.leaf, w.eta, precision=args.precision, flags=fmm.FMM_TIMING)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        E, B = plan.field(X, Pm, Q)
+        if adj:
+            return plan.adjoint(X, Pm, Q, WE, WB)
+        return E, B
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st0 = plan.stats()
+    m2l_ms, p2p_ms, step_ms = [], [], []
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = fmm.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+            st = plan.stats()  # stage events of this step (same stream)
+            m2l_ms.append(st["stage_ms"]["m2l"])
+            p2p_ms.append(st["stage_ms"]["p2p_l2p"])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    launches = fmm.kernel_launches() - launches0
+    barrier(world)
+    if args.profile:
+        plan.close()
+        return
+    for k in range(args.steps):
+        step_ms.append(ev0[k].elapsed_time(ev1[k]))
+    t_steps = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_steps, world, dev)
+    value = N * world * args.steps / t_max
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # step's inputs, the step, D2H of its results, all inside the timed region
+    hx, hp, hq = (torch.as_tensor(a).pin_memory() for a in (x, p, q))
+    hwE, hwB = torch.as_tensor(wE, dtype=out_dt).pin_memory(), torch.as_tensor(wB, dtype=out_dt).pin_memory()
+    outs = None
+    h2d = (hx.numel() + hp.numel() + hq.numel()) * 8 + ((hwE.numel() + hwB.numel()) * hwE.element_size() if adj else 0)
+    e2e_ms = []
+    for k in range(max(args.warmup, 3) + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd, Pd, Qd = hx.to(dev, non_blocking=True), hp.to(dev, non_blocking=True), hq.to(dev, non_blocking=True)
+        E, B = plan.field(Xd, Pd, Qd)
+        res = [E, B]
+        if adj:
+            WEd, WBd = hwE.to(dev, non_blocking=True), hwB.to(dev, non_blocking=True)
+            res = list(plan.adjoint(Xd, Pd, Qd, WEd, WBd)) + res
+        outs = [r.to("cpu") for r in res]
+        torch.cuda.synchronize()
+        if k >= max(args.warmup, 3):
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world, dev)
+    e2e_value = N * world * args.steps / e2e_t
+
+    # accuracy of this configuration against the FP64 brute force on sampled targets
+    tg = torch.as_tensor(sample_targets(N, 4096), device=dev)
+    E, B = plan.field(X, Pm, Q)
+    st = plan.stats()
+    Ed, Bd = fmm.direct_field(X, Pm, Q, gbar=st["gbar"], targets=tg)
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))
+
+    err = max(rel(E[tg], Ed), rel(B[tg], Bd))
+
+    side = {}
+    if rank == 0 and not args.no_fp64_side and args.precision == "fp32":
+        p64 = fmm.Plan(N, w.n, w.leaf, w.eta, precision="fp64")
+        for _ in range(2):
+            p64.field(X, Pm, Q)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record(stream)
+        for _ in range(reps):
+            E64, B64 = p64.field(X, Pm, Q)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3 / reps
+        err64 = max(rel(E64[tg], Ed), rel(B64[tg], Bd))
+        side = {"fp64_fwd_particles_per_s": N / t64, "fp64_fwd_err": err64, "fp32_fwd_err": err}
+        p64.close()
+
+    # roofline of the dominant kernel (M2L or P2P), ALU bound: FP32 SIMT peak
+    # = SMs x 128 lanes x 2 flop x SM clock (median sampled under load)
+    clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or 2070.0
+    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12 if args.precision == "fp32" else None
+    m2l_flop = 32.0 * st0["m2l_interactions"]
+    p2p_flop = 32.0 * st0["p2p_interactions"]
+    m2l_t = statistics.median(m2l_ms) / 1e3
+    p2p_t = statistics.median(p2p_ms) / 1e3
+    dom = "m2l" if m2l_t >= p2p_t else "p2p_l2p"
+    ach = (m2l_flop / m2l_t if dom == "m2l" else p2p_flop / p2p_t) / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": (ach / peak) if peak else None, "traffic": None,
+            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock)",
+            "flop_basis": "32 flop per pair interaction (P2P) or per proxy-point pair (M2L)",
+            "m2l_ms": statistics.median(m2l_ms), "p2p_l2p_ms": statistics.median(p2p_ms),
+            "m2l_tflops": m2l_flop / m2l_t / 1e12, "p2p_tflops": p2p_flop / p2p_t / 1e12}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded beam generator)",
+            "config": {"workload": args.workload, "N": N, "degree": w.n, "leaf": w.leaf, "eta": w.eta,
+                       "passes": args.passes, "precision": args.precision, "replicas": world,
+                       "l2": "flushed before every timed step (512 MiB write)", "note": w.note},
+            "rel_l2_error_vs_fp64_direct": err, "error_targets": 4096,
+            "stage_ms": {k: round(v, 4) for k, v in st0["stage_ms"].items() if v},
+            "lists": {"p2p_pairs": st0["p2p_pairs"], "m2l_pairs": st0["m2l_pairs"], "kappa": st0["kappa"]},
+            "wall_ms_per_step": 1e3 * t_wall / args.steps,
+            "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "launches_per_step": launches / args.steps,
+            "roofline": roof, "clocks": clocks, **side,
+        }
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload, adj)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_step(x, p, q, wE, wB, w, adj):
+    from oracle import bldtt, gradient
+    plan = bldtt.build_plan(x, p, w.n, w.leaf, w.eta)
+    if adj:
+        gradient.fmm_gradient(x, p, q, wE, wB, plan)
+    else:
+        bldtt.fmm_fields(x, p, q, w.n, w.leaf, w.eta, plan=plan)
+
+
+def cpu_baseline(workload: str, adj: bool, budget_s: float = 12.0):
+    """The oracle, as it stands, on a bounded sample of the workload on the host cores."""
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
+    w = WORKLOADS[workload]
+    Ns = min(w.N, 16384)
+    done, t_all, n_all = 0, 0.0, 0
+    while t_all < budget_s and done < 3:
+        x, p, q = make_beam(workload, N=Ns, seed_offset=done)
+        wE, wB = make_weights(Ns, seed_offset=done)
+        t0 = time.perf_counter()
+        _oracle_step(x, p, q, wE, wB, w, adj)
+        t_all += time.perf_counter() - t0
+        n_all += Ns
+        done += 1
+    return {"value": n_all / t_all, "unit": "particles/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{done} x serial FP64 BLDTT {'forward+autograd adjoint' if adj else 'forward'} on "
+                      f"N={Ns} draws of {workload} (n={w.n}, leaf={w.leaf}, eta={w.eta}); {t_all:.1f} s of CPU time"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
+    w = WORKLOADS[args.workload]
+    adj = args.passes == "fwd+adj"
+    Ns = min(w.N, 4096)
+    times = []
+    for k in range(max(args.warmup, 3) + args.steps):
+        x, p, q = make_beam(args.workload, N=Ns, seed_offset=k)
+        wE, wB = make_weights(Ns, seed_offset=k)
+        t0 = time.perf_counter()
+        _oracle_step(x, p, q, wE, wB, w, adj)
+        if k >= max(args.warmup, 3):
+            times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = Ns * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded beam generator)",
+            "impl": "reference",
+            "config": {"workload": args.workload, "N_sample": Ns, "degree": w.n, "leaf": w.leaf, "eta": w.eta,
+                       "passes": args.passes},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"each step: serial FP64 BLDTT on a fresh N={Ns} draw of {args.workload}"},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * fmm.h - C ABI of the GB300 relativistic space-charge FMM.
+ *
+ * The library computes, for N charged particles of a beam, the lab-frame
+ * space-charge fields of Section 3 of Kan, Kaertner, Le Borne, Zemke,
+ * "A GPU-parallelized interpolation-based fast multipole method for the
+ * relativistic space-charge field calculation" (arXiv 2302.07567):
+ *
+ *   E_i = 1/(4 pi eps0)      sum_{j != i} q_j gamma_j  g(x_i, x_j)       (Eq. 3.1)
+ *   B_i = 1/(4 pi eps0 c0)   sum_{j != i} q_j p_j  x  g(x_i, x_j)
+ *   g(x_i, x_j) = (x_i - x_j) / ((dx)^2 + (dy)^2 + gbar^2 (dz)^2)^(3/2)   (Eq. 3.2)
+ *
+ * with gamma_j = sqrt(1 + |p_j|^2) and gbar^2 = 1 + pbar.pbar, pbar the mean
+ * momentum.  The sums are evaluated by the barycentric Lagrange dual tree
+ * traversal FMM of the paper: a stretched k-d cluster tree (Algs. 1-2,
+ * Appendix B), P2M/M2M (Algs. 3-5), the dual tree traversal under the
+ * stretched admissibility condition (Eq. 4.x, Algs. 6-8, 11, 17), M2L and
+ * P2P (Algs. 9-10) and L2L/L2P (Algs. 13-15).  Every stage runs as CUDA on
+ * one GPU.  Units are SI: x in metres, p = gamma*beta dimensionless, q in
+ * coulomb, E in V/m, B in tesla; eps0 = 8.8541878128e-12 F/m and
+ * c0 = 299792458 m/s.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Device pointers are owned by the caller and must stay valid until the
+ *   work queued on `stream` has finished.  Arrays are dense, row-major:
+ *   [N,3] means x[3*i + k].
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * - Every function returns an fmm_status; none of them throws, aborts or
+ *   prints.  The library never allocates device memory: scratch space comes
+ *   from the workspace the caller attaches with fmm_plan_set_workspace.
+ * - A plan is not thread safe; use one plan per host thread.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fmm_status {
+  FMM_OK = 0,
+  FMM_EINVAL = 1,       /* bad argument: N < 1, degree outside 1..12, leaf size < 2,
+                           eta not finite or <= 0, unknown precision, NULL pointer  */
+  FMM_ENOWORKSPACE = 2, /* no workspace attached, or smaller than required          */
+  FMM_EOVERFLOW = 3,    /* an interaction-list capacity was exceeded; raise it with
+                           fmm_plan_set_capacity, re-attach a workspace, call again  */
+  FMM_ENONFINITE = 4,   /* x or p holds NaN or Inf                                   */
+  FMM_ESTATE = 5,       /* fmm_field_adjoint before a successful fmm_field           */
+  FMM_ECUDA = 6,        /* a CUDA runtime call failed (see fmm_last_cuda_error)      */
+  FMM_EBOUNDS = 7       /* an index check of FMM_BOUNDS_CHECK failed                 */
+} fmm_status;
+
+typedef enum fmm_precision {
+  FMM_FP64 = 0, /* every stage in double precision                                   */
+  FMM_FP32 = 1  /* tree, boxes, gbar, traversal and interpolation setup in FP64;
+                   P2M/M2M/M2L/P2P/L2L/L2P arithmetic in FP32 with FP32 accumulators
+                   and compensated (Kahan) sums across source clusters and leaves    */
+} fmm_precision;
+
+typedef enum fmm_flags {
+  FMM_RECOMPUTE = 1u,    /* the adjoint recomputes multipoles and local fields instead
+                            of reusing those of the forward call                      */
+  FMM_BOUNDS_CHECK = 2u, /* check every list and tree index on the device; a failure
+                            sets FMM_EBOUNDS instead of reading out of range         */
+  FMM_TIMING = 4u        /* record CUDA events around each stage (fmm_plan_stats)    */
+} fmm_flags;
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+/* Create a plan for N particles (Alg. 12, FMM(S, s, N0, eta)).
+ *   degree     interpolation degree n, 1..12: (n+1)^3 Chebyshev points per cluster
+ *   leaf_size  N0 >= 2: the tree depth is kappa = 0 if N <= N0, else the least
+ *              kappa with N0 * 2^kappa >= N (Section 8); every leaf holds at most N0
+ *   eta        admissibility parameter of max(diam_s)/dist_s < eta (Eq. 4.x, Alg. 8)
+ *   precision  FMM_FP64 or FMM_FP32;  flags: OR of fmm_flags.
+ * The plan is host memory only; destroy it with fmm_plan_destroy. */
+int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, double eta,
+                    int precision, unsigned flags);
+
+/* Capacities of the P2P and M2L interaction lists (pairs of clusters) and of
+ * the traversal frontier.  0 keeps the default.  Changing a capacity changes
+ * the workspace size: query and attach it again afterwards. */
+int fmm_plan_set_capacity(fmm_plan_t plan, int64_t p2p_pairs, int64_t m2l_pairs,
+                          int64_t frontier_pairs);
+
+/* Bytes of device workspace the plan needs (256-byte aligned start required). */
+int fmm_plan_workspace_bytes(fmm_plan_t plan, size_t* bytes);
+
+/* Attach caller-owned device memory of at least fmm_plan_workspace_bytes. The
+ * plan keeps the pointer; the caller frees it after fmm_plan_destroy.  Also
+ * uploads the plan's node tables (a synchronous copy on the legacy stream). */
+int fmm_plan_set_workspace(fmm_plan_t plan, void* device_ptr, size_t bytes);
+
+/* Forward pass: fields of all N particles (Alg. 12).
+ *   x, p  device, [N,3] float64;  q  device, [N] float64
+ *   E, B  device, [N,3]; float64 for FMM_FP64 plans, float32 for FMM_FP32 plans
+ * Rows of E and B follow the input order.  The call queues work on `stream`,
+ * waits once on it after the traversal (to size the list sort and read the
+ * device error flags) and returns; the remaining kernels may still be running.
+ * On FMM_EOVERFLOW / FMM_ENONFINITE nothing is written to E and B. */
+int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q,
+              void* E, void* B, void* stream);
+
+/* Adjoint of the forward pass of the same plan (not in the paper).  For the
+ * loss L = sum_i wE_i . E_i + wB_i . B_i it returns dL/dx [N,3], dL/dp [N,3]
+ * and dL/dq [N] (device float64), the exact derivative of the FMM operator
+ * with the tree, its boxes, the interaction lists and gbar held fixed at the
+ * values of the last fmm_field call.  wE, wB: device [N,3] of the plan's
+ * output type.  x, p, q must be the arrays of the last fmm_field call, still
+ * unchanged.  Returns FMM_ESTATE if no successful fmm_field preceded it. */
+int fmm_field_adjoint(fmm_plan_t plan, const double* x, const double* p, const double* q,
+                      const void* wE, const void* wB, double* dx, double* dp, double* dq,
+                      void* stream);
+
+typedef struct fmm_stats {
+  int64_t N, nodes, leaves;
+  int32_t degree, leaf_size, kappa, precision;
+  double eta, gbar, length_unit, mass_unit;
+  int64_t p2p_pairs, m2l_pairs;          /* cluster pairs in the interaction lists   */
+  double p2p_interactions;               /* sum |S_t||S_s| over P2P pairs minus N     */
+  double m2l_interactions;               /* m2l_pairs * (n+1)^6                       */
+  int64_t cap_p2p, cap_m2l, cap_frontier;
+  /* stage times of the last call in ms (FMM_TIMING only, else 0):
+     0 setup, 1 tree, 2 upward, 3 traversal, 4 list sort, 5 M2L, 6 L2L, 7 P2P+L2P,
+     8 adjoint upward (L2P^T, L2L^T), 9 adjoint M2L^T, 10 adjoint downward (M2M^T),
+     11 adjoint near field, 12 adjoint far field at particles, 13 whole call */
+  double stage_ms[16];
+} fmm_stats;
+
+/* Copy the plan's dimensions, list sizes and stage times (synchronises the
+ * stream of the last call when FMM_TIMING is set). */
+int fmm_plan_stats(fmm_plan_t plan, fmm_stats* out);
+
+/* Inspection of intermediate results of the last fmm_field, copied to host
+ * memory (synchronous).  `bytes` must be at least the size given below, with
+ * C = 2^(kappa+1) - 1 nodes numbered breadth first from 1 (Section 8) and
+ * m = (degree+1)^3 proxy points ordered nu = nu1 + (n+1) nu2 + (n+1)^2 nu3.
+ *   FMM_EXPORT_GBAR       double[1]
+ *   FMM_EXPORT_PERM       int32[N]    input index of the particle at leaf-order slot
+ *   FMM_EXPORT_NODES      int64[C][2] (first slot, count) of nodes 1..C
+ *   FMM_EXPORT_BBOX       double[C][6] (a_x, a_y, a_z, b_x, b_y, b_z) (Section 2)
+ *   FMM_EXPORT_AXIS       int32[C]    split axis of Alg. 1, -1 at leaves
+ *   FMM_EXPORT_P2P        int32[n][2] (target, source), sorted; n = stats.p2p_pairs
+ *   FMM_EXPORT_M2L        int32[n][2] (target, source), sorted; n = stats.m2l_pairs
+ *   FMM_EXPORT_MULTIPOLE  double[C][4][m]: sum_j l_nu(x_j) q_j gamma_j and
+ *                         sum_j l_nu(x_j) q_j p_j (Section 3, Algs. 3-5)
+ *   FMM_EXPORT_LOCAL      double[C][6][m]: cumulative local fields (E_mu, B_mu) of
+ *                         Eq. 2.9 without the 1/(4 pi eps0) and 1/c0 prefactors */
+typedef enum fmm_export {
+  FMM_EXPORT_GBAR = 0, FMM_EXPORT_PERM = 1, FMM_EXPORT_NODES = 2, FMM_EXPORT_BBOX = 3,
+  FMM_EXPORT_AXIS = 4, FMM_EXPORT_P2P = 5, FMM_EXPORT_M2L = 6, FMM_EXPORT_MULTIPOLE = 7,
+  FMM_EXPORT_LOCAL = 8
+} fmm_export;
+int fmm_plan_export(fmm_plan_t plan, int what, void* host_dst, size_t bytes);
+
+/* Brute force of Section 5 (Alg. 10 with S_t = S_s = S, i != j) in float64 for
+ * the T target rows listed in `targets` (device int64[T]; NULL = all N, T = N).
+ * gbar < 0 computes gbar from p as fmm_field does.  E, B: device float64 [T,3].
+ * Work is O(T N); it is the reference the library's error reports use. */
+int fmm_direct_field(const double* x, const double* p, const double* q, int64_t N,
+                     const int64_t* targets, int64_t T, double gbar, double* E, double* B,
+                     void* stream);
+
+void fmm_plan_destroy(fmm_plan_t plan);
+const char* fmm_strerror(int status);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char* fmm_last_cuda_error(void);
+int fmm_version(void);
+/* Number of CUDA kernels this process has launched through the library so far
+ * (all plans, all threads); differences around a region count its launches. */
+int64_t fmm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

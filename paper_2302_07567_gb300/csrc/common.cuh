@@ -1,0 +1,240 @@
+// Shared definitions of the CUDA translation units of the GB300 FMM.
+//
+// Coordinates inside the library.  After the tree is built every stage works
+// in "stretched, scaled" coordinates: x' = (x, y, gbar z) / ell, with ell a
+// power of two near the root box size.  In these coordinates the relativistic
+// kernel of Eq. 3.2 becomes the Coulomb kernel R'/|R'|^3 followed by a
+// diagonal rescale: g = ell^-2 diag(1, 1, 1/gbar) R'/|R'|^3.  The masses are
+// scaled by a power of two mu near max|q|: a' = q gamma / mu and
+// b~' = (q p_x / gbar, q p_y / gbar, q p_z) / mu, for which
+// b x g = ell^-2 diag(1, 1, gbar) (b~' x R') / |R'|^3 * mu.  Powers of two
+// make the scaling exact in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "fmm.h"
+
+namespace fmm {
+
+constexpr int kMaxDegree = 12;
+constexpr int kMaxNp1 = kMaxDegree + 1;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kC0 = 299792458.0;
+
+// device error bits (Counters::err)
+enum : unsigned {
+  kErrNonFinite = 1u,
+  kErrOvfFrontier = 2u,
+  kErrOvfP2P = 4u,
+  kErrOvfM2L = 8u,
+  kErrBounds = 16u,
+};
+
+// Device-resident counters of one call (first bytes of the workspace).
+struct Counters {
+  unsigned long long p2p_count;
+  unsigned long long m2l_count;
+  unsigned long long frontier_count[3];  // rotating: step k reads [k%3], appends to [(k+1)%3]
+  unsigned int err;
+  unsigned int pad[5];
+};
+
+// Chebyshev points of the second kind t_k = cos(k pi / n) and their
+// barycentric weights w_k = (-1)^k delta_k (delta = 1/2 at both ends), passed
+// to kernels by value.
+struct Cheb {
+  int n;
+  int np1;
+  double t[kMaxNp1];
+  double w[kMaxNp1];
+};
+
+// Per-node geometry in stretched, scaled coordinates (FP64).
+struct NodeGeo {
+  double c[3];  // box centre
+  double h[3];  // half widths (0 for a side of zero width)
+};
+
+// ------------------------------------------------------------- workspace
+struct Layout {
+  size_t total = 0;
+  // every field is a byte offset into the workspace
+  size_t counters, scal, psum_part, qmax_part;
+  size_t keys, keys_alt, vals, vals_alt, hist, scan_tmp;
+  size_t A, A_alt, rank, blocksum;
+  size_t nstart, ncount, nleftpre, nlo, nhi, naxis, nmed, ncen, ndiam, ngeo;
+  size_t perm, px, pb, pl;         // leaf-order particles (pl: low parts, FP32 only)
+  size_t p2p_dc, m2l_dc;           // per list pair: centre offset c_t - c_s as (hi, lo)
+  size_t mpole, local, srct;
+  size_t front0, front1, p2p, m2l, p2p_off, m2l_off, p2p_src, m2l_src, p2p_soff, m2l_soff;
+  size_t adj_w, adj_lam, adj_part;
+  size_t sort_n;      // elements the sort buffers hold
+  size_t nblk_sort;   // radix tiles at sort_n
+  size_t nblk_part;   // partition blocks at N
+};
+
+}  // namespace fmm
+
+struct fmm_plan_s {
+  int64_t N = 0;
+  int n = 0, np1 = 0, m = 0, leaf = 0, precision = 0;
+  unsigned flags = 0;
+  double eta = 0.0;
+  int kappa = 0;
+  int64_t C = 0, nleaves = 0;
+  int64_t cap_p2p = 0, cap_m2l = 0, cap_frontier = 0;
+  std::vector<int64_t> node_start, node_count, node_leftpre;  // index 0 unused
+  fmm::Layout lay;
+  fmm::Cheb cheb;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool have_forward = false;
+  int64_t p2p_count = 0, m2l_count = 0;
+  double gbar = 0.0, lunit = 1.0, munit = 1.0;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev[18] = {};
+  bool ev_made = false;
+  double stage_ms[16] = {};
+};
+
+namespace fmm {
+
+template <typename T>
+inline T* ws_ptr(const fmm_plan_s* p, size_t off) {
+  return reinterpret_cast<T*>(p->ws + off);
+}
+
+void set_last_cuda_error(cudaError_t e);
+void count_launch();
+
+#define FMM_CUDA_TRY(expr)                          \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) {                        \
+      ::fmm::set_last_cuda_error(_e);               \
+      return FMM_ECUDA;                             \
+    }                                               \
+  } while (0)
+
+#define FMM_LAUNCH_CHECK()                          \
+  do {                                              \
+    ::fmm::count_launch();                          \
+    cudaError_t _e = cudaGetLastError();            \
+    if (_e != cudaSuccess) {                        \
+      ::fmm::set_last_cuda_error(_e);               \
+      return FMM_ECUDA;                             \
+    }                                               \
+  } while (0)
+
+inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ------------------------------------------------------------- device helpers
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+// Squared separations (stretched, scaled units) at or below this count as a
+// coincident pair whose contribution is zero: 2^-84 in FP32 (below it r^-3
+// would overflow), 2^-100 in FP64.  Distinct particles closer than
+// 2^-42 (FP32) or 2^-50 (FP64) of the length unit are treated as coincident.
+template <typename T>
+__host__ __device__ __forceinline__ T tiny_sep2();
+template <>
+__host__ __device__ __forceinline__ float tiny_sep2<float>() { return 5.169878828456423e-26f; }
+template <>
+__host__ __device__ __forceinline__ double tiny_sep2<double>() { return 7.888609052210118e-31; }
+
+// Values of the n+1 Lagrange basis polynomials at the normalised coordinate
+// t in [-1, 1] (second, "true" barycentric form).  `degenerate` marks a box
+// side of zero width, whose basis is l_0 = 1, l_k = 0.  A coordinate that
+// coincides with a point t_k (to within `tiny`) gives the cardinal vector e_k.
+template <typename T>
+__device__ __forceinline__ void bary_basis(T t, bool degenerate, const Cheb& ch, T* out) {
+  const int np1 = ch.np1;
+  const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
+  int hit = degenerate ? 0 : -1;
+  if (!degenerate) {
+    for (int k = 0; k < np1; ++k) {
+      T d = t - T(ch.t[k]);
+      if (hit < 0 && fabs(d) <= tiny) hit = k;
+    }
+  }
+  if (hit >= 0) {
+    for (int k = 0; k < np1; ++k) out[k] = (k == hit) ? T(1) : T(0);
+    return;
+  }
+  T s = T(0);
+  for (int k = 0; k < np1; ++k) {
+    T v = T(ch.w[k]) / (t - T(ch.t[k]));
+    out[k] = v;
+    s += v;
+  }
+  T inv = T(1) / s;
+  for (int k = 0; k < np1; ++k) out[k] *= inv;
+}
+
+// Kahan-compensated accumulation: (sum, comp) += v.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
+  T y = v - comp;
+  T t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// Node of a breadth-first tree level containing slot `pos`: binary search in
+// the first slots of the 2^level nodes [first, first + count).
+__device__ __forceinline__ int64_t find_node(const int64_t* __restrict__ nstart, int64_t first,
+                                             int64_t count, int64_t pos) {
+  int64_t lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (nstart[first + mid] <= pos) lo = mid; else hi = mid - 1;
+  }
+  return first + lo;
+}
+
+}  // namespace fmm
+
+// ------------------------------------------------------------- stage entry points
+namespace fmm {
+int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
+int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s);
+int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
+int run_upward(fmm_plan_s* P, cudaStream_t s);
+int run_traverse(fmm_plan_s* P, cudaStream_t s);
+int run_list_sort(fmm_plan_s* P, cudaStream_t s);
+int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
+int run_pair_offsets(fmm_plan_s* P, cudaStream_t s);
+int run_m2l(fmm_plan_s* P, cudaStream_t s);
+int run_l2l(fmm_plan_s* P, cudaStream_t s);
+int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);
+int run_adjoint(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE,
+                const void* wB, double* dx, double* dp, double* dq, cudaStream_t s);
+// radix sort of 64-bit keys (optionally with 32-bit values) over bits
+// [begin_bit, end_bit); returns in `*in_alt` whether the result sits in the
+// alternate buffers.
+int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
+               int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
+               cudaStream_t s, bool* in_alt);
+int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
+// separable transfer between the nodes of `level` and their children (see upward.cu)
+template <typename T, int NC, bool UP>
+int launch_transfer(fmm_plan_s* P, int level, T* buf, cudaStream_t s);
+int64_t radix_tiles(int64_t n);
+int64_t scan_tmp_words(int64_t n);
+}  // namespace fmm

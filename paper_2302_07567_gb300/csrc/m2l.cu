@@ -1,0 +1,158 @@
+// M2L (Alg. 9, Eq. 2.5 with the effective masses of Section 3).
+//
+// One block per target cluster t drains t's M2L list (sorted by target, so no
+// two blocks write the same locals and no atomics are needed, Section 10).
+// Each thread owns KPT proxy points mu of t.  For every source cluster the
+// source's proxy table (point offsets Y_nu and effective masses a_nu, b~_nu)
+// is staged in shared memory and every owned point accumulates
+//   E_mu += a_nu R / |R|^3,  B_mu += b~_nu x R / |R|^3,  R = xi_t,mu - xi_s,nu
+// in stretched, scaled coordinates.  The centre difference c_t - c_s is
+// formed in FP64 once per list pair and rounded once; per-source partial sums are added to the
+// running sums with Kahan compensation.  Locals of clusters without M2L
+// sources are written as zeros.
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+template <typename T, int KPT>
+__global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
+                                             int shift, const NodeGeo* __restrict__ geo,
+                                             const void* __restrict__ pdc, Cheb ch, int m,
+                                             const typename Vec4<T>::type* __restrict__ src, T* __restrict__ Lout) {
+  using V4 = typename Vec4<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  V4* sm = reinterpret_cast<V4*>(smem_raw);
+  const int64_t t = (int64_t)blockIdx.x + 1;
+  const int np1 = ch.np1;
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const int b = off[t], e = off[t + 1];
+  const NodeGeo gt = geo[t];
+  const int per_pass = KPT * blockDim.x;
+  for (int pass0 = 0; pass0 < m; pass0 += per_pass) {
+    T xh[KPT][3];
+    bool valid[KPT];
+    T acc[KPT][6], cmp[KPT][6];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int mu = pass0 + threadIdx.x + k * blockDim.x;
+      valid[k] = mu < m;
+      const int mm = valid[k] ? mu : 0;
+      const int m1 = mm % np1, m2 = (mm / np1) % np1, m3 = mm / (np1 * np1);
+      xh[k][0] = (T)(gt.h[0] * ch.t[m1]);
+      xh[k][1] = (T)(gt.h[1] * ch.t[m2]);
+      xh[k][2] = (T)(gt.h[2] * ch.t[m3]);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[k][c] = cmp[k][c] = T(0);
+    }
+    for (int it = b; it < e; ++it) {
+      const int64_t s = (int64_t)(keys[it] & mask);
+      T dc0, dc1, dc2;
+      if constexpr (sizeof(T) == 4) {  // FP32: the pair's centre offset, rounded once from FP64
+        const float4 dh = static_cast<const float4*>(pdc)[2 * it];
+        dc0 = dh.x; dc1 = dh.y; dc2 = dh.z;
+      } else {
+        const double4 dd = static_cast<const double4*>(pdc)[it];
+        dc0 = dd.x; dc1 = dd.y; dc2 = dd.z;
+      }
+      const V4* tab = src + (size_t)s * m * 2;
+      __syncthreads();
+      for (int o = threadIdx.x; o < 2 * m; o += blockDim.x) sm[o] = tab[o];
+      __syncthreads();
+      T X[KPT][3], part[KPT][6];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        X[k][0] = dc0 + xh[k][0];
+        X[k][1] = dc1 + xh[k][1];
+        X[k][2] = dc2 + xh[k][2];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) part[k][c] = T(0);
+      }
+      for (int nu = 0; nu < m; ++nu) {
+        const V4 ya = sm[2 * nu], bb = sm[2 * nu + 1];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          const T rx = X[k][0] - ya.x, ry = X[k][1] - ya.y, rz = X[k][2] - ya.z;
+          const T d = rx * rx + ry * ry + rz * rz;
+          const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+          const T r3 = inv * inv * inv;
+          const T ar3 = ya.w * r3;
+          part[k][0] += ar3 * rx;
+          part[k][1] += ar3 * ry;
+          part[k][2] += ar3 * rz;
+          part[k][3] += r3 * (bb.y * rz - bb.z * ry);
+          part[k][4] += r3 * (bb.z * rx - bb.x * rz);
+          part[k][5] += r3 * (bb.x * ry - bb.y * rx);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int mu = pass0 + threadIdx.x + k * blockDim.x;
+      if (!valid[k]) continue;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + mu] = acc[k][c];
+    }
+  }
+}
+
+// Block shape: threads nt <= 256 (a multiple of 32) owning KPT points each,
+// chosen to waste the fewest thread slots, then to need the fewest passes.
+void pick_shape(int m, int* nt, int* kpt) {
+  int best_nt = 256, best_k = 4;
+  int64_t best_waste = -1, best_passes = 0;
+  for (int k = 1; k <= 4; ++k) {
+    int t = (int)(div_up(div_up(m, k), 32) * 32);
+    if (t > 256) t = 256;
+    const int64_t passes = div_up(m, (int64_t)t * k);
+    const int64_t waste = passes * t * k - m;
+    if (best_waste < 0 || waste < best_waste || (waste == best_waste && passes < best_passes)) {
+      best_waste = waste;
+      best_passes = passes;
+      best_nt = t;
+      best_k = k;
+    }
+  }
+  *nt = best_nt;
+  *kpt = best_k;
+}
+
+template <typename T, int KPT>
+int launch(fmm_plan_s* P, int nt, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const size_t smem = (size_t)2 * P->m * sizeof(typename Vec4<T>::type);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_m2l<T, KPT><<<(unsigned)P->C, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
+                                                  P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_dc, P->cheb, P->m,
+                                                  ws_ptr<typename Vec4<T>::type>(P, L.srct), ws_ptr<T>(P, L.local));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int m2l_t(fmm_plan_s* P, cudaStream_t s) {
+  int nt, kpt;
+  pick_shape(P->m, &nt, &kpt);
+  switch (kpt) {
+    case 1: return launch<T, 1>(P, nt, s);
+    case 2: return launch<T, 2>(P, nt, s);
+    case 3: return launch<T, 3>(P, nt, s);
+    default: return launch<T, 4>(P, nt, s);
+  }
+}
+
+}  // namespace
+
+int run_m2l(fmm_plan_s* P, cudaStream_t s) {
+  return P->precision == FMM_FP32 ? m2l_t<float>(P, s) : m2l_t<double>(P, s);
+}
+
+}  // namespace fmm

@@ -1,0 +1,265 @@
+// P2P (Alg. 10) fused with L2P (Alg. 14) and the output transform.
+//
+// One block per target leaf drains the leaf's P2P list (sorted by target, so
+// each particle's fields are written by exactly one thread; Section 10).
+// Every thread owns KPT target particles.  Source leaves are contiguous
+// slot ranges of the leaf-ordered particle arrays, staged through shared
+// memory a block-width at a time.  A pair whose squared stretched, scaled
+// separation is at or below tiny_sep2 (the particle itself, or two particles
+// at the same position, which the leaf-relative coordinates may place a few
+// units of the last place apart) contributes nothing.  Per-source-leaf partial sums are added with Kahan compensation.
+//
+// Separations in FP32: positions are stored relative to their leaf's centre
+// as unevaluated sums hi + lo of two floats, and the centre offset c_t - c_s
+// of every pair likewise, so R = (X_hi - x_hi) + (X_lo - x_lo) with
+// X = x_i + (c_t - c_s) keeps the relative precision of R itself even for
+// two particles much closer to each other than to their leaf centres.
+// (With single floats the absolute position error, ~2^-24 of the leaf size,
+// dominates the field of such close pairs.)
+//
+// Separations in FP64: positions are absolute physical coordinates and R is
+// x_i - x_j with the stretch applied inside D, exactly as Eq. 3.2 is written
+// (exact for close pairs); the summed near field is then converted to the
+// stretched, scaled convention of the far field.
+//
+// Afterwards each thread adds the far field of its particles from the
+// leaf's cumulative local field (Eq. 2.8), converts from stretched, scaled
+// units to SI (E_z / gbar, B_z * gbar, prefactors 1/(4 pi eps0) and 1/c0) and
+// writes the row of the particle's input index.
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <typename T, int KPT>
+__global__ void __launch_bounds__(256) k_p2p_l2p(
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
+    const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
+    const typename Vec4<T>::type* __restrict__ pb, const float4* __restrict__ pl,  // Vec4<T> rows
+    const void* __restrict__ pdc_raw, const T* __restrict__ Lcum, Cheb ch, int m,
+    const int32_t* __restrict__ perm, const double* __restrict__ scal, T* __restrict__ Eout,
+    T* __restrict__ Bout) {
+  using V4 = typename Vec4<T>::type;
+  constexpr bool kSplit = std::is_same<T, float>::value;  // hi + lo separations
+  constexpr int kRow = kSplit ? 3 : 2;                      // V4 per staged source particle
+  extern __shared__ unsigned char smem_raw[];
+  V4* sp = reinterpret_cast<V4*>(smem_raw);                                // [blockDim][kRow]
+  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [6][m]
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[t], cnt = ncount[t];
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const NodeGeo gt = geo[t];
+  const int b = off[t], e = off[t + 1];
+  const int np1 = ch.np1;
+  const double gbar = scal[0], kE = scal[4], kB = scal[5];
+  T invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(gt.h[d] > 0.0);
+    invh[d] = deg[d] ? T(0) : (T)(1.0 / gt.h[d]);
+  }
+  if (kappa > 0) {  // the leaf's cumulative local field, for L2P below
+    const T* Lt = Lcum + (size_t)t * 6 * m;
+    for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
+  }
+  const double ell2 = scal[2] * scal[2];
+  const T g2 = (T)(gbar * gbar);
+  const int64_t per_pass = (int64_t)KPT * blockDim.x;
+  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+    T ri[KPT][3], rl[KPT][3];
+    bool valid[KPT];
+    T acc[KPT][6], cmp[KPT][6];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      valid[k] = j < cnt;
+      const int64_t jj = st + (valid[k] ? j : 0);
+      const V4 u = px[jj];
+      ri[k][0] = u.x; ri[k][1] = u.y; ri[k][2] = u.z;
+      // FP32: low parts of the leaf-relative position; FP64: absolute physical position
+      const V4 l = reinterpret_cast<const V4*>(pl)[jj];
+      rl[k][0] = l.x; rl[k][1] = l.y; rl[k][2] = l.z;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[k][c] = cmp[k][c] = T(0);
+    }
+    for (int it = b; it < e; ++it) {
+      const int64_t s = (int64_t)(keys[it] & mask);
+      const int64_t sst = nstart[s], scnt = ncount[s];
+      T X[KPT][3], XL[KPT][3], part[KPT][6];
+      if constexpr (kSplit) {
+        const float4* pdc = static_cast<const float4*>(pdc_raw);
+        const float4 dh = pdc[2 * it], dl = pdc[2 * it + 1];
+        const float dch[3] = {dh.x, dh.y, dh.z}, dcl[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float hs, he;
+            two_sum(ri[k][d], dch[d], hs, he);
+            const float lo = he + (rl[k][d] + dcl[d]);
+            X[k][d] = hs + lo;
+            XL[k][d] = lo - (X[k][d] - hs);
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            X[k][d] = rl[k][d];
+            XL[k][d] = T(0);
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) part[k][c] = T(0);
+      for (int64_t base = 0; base < scnt; base += blockDim.x) {
+        __syncthreads();
+        const int64_t j = base + threadIdx.x;
+        if (j < scnt) {
+          if constexpr (kSplit) {
+            sp[kRow * threadIdx.x] = px[sst + j];
+            sp[kRow * threadIdx.x + 1] = pb[sst + j];
+            reinterpret_cast<float4*>(sp)[kRow * threadIdx.x + 2] = pl[sst + j];
+          } else {  // absolute physical position with a', and b' = (b~x gbar, b~y gbar, b~z)
+            const V4 a = reinterpret_cast<const V4*>(pl)[sst + j], u = px[sst + j], w = pb[sst + j];
+            V4 r0, r1;
+            r0.x = a.x; r0.y = a.y; r0.z = a.z; r0.w = u.w;
+            r1.x = w.x * (T)gbar; r1.y = w.y * (T)gbar; r1.z = w.z; r1.w = T(0);
+            sp[kRow * threadIdx.x] = r0;
+            sp[kRow * threadIdx.x + 1] = r1;
+          }
+        }
+        __syncthreads();
+        const int nj = (int)min64(blockDim.x, scnt - base);
+        for (int jj = 0; jj < nj; ++jj) {
+          const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
+          V4 ul;
+          if constexpr (kSplit) ul = sp[kRow * jj + 2];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            T rx, ry, rz, d, inv;
+            if constexpr (kSplit) {
+              rx = (X[k][0] - u.x) + (XL[k][0] - ul.x);
+              ry = (X[k][1] - u.y) + (XL[k][1] - ul.y);
+              rz = (X[k][2] - u.z) + (XL[k][2] - ul.z);
+              d = rx * rx + ry * ry + rz * rz;
+              inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+            } else {  // Eq. 3.2 as written, in physical coordinates
+              rx = X[k][0] - u.x;
+              ry = X[k][1] - u.y;
+              rz = X[k][2] - u.z;
+              d = rx * rx + ry * ry + g2 * (rz * rz);
+              inv = d > T(0) ? rsqrt_t<T>(d) : T(0);
+            }
+            const T r3 = inv * inv * inv;
+            const T ar3 = u.w * r3;
+            part[k][0] += ar3 * rx;
+            part[k][1] += ar3 * ry;
+            part[k][2] += ar3 * rz;
+            part[k][3] += r3 * (w.y * rz - w.z * ry);
+            part[k][4] += r3 * (w.z * rx - w.x * rz);
+            part[k][5] += r3 * (w.x * ry - w.y * rx);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
+    }
+    if constexpr (!kSplit) {  // physical near field -> stretched, scaled convention of the far field
+      const T fe[6] = {(T)ell2, (T)ell2, (T)(ell2 * gbar), (T)ell2, (T)ell2, (T)(ell2 / gbar)};
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          acc[k][c] *= fe[c];
+          cmp[k][c] *= fe[c];
+        }
+    }
+    __syncthreads();  // sl (loaded above) is visible to every thread from here on
+
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (!valid[k]) continue;
+      if (kappa > 0) {  // far field: L2P from the cumulative local field of the leaf
+        T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1];
+        const T lof = kSplit ? T(1) : T(0);
+        bary_basis<T>((ri[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, lx);
+        bary_basis<T>((ri[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, ly);
+        bary_basis<T>((ri[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, lz);
+        T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        int mu = 0;
+        for (int a3 = 0; a3 < np1; ++a3) {
+          for (int a2 = 0; a2 < np1; ++a2) {
+            const T w = lz[a3] * ly[a2];
+            T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+            for (int a1 = 0; a1 < np1; ++a1, ++mu) {
+#pragma unroll
+              for (int c = 0; c < 6; ++c) g[c] += lx[a1] * sl[c * m + mu];
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) f[c] += w * g[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kahan_add(acc[k][c], cmp[k][c], f[c]);
+      }
+      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      const int64_t i = perm[pos];
+      Eout[3 * i + 0] = (T)(kE * (double)acc[k][0]);
+      Eout[3 * i + 1] = (T)(kE * (double)acc[k][1]);
+      Eout[3 * i + 2] = (T)(kE * (double)acc[k][2] / gbar);
+      Bout[3 * i + 0] = (T)(kB * (double)acc[k][3]);
+      Bout[3 * i + 1] = (T)(kB * (double)acc[k][4]);
+      Bout[3 * i + 2] = (T)(kB * (double)acc[k][5] * gbar);
+    }
+  }
+}
+
+template <typename T, int KPT>
+int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const int nt = (int)std::min<int64_t>(256, div_up(div_up(P->leaf, KPT), 32) * 32);
+  const int row = std::is_same<T, float>::value ? 3 : 2;
+  const size_t smem = sizeof(typename Vec4<T>::type) * row * nt + sizeof(T) * 6 * P->m;
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2p_l2p<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_p2p_l2p<T, KPT><<<(unsigned)P->nleaves, nt, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+      ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb), ws_ptr<float4>(P, L.pl),
+      P->ws + L.p2p_dc, ws_ptr<T>(P, L.local), P->cheb, P->m, ws_ptr<int32_t>(P, L.perm),
+      ws_ptr<double>(P, L.scal), static_cast<T*>(E), static_cast<T*>(B));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int p2p_t(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
+  const int64_t kpt = div_up(P->leaf, 256);
+  if (kpt <= 1) return launch<T, 1>(P, E, B, s);
+  return launch<T, 2>(P, E, B, s);
+}
+
+}  // namespace
+
+int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
+  return P->precision == FMM_FP32 ? p2p_t<float>(P, E, B, s) : p2p_t<double>(P, E, B, s);
+}
+
+}  // namespace fmm

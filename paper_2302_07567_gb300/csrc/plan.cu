@@ -1,0 +1,463 @@
+// C ABI: plans, workspace, forward pass driver (Alg. 12), statistics, export.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace fmm {
+
+static thread_local std::string g_last_cuda_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_last_cuda_error(cudaError_t e) {
+  g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+}
+
+namespace {
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+void make_layout(fmm_plan_s* P) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t N = (size_t)P->N, C1 = (size_t)P->C + 1, m = (size_t)P->m;
+  const size_t R = P->precision == FMM_FP32 ? sizeof(float) : sizeof(double);
+  const size_t V4 = 4 * R;
+  const int64_t sort_n = std::max<int64_t>({P->N, P->cap_p2p, P->cap_m2l, 1});
+  const int64_t tiles = radix_tiles(sort_n);
+  const int64_t nblk_part = div_up(P->N, 2048);
+  L.sort_n = (size_t)sort_n;
+  L.nblk_sort = (size_t)tiles;
+  L.nblk_part = (size_t)nblk_part;
+  L.counters = take(sizeof(Counters));
+  L.scal = take(16 * sizeof(double));
+  const size_t np0 = (size_t)div_up(P->N, 2048);
+  L.psum_part = take(3 * 2 * (np0 + 2) * sizeof(double));
+  L.qmax_part = take(1024 * sizeof(double));
+  L.keys = take(sort_n * 8);
+  L.keys_alt = take(sort_n * 8);
+  L.vals = take(N * 4);
+  L.vals_alt = take(N * 4);
+  L.hist = take((size_t)256 * tiles * 4);
+  L.scan_tmp = take((size_t)scan_tmp_words(std::max<int64_t>(256 * tiles, nblk_part)) * 4 + 1024);
+  L.A = take(3 * N * 4);
+  L.A_alt = take(3 * N * 4);
+  L.rank = take(3 * N * 4);
+  L.blocksum = take(3 * (size_t)nblk_part * 4);
+  L.nstart = take(C1 * 8);
+  L.ncount = take(C1 * 8);
+  L.nleftpre = take(C1 * 8);
+  L.nlo = take(C1 * 3 * 8);
+  L.nhi = take(C1 * 3 * 8);
+  L.naxis = take(C1 * 4);
+  L.nmed = take(C1 * 4);
+  L.ncen = take(C1 * 3 * 8);
+  L.ndiam = take(C1 * 8);
+  L.ngeo = take(C1 * sizeof(NodeGeo));
+  L.perm = take(N * 4);
+  L.px = take(N * V4);
+  L.pb = take(N * V4);
+  L.pl = take(N * V4);
+  L.mpole = take(C1 * 4 * m * R);
+  L.local = take(C1 * 6 * m * R);
+  L.srct = take(C1 * m * 2 * V4);
+  L.front0 = take((size_t)P->cap_frontier * 8);
+  L.front1 = take((size_t)P->cap_frontier * 8);
+  L.p2p = take((size_t)P->cap_p2p * 8);
+  L.m2l = take((size_t)P->cap_m2l * 8);
+  L.p2p_off = take((C1 + 1) * 4);
+  L.m2l_off = take((C1 + 1) * 4);
+  L.p2p_src = take((size_t)P->cap_p2p * 8);
+  L.m2l_src = take((size_t)P->cap_m2l * 8);
+  L.p2p_soff = take((C1 + 1) * 4);
+  L.p2p_dc = take((size_t)P->cap_p2p * 32);
+  L.m2l_dc = take((size_t)P->cap_m2l * 32);
+  L.m2l_soff = take((C1 + 1) * 4);
+  // adjoint: weights W (6 comp) and adjoint moments Lambda (4 comp) per node,
+  // and per-particle gradient parts in leaf order
+  L.adj_w = take(C1 * 6 * m * R);
+  L.adj_lam = take(C1 * 4 * m * R);
+  L.adj_part = take(N * 8 * sizeof(double));
+  L.total = off;
+  P->lay = L;
+}
+
+void make_tables(fmm_plan_s* P) {
+  const int64_t C = P->C;
+  P->node_start.assign(C + 1, 0);
+  P->node_count.assign(C + 1, 0);
+  P->node_leftpre.assign(C + 1, 0);
+  P->node_start[1] = 0;
+  P->node_count[1] = P->N;
+  for (int l = 0; l < P->kappa; ++l) {
+    int64_t pre = 0;
+    for (int64_t i = (int64_t)1 << l; i < ((int64_t)2 << l); ++i) {
+      const int64_t c = P->node_count[i], h1 = (c + 1) / 2;
+      P->node_leftpre[i] = pre;
+      pre += h1;
+      P->node_start[2 * i] = P->node_start[i];
+      P->node_count[2 * i] = h1;
+      P->node_start[2 * i + 1] = P->node_start[i] + h1;
+      P->node_count[2 * i + 1] = c - h1;
+    }
+  }
+  Cheb& ch = P->cheb;
+  std::memset(&ch, 0, sizeof(ch));
+  ch.n = P->n;
+  ch.np1 = P->np1;
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k <= P->n; ++k) {
+    // cos(k pi / n) written as sin(pi (n - 2k) / (2n)): exact symmetry, exact 0
+    ch.t[k] = std::sin(pi * (double)(P->n - 2 * k) / (2.0 * P->n));
+    ch.w[k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == P->n) ? 0.5 : 1.0);
+  }
+}
+
+void default_caps(fmm_plan_s* P) {
+  if (P->cap_p2p <= 0) P->cap_p2p = 64 * P->nleaves + 1024;
+  if (P->cap_m2l <= 0) P->cap_m2l = 128 * P->C + 1024;
+  if (P->cap_frontier <= 0) P->cap_frontier = P->cap_p2p + P->cap_m2l;
+}
+
+int ensure_events(fmm_plan_s* P) {
+  if (P->ev_made) return FMM_OK;
+  for (auto& e : P->ev) FMM_CUDA_TRY(cudaEventCreate(&e));
+  P->ev_made = true;
+  return FMM_OK;
+}
+
+int record(fmm_plan_s* P, int k, cudaStream_t s) {
+  if (!(P->flags & FMM_TIMING)) return FMM_OK;
+  FMM_CUDA_TRY(cudaEventRecord(P->ev[k], s));
+  return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+int fmm_version(void) { return 1; }
+
+int64_t fmm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char* fmm_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+const char* fmm_strerror(int status) {
+  switch (status) {
+    case FMM_OK: return "ok";
+    case FMM_EINVAL: return "invalid argument";
+    case FMM_ENOWORKSPACE: return "no or too small workspace attached";
+    case FMM_EOVERFLOW: return "interaction-list capacity exceeded";
+    case FMM_ENONFINITE: return "non-finite value in x or p";
+    case FMM_ESTATE: return "adjoint called without a successful forward call";
+    case FMM_ECUDA: return "CUDA runtime error";
+    case FMM_EBOUNDS: return "device index check failed";
+    default: return "unknown status";
+  }
+}
+
+int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, double eta, int precision,
+                    unsigned flags) {
+  if (!out) return FMM_EINVAL;
+  *out = nullptr;
+  if (N < 1 || N > ((int64_t)1 << 30)) return FMM_EINVAL;
+  if (degree < 1 || degree > kMaxDegree) return FMM_EINVAL;
+  if (leaf_size < 2 || leaf_size > 4096) return FMM_EINVAL;
+  if (!(eta > 0.0) || !std::isfinite(eta)) return FMM_EINVAL;
+  if (precision != FMM_FP32 && precision != FMM_FP64) return FMM_EINVAL;
+  fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
+  if (!P) return FMM_EINVAL;
+  P->N = N;
+  P->n = degree;
+  P->np1 = degree + 1;
+  P->m = P->np1 * P->np1 * P->np1;
+  P->leaf = leaf_size;
+  P->eta = eta;
+  P->precision = precision;
+  P->flags = flags;
+  int kappa = 0;
+  if (N > leaf_size) {
+    while ((int64_t)leaf_size * ((int64_t)1 << kappa) < N) ++kappa;
+  }
+  P->kappa = kappa;
+  P->C = ((int64_t)2 << kappa) - 1;
+  P->nleaves = (int64_t)1 << kappa;
+  default_caps(P);
+  make_tables(P);
+  make_layout(P);
+  *out = P;
+  return FMM_OK;
+}
+
+int fmm_plan_set_capacity(fmm_plan_t P, int64_t p2p_pairs, int64_t m2l_pairs, int64_t frontier_pairs) {
+  if (!P || p2p_pairs < 0 || m2l_pairs < 0 || frontier_pairs < 0) return FMM_EINVAL;
+  if (p2p_pairs > 0) P->cap_p2p = p2p_pairs;
+  if (m2l_pairs > 0) P->cap_m2l = m2l_pairs;
+  if (frontier_pairs > 0) P->cap_frontier = frontier_pairs;
+  default_caps(P);
+  make_layout(P);
+  P->ws = nullptr;
+  P->ws_bytes = 0;
+  P->have_forward = false;
+  return FMM_OK;
+}
+
+int fmm_plan_workspace_bytes(fmm_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return FMM_EINVAL;
+  *bytes = P->lay.total;
+  return FMM_OK;
+}
+
+int fmm_plan_set_workspace(fmm_plan_t P, void* dev, size_t bytes) {
+  if (!P || !dev) return FMM_EINVAL;
+  if (bytes < P->lay.total || ((uintptr_t)dev & 255u)) return FMM_ENOWORKSPACE;
+  P->ws = static_cast<char*>(dev);
+  P->ws_bytes = bytes;
+  P->have_forward = false;
+  const size_t tb = sizeof(int64_t) * (size_t)(P->C + 1);
+  FMM_CUDA_TRY(cudaMemcpy(P->ws + P->lay.nstart, P->node_start.data(), tb, cudaMemcpyHostToDevice));
+  FMM_CUDA_TRY(cudaMemcpy(P->ws + P->lay.ncount, P->node_count.data(), tb, cudaMemcpyHostToDevice));
+  FMM_CUDA_TRY(cudaMemcpy(P->ws + P->lay.nleftpre, P->node_leftpre.data(), tb, cudaMemcpyHostToDevice));
+  return FMM_OK;
+}
+
+int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, void* E, void* B, void* stream) {
+  if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
+  if (!P->ws) return FMM_ENOWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->have_forward = false;
+  P->last_stream = s;
+  int rc;
+  if (P->flags & FMM_TIMING) {
+    if ((rc = ensure_events(P)) != FMM_OK) return rc;
+  }
+  if ((rc = record(P, 0, s)) != FMM_OK) return rc;
+  if ((rc = run_setup(P, x, p, q, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 1, s)) != FMM_OK) return rc;
+  if ((rc = run_tree(P, x, s)) != FMM_OK) return rc;
+  if ((rc = run_prep(P, x, p, q, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 2, s)) != FMM_OK) return rc;
+  if ((rc = run_upward(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 3, s)) != FMM_OK) return rc;
+  if ((rc = run_traverse(P, s)) != FMM_OK) return rc;
+  Counters hc;
+  double hs[8];
+  FMM_CUDA_TRY(cudaMemcpyAsync(&hc, P->ws + P->lay.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaMemcpyAsync(hs, P->ws + P->lay.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hc.err & kErrNonFinite) return FMM_ENONFINITE;
+  if ((hc.err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || (int64_t)hc.p2p_count > P->cap_p2p ||
+      (int64_t)hc.m2l_count > P->cap_m2l) {
+    P->p2p_count = (int64_t)hc.p2p_count;
+    P->m2l_count = (int64_t)hc.m2l_count;
+    return FMM_EOVERFLOW;
+  }
+  P->p2p_count = (int64_t)hc.p2p_count;
+  P->m2l_count = (int64_t)hc.m2l_count;
+  P->gbar = hs[0];
+  P->munit = hs[1];
+  P->lunit = hs[2];
+  if ((rc = record(P, 4, s)) != FMM_OK) return rc;
+  if ((rc = run_list_sort(P, s)) != FMM_OK) return rc;
+  if ((rc = run_pair_offsets(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 5, s)) != FMM_OK) return rc;
+  if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 6, s)) != FMM_OK) return rc;
+  if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 7, s)) != FMM_OK) return rc;
+  if ((rc = run_p2p_l2p(P, E, B, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 8, s)) != FMM_OK) return rc;
+  P->have_forward = true;
+  return FMM_OK;
+}
+
+int fmm_field_adjoint(fmm_plan_t P, const double* x, const double* p, const double* q, const void* wE,
+                      const void* wB, double* dx, double* dp, double* dq, void* stream) {
+  if (!P || !x || !p || !q || !wE || !wB || !dx || !dp || !dq) return FMM_EINVAL;
+  if (!P->ws) return FMM_ENOWORKSPACE;
+  if (!P->have_forward) return FMM_ESTATE;
+  return run_adjoint(P, x, p, q, wE, wB, dx, dp, dq, static_cast<cudaStream_t>(stream));
+}
+
+int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
+  if (!P || !out) return FMM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->N = P->N;
+  out->nodes = P->C;
+  out->leaves = P->nleaves;
+  out->degree = P->n;
+  out->leaf_size = P->leaf;
+  out->kappa = P->kappa;
+  out->precision = P->precision;
+  out->eta = P->eta;
+  out->gbar = P->gbar;
+  out->length_unit = P->lunit;
+  out->mass_unit = P->munit;
+  out->p2p_pairs = P->p2p_count;
+  out->m2l_pairs = P->m2l_count;
+  out->cap_p2p = P->cap_p2p;
+  out->cap_m2l = P->cap_m2l;
+  out->cap_frontier = P->cap_frontier;
+  out->m2l_interactions = (double)P->m2l_count * (double)P->m * (double)P->m;
+  if (P->have_forward && P->p2p_count > 0 && P->ws) {
+    std::vector<uint64_t> keys((size_t)P->p2p_count);
+    FMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    FMM_CUDA_TRY(cudaMemcpy(keys.data(), P->ws + P->lay.p2p, 8 * keys.size(), cudaMemcpyDeviceToHost));
+    const int shift = P->kappa + 1;
+    const uint64_t mask = ((uint64_t)1 << shift) - 1;
+    double tot = 0.0;
+    for (uint64_t k : keys) tot += (double)P->node_count[k >> shift] * (double)P->node_count[k & mask];
+    out->p2p_interactions = tot - (double)P->N;
+  }
+  if ((P->flags & FMM_TIMING) && P->ev_made) {
+    FMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    for (int k = 0; k < 16; ++k) P->stage_ms[k] = 0.0;
+    auto el = [&](int a, int b) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, P->ev[a], P->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+      }
+      return (double)ms;
+    };
+    P->stage_ms[0] = el(0, 1);
+    P->stage_ms[1] = el(1, 2);
+    P->stage_ms[2] = el(2, 3);
+    P->stage_ms[3] = el(3, 4);
+    P->stage_ms[4] = el(4, 5);
+    P->stage_ms[5] = el(5, 6);
+    P->stage_ms[6] = el(6, 7);
+    P->stage_ms[7] = el(7, 8);
+    P->stage_ms[13] = el(0, 8);
+    if (P->flags & 0x100u) {  // adjoint events recorded
+      P->stage_ms[8] = el(9, 10);
+      P->stage_ms[9] = el(10, 11);
+      P->stage_ms[10] = el(11, 12);
+      P->stage_ms[11] = el(12, 13);
+      P->stage_ms[12] = el(13, 14);
+      P->stage_ms[14] = el(9, 14);
+    }
+    for (int k = 0; k < 16; ++k) out->stage_ms[k] = P->stage_ms[k];
+  }
+  return FMM_OK;
+}
+
+int fmm_plan_export(fmm_plan_t P, int what, void* host, size_t bytes) {
+  if (!P || !host) return FMM_EINVAL;
+  if (!P->ws || !P->have_forward) return FMM_ESTATE;
+  const int64_t C = P->C, N = P->N, m = P->m;
+  FMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+  const Layout& L = P->lay;
+  const bool f32 = P->precision == FMM_FP32;
+  auto need = [&](size_t b) { return bytes >= b; };
+  switch (what) {
+    case FMM_EXPORT_GBAR: {
+      if (!need(8)) return FMM_EINVAL;
+      std::memcpy(host, &P->gbar, 8);
+      return FMM_OK;
+    }
+    case FMM_EXPORT_PERM: {
+      if (!need(4 * N)) return FMM_EINVAL;
+      FMM_CUDA_TRY(cudaMemcpy(host, P->ws + L.perm, 4 * N, cudaMemcpyDeviceToHost));
+      return FMM_OK;
+    }
+    case FMM_EXPORT_NODES: {
+      if (!need(16 * C)) return FMM_EINVAL;
+      int64_t* o = static_cast<int64_t*>(host);
+      for (int64_t i = 1; i <= C; ++i) {
+        o[2 * (i - 1)] = P->node_start[i];
+        o[2 * (i - 1) + 1] = P->node_count[i];
+      }
+      return FMM_OK;
+    }
+    case FMM_EXPORT_BBOX: {
+      if (!need(48 * C)) return FMM_EINVAL;
+      std::vector<double> lo(3 * (C + 1)), hi(3 * (C + 1));
+      FMM_CUDA_TRY(cudaMemcpy(lo.data(), P->ws + L.nlo, 8 * lo.size(), cudaMemcpyDeviceToHost));
+      FMM_CUDA_TRY(cudaMemcpy(hi.data(), P->ws + L.nhi, 8 * hi.size(), cudaMemcpyDeviceToHost));
+      double* o = static_cast<double*>(host);
+      for (int64_t i = 1; i <= C; ++i)
+        for (int k = 0; k < 3; ++k) {
+          o[6 * (i - 1) + k] = lo[3 * i + k];
+          o[6 * (i - 1) + 3 + k] = hi[3 * i + k];
+        }
+      return FMM_OK;
+    }
+    case FMM_EXPORT_AXIS: {
+      if (!need(4 * C)) return FMM_EINVAL;
+      std::vector<int32_t> ax(C + 1);
+      FMM_CUDA_TRY(cudaMemcpy(ax.data(), P->ws + L.naxis, 4 * ax.size(), cudaMemcpyDeviceToHost));
+      std::memcpy(host, ax.data() + 1, 4 * C);
+      return FMM_OK;
+    }
+    case FMM_EXPORT_P2P:
+    case FMM_EXPORT_M2L: {
+      const int64_t n = what == FMM_EXPORT_P2P ? P->p2p_count : P->m2l_count;
+      if (!need(8 * n)) return FMM_EINVAL;
+      std::vector<uint64_t> keys((size_t)n);
+      if (n > 0)
+        FMM_CUDA_TRY(cudaMemcpy(keys.data(), P->ws + (what == FMM_EXPORT_P2P ? L.p2p : L.m2l), 8 * n,
+                                cudaMemcpyDeviceToHost));
+      const int shift = P->kappa + 1;
+      const uint64_t mask = ((uint64_t)1 << shift) - 1;
+      int32_t* o = static_cast<int32_t*>(host);
+      for (int64_t e = 0; e < n; ++e) {
+        o[2 * e] = (int32_t)(keys[e] >> shift);
+        o[2 * e + 1] = (int32_t)(keys[e] & mask);
+      }
+      return FMM_OK;
+    }
+    case FMM_EXPORT_MULTIPOLE:
+    case FMM_EXPORT_LOCAL: {
+      const int nc = what == FMM_EXPORT_MULTIPOLE ? 4 : 6;
+      if (!need(sizeof(double) * C * nc * m)) return FMM_EINVAL;
+      const size_t cnt = (size_t)(C + 1) * nc * m;
+      std::vector<double> buf(cnt);
+      const size_t off = what == FMM_EXPORT_MULTIPOLE ? L.mpole : L.local;
+      if (f32) {
+        std::vector<float> tmp(cnt);
+        FMM_CUDA_TRY(cudaMemcpy(tmp.data(), P->ws + off, 4 * cnt, cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < cnt; ++e) buf[e] = tmp[e];
+      } else {
+        FMM_CUDA_TRY(cudaMemcpy(buf.data(), P->ws + off, 8 * cnt, cudaMemcpyDeviceToHost));
+      }
+      const double mu = P->munit, g = P->gbar, il2 = 1.0 / (P->lunit * P->lunit);
+      double sc[6];
+      if (nc == 4) {
+        sc[0] = mu; sc[1] = g * mu; sc[2] = g * mu; sc[3] = mu;
+      } else {
+        sc[0] = mu * il2; sc[1] = mu * il2; sc[2] = mu * il2 / g;
+        sc[3] = mu * il2; sc[4] = mu * il2; sc[5] = mu * il2 * g;
+      }
+      double* o = static_cast<double*>(host);
+      for (int64_t i = 1; i <= C; ++i)
+        for (int c = 0; c < nc; ++c)
+          for (int64_t v = 0; v < m; ++v)
+            o[((i - 1) * nc + c) * m + v] = sc[c] * buf[((size_t)i * nc + c) * m + v];
+      return FMM_OK;
+    }
+    default:
+      return FMM_EINVAL;
+  }
+}
+
+void fmm_plan_destroy(fmm_plan_t P) {
+  if (!P) return;
+  if (P->ev_made)
+    for (auto& e : P->ev) cudaEventDestroy(e);
+  delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Device-wide exclusive scan and stable LSD radix sort (64-bit keys).
+//
+// Used by the tree build (one presort of the particles along each axis, so
+// that equal coordinates stay in input-index order, which is the tie rule of
+// the median split) and by the traversal (interaction lists sorted by
+// (target, source), which groups every target's pairs as Section 10 asks and
+// makes the lists deterministic).
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kSortWarps = kSortThreads / 32;
+
+// Exclusive prefix of `v` over the block (blocked arrangement); returns the
+// block total through `total`.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_tot[lane] = wi - w;  // exclusive warp offsets
+    if (lane == nw - 1) warp_tot[32] = wi;
+  }
+  __syncthreads();
+  uint32_t res = warp_tot[warp] + inc - v;
+  total = warp_tot[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_chunk_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wt[33];
+  int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s += (base + k < n) ? in[base + k] : 0u;
+  uint32_t tot;
+  block_exclusive_scan(s, wt, tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// In-place safe: every thread reads its items before the block-wide scan.
+__global__ void k_chunk_scan(const uint32_t* in, int64_t n, uint32_t* out,
+                             const uint32_t* __restrict__ offsets) {
+  __shared__ uint32_t wt[33];
+  int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(s, wt, tot) + (offsets ? offsets[blockIdx.x] : 0u);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* __restrict__ keys,
+                                                               int64_t n, int shift, int64_t ntiles,
+                                                               uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    bool valid = i < n;
+    unsigned d = valid ? (unsigned)((keys[i] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
+    int64_t ntiles, const uint32_t* __restrict__ hist, uint64_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out) {
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t gbase[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
+  run[threadIdx.x] = 0;
+  gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    bool valid = i < n;
+    uint64_t key = valid ? keys[i] : 0ull;
+    uint32_t val = (valid && vals) ? vals[i] : 0u;
+    unsigned d = valid ? (unsigned)((key >> shift) & 0xffu) : 0x100u + lane;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    unsigned wr = __popc(peers & lanemask_lt());
+    if (valid && wr == 0u) wcnt[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pre = run[d];
+      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
+      uint32_t pos = gbase[d] + pre + wr;
+      keys_out[pos] = key;
+      if (vals) vals_out[pos] = val;
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+      tot += wcnt[w][threadIdx.x];
+      wcnt[w][threadIdx.x] = 0;
+    }
+    run[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int64_t scan_tmp_words(int64_t n) {
+  int64_t nc = div_up(n, kScanChunk);
+  if (nc <= 1) return 1;
+  return nc + scan_tmp_words(nc);
+}
+
+int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s) {
+  if (n <= 0) return FMM_OK;
+  int64_t nc = div_up(n, kScanChunk);
+  if (nc == 1) {
+    k_chunk_scan<<<1, kScanThreads, 0, s>>>(in, n, out, nullptr);
+    FMM_LAUNCH_CHECK();
+    return FMM_OK;
+  }
+  k_chunk_sums<<<(unsigned)nc, kScanThreads, 0, s>>>(in, n, tmp);
+  FMM_LAUNCH_CHECK();
+  int rc = scan_exclusive(tmp, tmp, nc, tmp + nc, s);
+  if (rc != FMM_OK) return rc;
+  k_chunk_scan<<<(unsigned)nc, kScanThreads, 0, s>>>(in, n, out, tmp);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+int64_t radix_tiles(int64_t n) { return div_up(n > 0 ? n : 1, kSortTile); }
+
+int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
+               int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
+               cudaStream_t s, bool* in_alt) {
+  *in_alt = false;
+  if (n <= 1) return FMM_OK;
+  int64_t nt = radix_tiles(n);
+  if (nt > max_tiles) return FMM_EINVAL;
+  uint64_t* k_in = keys;
+  uint64_t* k_out = keys_alt;
+  uint32_t* v_in = vals;
+  uint32_t* v_out = vals_alt;
+  bool alt = false;
+  for (int b = begin_bit; b < end_bit; b += 8) {
+    k_radix_upsweep<<<(unsigned)nt, kSortThreads, 0, s>>>(k_in, n, b, nt, hist);
+    FMM_LAUNCH_CHECK();
+    int rc = scan_exclusive(hist, hist, 256 * nt, scan_tmp, s);
+    if (rc != FMM_OK) return rc;
+    k_radix_downsweep<<<(unsigned)nt, kSortThreads, 0, s>>>(k_in, v_in, n, b, nt, hist, k_out, v_out);
+    FMM_LAUNCH_CHECK();
+    uint64_t* tk = k_in; k_in = k_out; k_out = tk;
+    uint32_t* tv = v_in; v_in = v_out; v_out = tv;
+    alt = !alt;
+  }
+  *in_alt = alt;
+  return FMM_OK;
+}
+
+}  // namespace fmm

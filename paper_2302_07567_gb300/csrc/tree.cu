@@ -1,0 +1,363 @@
+// Setup and cluster tree (Section 3 averages; Algs. 1-2; Appendix B; Section 8).
+//
+// gbar: the mean momentum is summed by the adjacent-pair binary tree over
+// 2^ceil(log2 N) zero-padded terms, so gbar is the same to the last bit
+// whatever the launch shape, and the tree and traversal decisions that depend
+// on it are reproducible.
+//
+// Tree: the particles are sorted once along each axis by (coordinate, input
+// index).  Three index arrays A_x, A_y, A_z are kept, each holding every
+// node's members as a contiguous slot range sorted along its own axis.  For a
+// node the bounding box of Section 2 is then read off the end slots of the
+// three arrays, the split axis of Alg. 1 is argmax_k s_k (b_k - a_k), and the
+// median of Appendix B is the element at slot first + ceil(|S|/2) - 1 of the
+// split axis' array.  Each array is then stably partitioned inside every
+// node by "rank along the split axis <= rank of the median", which keeps all
+// three arrays sorted inside the children.  Node slot ranges depend only on
+// N and N0 (balanced halving, ceil to the first child), so they are tables
+// computed when the plan is created.
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedItems = 8;
+constexpr int kRedChunk = kRedThreads * kRedItems;  // 2048 = 2^11
+
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 8;
+constexpr int kPartChunk = kPartThreads * kPartItems;
+
+// Adjacent-pair (binary tree) sum of the aligned chunk of 2048 terms
+// in[chunk*2048 ...], stride `stride`, zero beyond n.  Writes out[chunk].
+__global__ void __launch_bounds__(kRedThreads) k_pairwise(const double* __restrict__ in, int64_t n,
+                                                         int64_t stride, double* __restrict__ out) {
+  __shared__ double wsum[kRedThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kRedChunk + (int64_t)threadIdx.x * kRedItems;
+  double e[kRedItems];
+#pragma unroll
+  for (int k = 0; k < kRedItems; ++k) e[k] = (base + k < n) ? in[(base + k) * stride] : 0.0;
+  double v = __dadd_rn(__dadd_rn(__dadd_rn(e[0], e[1]), __dadd_rn(e[2], e[3])),
+                       __dadd_rn(__dadd_rn(e[4], e[5]), __dadd_rn(e[6], e[7])));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = __dadd_rn(__dadd_rn(__dadd_rn(wsum[0], wsum[1]), __dadd_rn(wsum[2], wsum[3])),
+                         __dadd_rn(__dadd_rn(wsum[4], wsum[5]), __dadd_rn(wsum[6], wsum[7])));
+    out[blockIdx.x] = a;
+  }
+}
+
+// max |q| per chunk, and non-finite inputs flagged.
+__global__ void k_check_inputs(const double* __restrict__ x, const double* __restrict__ p,
+                               const double* __restrict__ q, int64_t N, double* __restrict__ qmax,
+                               Counters* cnt) {
+  __shared__ double wmax[kRedThreads / 32];
+  double m = 0.0;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a = fabs(q[i]);
+    bad |= !isfinite(q[i]);
+    m = fmax(m, a);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bad |= !isfinite(x[3 * i + k]) || !isfinite(p[3 * i + k]);
+  }
+  if (bad) atomicOr(&cnt->err, kErrNonFinite);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, wmax[w]);
+    qmax[blockIdx.x] = r;
+  }
+}
+
+// scal[0] = gbar, scal[1] = mass unit mu (power of two near max|q|).
+__global__ void k_gbar(const double* __restrict__ sx, const double* __restrict__ sy,
+                       const double* __restrict__ sz, int64_t N, const double* __restrict__ qmax,
+                       int nq, double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double dn = (double)N;
+  double px = __ddiv_rn(sx[0], dn), py = __ddiv_rn(sy[0], dn), pz = __ddiv_rn(sz[0], dn);
+  double pp = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+  scal[0] = __dsqrt_rn(__dadd_rn(1.0, pp));
+  double m = 0.0;
+  for (int i = 0; i < nq; ++i) m = fmax(m, qmax[i]);
+  scal[1] = (m > 0.0 && isfinite(m)) ? ldexp(1.0, (int)rint(log2(m))) : 1.0;
+}
+
+// Order-preserving 64-bit key of a double; -0 is folded onto +0.
+__device__ __forceinline__ uint64_t dkey(double v) {
+  if (v == 0.0) v = 0.0;
+  uint64_t u = (uint64_t)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void k_make_keys(const double* __restrict__ x, int64_t N, int axis,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = dkey(x[3 * i + axis]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_store_axis(const uint32_t* __restrict__ sorted, int64_t N, int32_t* __restrict__ A,
+                             int32_t* __restrict__ rank) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = sorted[i];
+    A[i] = (int32_t)v;
+    rank[v] = (int32_t)i;
+  }
+}
+
+// Boxes of the nodes of one level; for inner levels also the split axis
+// (Alg. 1) and the rank of the median element (Appendix B).
+__global__ void k_node_split(const double* __restrict__ x, const int32_t* __restrict__ A,
+                             const int32_t* __restrict__ rank, int64_t N, const int64_t* __restrict__ nstart,
+                             const int64_t* __restrict__ ncount, int level, int kappa,
+                             const double* __restrict__ scal, double* __restrict__ nlo,
+                             double* __restrict__ nhi, int32_t* __restrict__ naxis,
+                             int32_t* __restrict__ nmed) {
+  const int64_t first = (int64_t)1 << level;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= first) return;
+  const int64_t i = first + t;
+  const int64_t st = nstart[i], c = ncount[i];
+  const double s[3] = {1.0, 1.0, scal[0]};
+  double w[3];
+  for (int k = 0; k < 3; ++k) {
+    double lo = x[3 * (int64_t)A[k * N + st] + k];
+    double hi = x[3 * (int64_t)A[k * N + st + c - 1] + k];
+    nlo[3 * i + k] = lo;
+    nhi[3 * i + k] = hi;
+    w[k] = __dmul_rn(s[k], __dsub_rn(hi, lo));
+  }
+  if (level == kappa) {
+    naxis[i] = -1;
+    nmed[i] = -1;
+    return;
+  }
+  int ax = 0;
+  if (w[1] > w[ax]) ax = 1;
+  if (w[2] > w[ax]) ax = 2;
+  const int64_t h1 = (c + 1) / 2;
+  naxis[i] = ax;
+  nmed[i] = rank[ax * N + A[ax * N + st + h1 - 1]];
+}
+
+__device__ __forceinline__ bool part_flag(const int32_t* __restrict__ Ak, const int32_t* __restrict__ rank,
+                                          int64_t N, int64_t pos, int64_t node,
+                                          const int32_t* __restrict__ naxis,
+                                          const int32_t* __restrict__ nmed) {
+  const int ax = naxis[node];
+  return rank[ax * N + Ak[pos]] <= nmed[node];
+}
+
+// Per-chunk count of elements going to the first child (grid.y = array k).
+__global__ void __launch_bounds__(kPartThreads) k_part_count(
+    const int32_t* __restrict__ A, const int32_t* __restrict__ rank, int64_t N,
+    const int64_t* __restrict__ nstart, int level, const int32_t* __restrict__ naxis,
+    const int32_t* __restrict__ nmed, int64_t nblk, uint32_t* __restrict__ bsum) {
+  __shared__ uint32_t red[kPartThreads / 32];
+  const int k = blockIdx.y;
+  const int32_t* Ak = A + (int64_t)k * N;
+  const int64_t first = (int64_t)1 << level;
+  const int64_t base = (int64_t)blockIdx.x * kPartChunk + (int64_t)threadIdx.x * kPartItems;
+  uint32_t c = 0;
+  int64_t node = -1, node_end = -1;
+  for (int j = 0; j < kPartItems; ++j) {
+    int64_t pos = base + j;
+    if (pos >= N) break;
+    if (pos >= node_end) {
+      node = find_node(nstart, first, first, pos);
+      node_end = (node + 1 < 2 * first) ? nstart[node + 1] : N;
+    }
+    c += part_flag(Ak, rank, N, pos, node, naxis, nmed) ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kPartThreads / 32; ++w) t += red[w];
+    bsum[(int64_t)k * nblk + blockIdx.x] = t;
+  }
+}
+
+// Stable partition of every node's slot range (grid.y = array k).
+__global__ void __launch_bounds__(kPartThreads) k_part_scatter(
+    const int32_t* __restrict__ A, const int32_t* __restrict__ rank, int64_t N,
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount,
+    const int64_t* __restrict__ nleftpre, int level, const int32_t* __restrict__ naxis,
+    const int32_t* __restrict__ nmed, int64_t nblk, const uint32_t* __restrict__ bscan,
+    int32_t* __restrict__ Aout) {
+  __shared__ uint32_t wt[33];
+  const int k = blockIdx.y;
+  const int32_t* Ak = A + (int64_t)k * N;
+  int32_t* Ok = Aout + (int64_t)k * N;
+  const int64_t first = (int64_t)1 << level;
+  const int64_t base = (int64_t)blockIdx.x * kPartChunk + (int64_t)threadIdx.x * kPartItems;
+  bool f[kPartItems];
+  int64_t nd[kPartItems];
+  uint32_t c = 0;
+  int64_t node = -1, node_end = -1;
+  for (int j = 0; j < kPartItems; ++j) {
+    int64_t pos = base + j;
+    f[j] = false;
+    nd[j] = -1;
+    if (pos >= N) continue;
+    if (pos >= node_end) {
+      node = find_node(nstart, first, first, pos);
+      node_end = (node + 1 < 2 * first) ? nstart[node + 1] : N;
+    }
+    nd[j] = node;
+    f[j] = part_flag(Ak, rank, N, pos, node, naxis, nmed);
+    c += f[j] ? 1u : 0u;
+  }
+  uint32_t tot;
+  // this function has __syncthreads inside; every thread reaches it
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wt[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = kPartThreads / 32;
+    uint32_t w = lane < nw ? wt[lane] : 0u, wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) wt[lane] = wi - w;
+    if (lane == nw - 1) wt[32] = wi;
+  }
+  __syncthreads();
+  tot = wt[32];
+  (void)tot;
+  int64_t P = (int64_t)bscan[(int64_t)k * nblk + blockIdx.x] + wt[warp] + (inc - c);
+  for (int j = 0; j < kPartItems; ++j) {
+    int64_t pos = base + j;
+    if (pos >= N) break;
+    const int64_t n0 = nd[j];
+    const int64_t st = nstart[n0], cnt = ncount[n0], h1 = (cnt + 1) / 2;
+    const int64_t lb = P - nleftpre[n0];  // first-child elements before pos inside the node
+    const int64_t dst = f[j] ? st + lb : st + h1 + ((pos - st) - lb);
+    Ok[dst] = Ak[pos];
+    P += f[j] ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const int64_t N = P->N;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  double* scal = ws_ptr<double>(P, L.scal);
+  FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(Counters), s));
+  const int nq = (int)std::min<int64_t>(1024, div_up(N, kRedThreads));
+  double* qmax = ws_ptr<double>(P, L.qmax_part);
+  k_check_inputs<<<nq, kRedThreads, 0, s>>>(x, p, q, N, qmax, cnt);
+  FMM_LAUNCH_CHECK();
+  // pairwise momentum sums: three arrays of partials, reduced level by level
+  double* part = ws_ptr<double>(P, L.psum_part);
+  const int64_t np0 = div_up(N, kRedChunk);
+  const double* res[3];
+  for (int k = 0; k < 3; ++k) {
+    double* a = part + (size_t)k * 2 * (np0 + 2);
+    double* b = a + (np0 + 2);
+    int64_t n = N;
+    const double* src = p + k;
+    int64_t stride = 3;
+    double* dst = a;
+    do {
+      int64_t nb = div_up(n, kRedChunk);
+      k_pairwise<<<(unsigned)nb, kRedThreads, 0, s>>>(src, n, stride, dst);
+      FMM_LAUNCH_CHECK();
+      n = nb;
+      src = dst;
+      stride = 1;
+      dst = (dst == a) ? b : a;
+    } while (n > 1);
+    res[k] = src;
+  }
+  k_gbar<<<1, 32, 0, s>>>(res[0], res[1], res[2], N, qmax, nq, scal);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const int64_t N = P->N;
+  uint64_t* keys = ws_ptr<uint64_t>(P, L.keys);
+  uint64_t* keys_alt = ws_ptr<uint64_t>(P, L.keys_alt);
+  uint32_t* vals = ws_ptr<uint32_t>(P, L.vals);
+  uint32_t* vals_alt = ws_ptr<uint32_t>(P, L.vals_alt);
+  uint32_t* hist = ws_ptr<uint32_t>(P, L.hist);
+  uint32_t* stmp = ws_ptr<uint32_t>(P, L.scan_tmp);
+  int32_t* A = ws_ptr<int32_t>(P, L.A);
+  int32_t* Aalt = ws_ptr<int32_t>(P, L.A_alt);
+  int32_t* rank = ws_ptr<int32_t>(P, L.rank);
+  const double* scal = ws_ptr<double>(P, L.scal);
+  const int64_t* nstart = ws_ptr<int64_t>(P, L.nstart);
+  const int64_t* ncount = ws_ptr<int64_t>(P, L.ncount);
+  const int64_t* nleftpre = ws_ptr<int64_t>(P, L.nleftpre);
+  double* nlo = ws_ptr<double>(P, L.nlo);
+  double* nhi = ws_ptr<double>(P, L.nhi);
+  int32_t* naxis = ws_ptr<int32_t>(P, L.naxis);
+  int32_t* nmed = ws_ptr<int32_t>(P, L.nmed);
+  const int gs = (int)std::min<int64_t>(4096, div_up(N, 256));
+
+  for (int k = 0; k < 3; ++k) {
+    k_make_keys<<<gs, 256, 0, s>>>(x, N, k, keys, vals);
+    FMM_LAUNCH_CHECK();
+    bool alt = false;
+    int rc = radix_sort(keys, keys_alt, vals, vals_alt, N, 0, 64, hist, stmp, (int64_t)L.nblk_sort, s, &alt);
+    if (rc != FMM_OK) return rc;
+    k_store_axis<<<gs, 256, 0, s>>>(alt ? vals_alt : vals, N, A + (int64_t)k * N, rank + (int64_t)k * N);
+    FMM_LAUNCH_CHECK();
+  }
+
+  const int64_t nblk = div_up(N, kPartChunk);
+  uint32_t* bsum = ws_ptr<uint32_t>(P, L.blocksum);
+  int32_t* cur = A;
+  int32_t* nxt = Aalt;
+  for (int l = 0; l <= P->kappa; ++l) {
+    const int64_t nodes = (int64_t)1 << l;
+    k_node_split<<<(unsigned)div_up(nodes, 128), 128, 0, s>>>(x, cur, rank, N, nstart, ncount, l, P->kappa,
+                                                             scal, nlo, nhi, naxis, nmed);
+    FMM_LAUNCH_CHECK();
+    if (l == P->kappa) break;
+    dim3 g((unsigned)nblk, 3);
+    k_part_count<<<g, kPartThreads, 0, s>>>(cur, rank, N, nstart, l, naxis, nmed, nblk, bsum);
+    FMM_LAUNCH_CHECK();
+    for (int k = 0; k < 3; ++k) {
+      int rc = scan_exclusive(bsum + k * nblk, bsum + k * nblk, nblk, stmp, s);
+      if (rc != FMM_OK) return rc;
+    }
+    k_part_scatter<<<g, kPartThreads, 0, s>>>(cur, rank, N, nstart, ncount, nleftpre, l, naxis, nmed, nblk,
+                                              bsum, nxt);
+    FMM_LAUNCH_CHECK();
+    int32_t* t = cur; cur = nxt; nxt = t;
+  }
+  // leaf order: the x-array's slot order (members of each leaf sorted by x)
+  FMM_CUDA_TRY(cudaMemcpyAsync(ws_ptr<int32_t>(P, L.perm), cur, sizeof(int32_t) * N,
+                               cudaMemcpyDeviceToDevice, s));
+  return FMM_OK;
+}
+
+}  // namespace fmm

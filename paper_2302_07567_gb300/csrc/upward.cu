@@ -1,0 +1,406 @@
+// Node geometry, particle preparation, upward pass (P2M Alg. 3, M2M Alg. 4 /
+// Eq. 2.7, Alg. 5) and the separable transfer that also serves L2L (Alg. 13 /
+// Eq. 2.9).
+//
+// The interpolation points of a box side [a, b] are xi_k = c + h t_k with
+// t_k the Chebyshev points of the second kind; the Lagrange basis is
+// evaluated in the barycentric form in the normalised variable t = (x - c)/h.
+// A side of zero width carries the basis l_0 = 1.  The transfer matrices
+// T_d[nu][nu'] = l^d_{parent, nu}(xi^d_{child, nu'}) are formed in FP64 and
+// applied one axis at a time, (n+1)^4 multiply-adds per axis and component.
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+// scal[2] = ell, scal[3] = 1/ell (powers of two near the root box's stretched
+// half-diagonal), scal[4] = (1/(4 pi eps0)) mu / ell^2, scal[5] = scal[4] / c0.
+__global__ void k_units(const double* __restrict__ nlo, const double* __restrict__ nhi,
+                        double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double s[3] = {1.0, 1.0, scal[0]};
+  double r2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double v = s[k] * ((nhi[3 + k] - nlo[3 + k]) * 0.5);
+    r2 += v * v;
+  }
+  double r = sqrt(r2);
+  int e = (r > 0.0 && isfinite(r)) ? (int)ceil(log2(r)) : 0;
+  double ell = ldexp(1.0, e);
+  double inv = ldexp(1.0, -e);
+  scal[2] = ell;
+  scal[3] = inv;
+  const double ke = 1.0 / (4.0 * 3.14159265358979323846 * kEps0);
+  scal[4] = ke * scal[1] * inv * inv;
+  scal[5] = scal[4] / kC0;
+}
+
+// Centres and stretched half-diagonals (Algs. 6-7, FP64, fixed operation
+// order, no contraction) for the traversal, plus the scaled geometry.
+__global__ void k_node_geo(const double* __restrict__ nlo, const double* __restrict__ nhi, int64_t C,
+                           const double* __restrict__ scal, double* __restrict__ ncen,
+                           double* __restrict__ ndiam, NodeGeo* __restrict__ geo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (i > C) return;
+  const double s[3] = {1.0, 1.0, scal[0]};
+  const double inv = scal[3];
+  double v[3];
+  NodeGeo g;
+  for (int k = 0; k < 3; ++k) {
+    const double lo = nlo[3 * i + k], hi = nhi[3 * i + k];
+    const double c = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    ncen[3 * i + k] = c;
+    v[k] = __dmul_rn(s[k], __dmul_rn(__dsub_rn(lo, hi), 0.5));
+    g.c[k] = __dmul_rn(__dmul_rn(s[k], c), inv);
+    g.h[k] = __dmul_rn(__dmul_rn(s[k], __dmul_rn(__dsub_rn(hi, lo), 0.5)), inv);
+  }
+  ndiam[i] = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
+                                  __dmul_rn(v[2], v[2])));
+  geo[i] = g;
+}
+
+// Particles in leaf order: position relative to the leaf centre in stretched,
+// scaled coordinates with the scaled mass a' (px), and the scaled momentum
+// moment b~' (pb).  The offset from the centre is taken in physical
+// coordinates first, s o (x - c) / ell, so that a narrow box far from the
+// origin keeps its relative precision.
+template <typename T>
+__global__ void k_prep(const double* __restrict__ x, const double* __restrict__ p,
+                       const double* __restrict__ q, int64_t N, const int32_t* __restrict__ perm,
+                       const int64_t* __restrict__ nstart, int kappa, const double* __restrict__ ncen,
+                       const double* __restrict__ scal, typename Vec4<T>::type* __restrict__ px,
+                       typename Vec4<T>::type* __restrict__ pb, typename Vec4<T>::type* __restrict__ pl) {
+  const int64_t first = (int64_t)1 << kappa;
+  const double gbar = scal[0], imu = 1.0 / scal[1], inv = scal[3];
+  for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < N;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = find_node(nstart, first, first, pos);
+    const int64_t i = perm[pos];
+    const double* c = ncen + 3 * leaf;
+    const double xs = (x[3 * i] - c[0]) * inv;
+    const double ys = (x[3 * i + 1] - c[1]) * inv;
+    const double zs = (gbar * (x[3 * i + 2] - c[2])) * inv;
+    const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2], qi = q[i];
+    const double gam = sqrt(1.0 + ((p0 * p0 + p1 * p1) + p2 * p2));
+    typename Vec4<T>::type u, w;
+    u.x = (T)xs; u.y = (T)ys; u.z = (T)zs; u.w = (T)(qi * gam * imu);
+    typename Vec4<T>::type lo;
+    if (sizeof(T) == 4) {  // FP32: the rounding remainders, x = hi + lo to ~2^-48
+      lo.x = (T)(xs - (double)u.x); lo.y = (T)(ys - (double)u.y); lo.z = (T)(zs - (double)u.z);
+    } else {               // FP64: the absolute physical position, for P2P
+      lo.x = (T)x[3 * i]; lo.y = (T)x[3 * i + 1]; lo.z = (T)x[3 * i + 2];
+    }
+    lo.w = (T)0;
+    pl[pos] = lo;
+    w.x = (T)((qi * p0) / gbar * imu);
+    w.y = (T)((qi * p1) / gbar * imu);
+    w.z = (T)(qi * p2 * imu);
+    w.w = (T)0;
+    px[pos] = u;
+    pb[pos] = w;
+  }
+}
+
+// P2M (Alg. 3): one block per leaf, thread per (proxy point, up to NV of them).
+// Multipoles M[node][c][nu], c = (a, b~x, b~y, b~z).
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __restrict__ px,
+                                             const typename Vec4<T>::type* __restrict__ pb,
+                                             const int64_t* __restrict__ nstart,
+                                             const int64_t* __restrict__ ncount, int kappa,
+                                             const NodeGeo* __restrict__ geo, Cheb ch, int m,
+                                             T* __restrict__ M) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int np1 = ch.np1;
+  const int stride = 3 * np1 + 4;
+  const int64_t leaf = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[leaf], cnt = ncount[leaf];
+  const NodeGeo g = geo[leaf];
+  T invh[3];
+  bool deg[3];
+  for (int k = 0; k < 3; ++k) {
+    deg[k] = !(g.h[k] > 0.0);
+    invh[k] = deg[k] ? T(0) : (T)(1.0 / g.h[k]);
+  }
+  T acc[NV][4], cmp[NV][4];
+  int nu1[NV], nu2[NV], nu3[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int nu = threadIdx.x + v * blockDim.x;
+    nu1[v] = nu % np1;
+    nu2[v] = (nu / np1) % np1;
+    nu3[v] = nu / (np1 * np1);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[v][c] = cmp[v][c] = T(0);
+  }
+  for (int64_t base = 0; base < cnt; base += blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    T* row = sm + (size_t)threadIdx.x * stride;
+    if (j < cnt) {
+      const typename Vec4<T>::type u = px[st + j], w = pb[st + j];
+      const T rel[3] = {u.x, u.y, u.z};
+      for (int k = 0; k < 3; ++k) bary_basis<T>(rel[k] * invh[k], deg[k], ch, row + k * np1);
+      row[3 * np1 + 0] = u.w;
+      row[3 * np1 + 1] = w.x;
+      row[3 * np1 + 2] = w.y;
+      row[3 * np1 + 3] = w.z;
+    }
+    __syncthreads();
+    const int nj = (int)min64(blockDim.x, cnt - base);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int nu = threadIdx.x + v * blockDim.x;
+      if (nu >= m) continue;
+      for (int j0 = 0; j0 < nj; j0 += 32) {
+        T part[4] = {T(0), T(0), T(0), T(0)};
+        const int j1 = min(nj, j0 + 32);
+        for (int jj = j0; jj < j1; ++jj) {
+          const T* r = sm + (size_t)jj * stride;
+          const T wgt = r[nu1[v]] * r[np1 + nu2[v]] * r[2 * np1 + nu3[v]];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) part[c] += wgt * r[3 * np1 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) kahan_add(acc[v][c], cmp[v][c], part[c]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int nu = threadIdx.x + v * blockDim.x;
+    if (nu >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) M[((size_t)leaf * 4 + c) * m + nu] = acc[v][c];
+  }
+}
+
+// out[a,b,c] = sum_{a',b',c'} Mx[a][a'] My[b][b'] Mz[c][c'] in[a',b',c'] (x fastest),
+// matrices stored row-major [np1][np1] in shared memory.
+template <typename T>
+__device__ void apply3(const T* Mx, const T* My, const T* Mz, const T* in, T* tmp1, T* tmp2,
+                       T* out, int np1, int m, bool accumulate) {
+  for (int o = threadIdx.x; o < m; o += blockDim.x) {
+    const int a = o % np1, r = o / np1;
+    T s = T(0);
+    for (int k = 0; k < np1; ++k) s += Mx[a * np1 + k] * in[r * np1 + k];
+    tmp1[o] = s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < m; o += blockDim.x) {
+    const int a = o % np1, b = (o / np1) % np1, c = o / (np1 * np1);
+    T s = T(0);
+    for (int k = 0; k < np1; ++k) s += My[b * np1 + k] * tmp1[(c * np1 + k) * np1 + a];
+    tmp2[o] = s;
+  }
+  __syncthreads();
+  const int pl = np1 * np1;
+  for (int o = threadIdx.x; o < m; o += blockDim.x) {
+    const int ab = o % pl, c = o / pl;
+    T s = T(0);
+    for (int k = 0; k < np1; ++k) s += Mz[c * np1 + k] * tmp2[k * pl + ab];
+    out[o] = accumulate ? out[o] + s : s;
+  }
+  __syncthreads();
+}
+
+// Transfer between a parent at `level` and its two children, NC components.
+// UP (M2M, Eq. 2.7):   parent[nu]  = sum_children sum_nu' T[nu][nu'] child[nu']
+// DOWN (L2L, Eq. 2.9): child[mu'] += sum_mu T[mu][mu'] parent[mu]
+// with T = T_x (x) T_y (x) T_z, T_d[nu][nu'] = l^d_{parent,nu}(xi^d_{child,nu'}),
+// formed in FP64 from the physical boxes: xi = c + h t_k, t = (xi - c_p) / h_p.
+template <typename T, int NC, bool UP>
+__global__ void k_transfer(int level, const double* __restrict__ nlo, const double* __restrict__ nhi, Cheb ch,
+                           int m, T* __restrict__ buf) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int np1 = ch.np1, q = np1 * np1;
+  T* mat = sm;                 // [2 children][3 axes][np1][np1], stored as used by apply3
+  T* in = mat + 6 * q;
+  T* t1 = in + m;
+  T* t2 = t1 + m;
+  T* acc = t2 + m;
+  const int64_t parent = ((int64_t)1 << level) + blockIdx.x;
+  for (int job = threadIdx.x; job < 6 * np1; job += blockDim.x) {
+    const int child = job / (3 * np1), d = (job / np1) % 3, nup = job % np1;
+    const int64_t cn = 2 * parent + child;
+    const double clo = nlo[3 * cn + d], chi = nhi[3 * cn + d];
+    const double plo = nlo[3 * parent + d], phi = nhi[3 * parent + d];
+    const double xc = chi > clo ? (clo + chi) / 2.0 + ((chi - clo) / 2.0) * ch.t[nup] : clo;
+    const bool deg = !(phi > plo);
+    const double t = deg ? 0.0 : (xc - (plo + phi) / 2.0) / ((phi - plo) / 2.0);
+    double b[kMaxNp1];
+    bary_basis<double>(t, deg, ch, b);
+    T* Md = mat + (child * 3 + d) * q;
+    for (int nu = 0; nu < np1; ++nu) {
+      // UP contracts over nu' (second index); DOWN over nu: store the transpose
+      if (UP) Md[nu * np1 + nup] = (T)b[nu];
+      else Md[nup * np1 + nu] = (T)b[nu];
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < NC; ++c) {
+    for (int child = 0; child < 2; ++child) {
+      const int64_t cn = 2 * parent + child;
+      const T* src = buf + ((size_t)(UP ? cn : parent) * NC + c) * m;
+      for (int o = threadIdx.x; o < m; o += blockDim.x) in[o] = src[o];
+      __syncthreads();
+      const T* Mx = mat + (child * 3 + 0) * q;
+      const T* My = mat + (child * 3 + 1) * q;
+      const T* Mz = mat + (child * 3 + 2) * q;
+      if (UP) {
+        apply3<T>(Mx, My, Mz, in, t1, t2, acc, np1, m, child == 1);
+      } else {
+        T* dst = buf + ((size_t)cn * NC + c) * m;
+        apply3<T>(Mx, My, Mz, in, t1, t2, acc, np1, m, false);
+        for (int o = threadIdx.x; o < m; o += blockDim.x) dst[o] += acc[o];
+        __syncthreads();
+      }
+    }
+    if (UP) {
+      T* dst = buf + ((size_t)parent * NC + c) * m;
+      for (int o = threadIdx.x; o < m; o += blockDim.x) dst[o] = acc[o];
+      __syncthreads();
+    }
+  }
+}
+
+// M2L source table: per node and proxy point, (Y, a) and (b~, 0) with
+// Y = h o t_nu the point's offset from the box centre.
+template <typename T>
+__global__ void k_srctab(const T* __restrict__ M, const NodeGeo* __restrict__ geo, int64_t C, Cheb ch,
+                         int m, typename Vec4<T>::type* __restrict__ src) {
+  const int64_t total = (C + 1) * (int64_t)m;
+  const int np1 = ch.np1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = e / m;
+    const int nu = (int)(e % m);
+    if (node == 0) continue;
+    const NodeGeo g = geo[node];
+    const int n1 = nu % np1, n2 = (nu / np1) % np1, n3 = nu / (np1 * np1);
+    typename Vec4<T>::type u, w;
+    u.x = (T)(g.h[0] * ch.t[n1]);
+    u.y = (T)(g.h[1] * ch.t[n2]);
+    u.z = (T)(g.h[2] * ch.t[n3]);
+    u.w = M[((size_t)node * 4 + 0) * m + nu];
+    w.x = M[((size_t)node * 4 + 1) * m + nu];
+    w.y = M[((size_t)node * 4 + 2) * m + nu];
+    w.z = M[((size_t)node * 4 + 3) * m + nu];
+    w.w = T(0);
+    src[2 * e] = u;
+    src[2 * e + 1] = w;
+  }
+}
+
+template <typename T, int NV>
+int launch_p2m(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const size_t smem = (size_t)256 * (3 * P->np1 + 4) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m<T, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  k_p2m<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(
+      ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb),
+      ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
+      P->cheb, P->m, ws_ptr<T>(P, L.mpole));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int upward_t(fmm_plan_s* P, cudaStream_t s) {
+  const int nv = (int)div_up(P->m, 256);
+  int rc;
+  switch (nv) {
+    case 1: rc = launch_p2m<T, 1>(P, s); break;
+    case 2: rc = launch_p2m<T, 2>(P, s); break;
+    case 3: rc = launch_p2m<T, 3>(P, s); break;
+    case 4: rc = launch_p2m<T, 4>(P, s); break;
+    case 5: rc = launch_p2m<T, 5>(P, s); break;
+    case 6: rc = launch_p2m<T, 6>(P, s); break;
+    case 7: rc = launch_p2m<T, 7>(P, s); break;
+    case 8: rc = launch_p2m<T, 8>(P, s); break;
+    default: rc = launch_p2m<T, 9>(P, s); break;
+  }
+  if (rc != FMM_OK) return rc;
+  const Layout& L = P->lay;
+  for (int l = P->kappa - 1; l >= 0; --l) {
+    rc = launch_transfer<T, 4, true>(P, l, ws_ptr<T>(P, L.mpole), s);
+    if (rc != FMM_OK) return rc;
+  }
+  const int64_t total = (P->C + 1) * (int64_t)P->m;
+  k_srctab<T><<<(unsigned)std::min<int64_t>(div_up(total, 256), 8192), 256, 0, s>>>(
+      ws_ptr<T>(P, L.mpole), ws_ptr<NodeGeo>(P, L.ngeo), P->C, P->cheb, P->m,
+      ws_ptr<typename Vec4<T>::type>(P, L.srct));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+}  // namespace
+
+template <typename T, int NC, bool UP>
+int launch_transfer(fmm_plan_s* P, int level, T* buf, cudaStream_t s) {
+  const size_t smem = (size_t)(6 * P->np1 * P->np1 + 4 * P->m) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_transfer<T, NC, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+    attr_set = true;
+  }
+  k_transfer<T, NC, UP><<<(unsigned)(1u << level), 256, smem, s>>>(
+      level, ws_ptr<double>(P, P->lay.nlo), ws_ptr<double>(P, P->lay.nhi), P->cheb, P->m, buf);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template int launch_transfer<float, 4, true>(fmm_plan_s*, int, float*, cudaStream_t);
+template int launch_transfer<double, 4, true>(fmm_plan_s*, int, double*, cudaStream_t);
+template int launch_transfer<float, 6, false>(fmm_plan_s*, int, float*, cudaStream_t);
+template int launch_transfer<double, 6, false>(fmm_plan_s*, int, double*, cudaStream_t);
+template int launch_transfer<float, 6, true>(fmm_plan_s*, int, float*, cudaStream_t);
+template int launch_transfer<double, 6, true>(fmm_plan_s*, int, double*, cudaStream_t);
+template int launch_transfer<float, 4, false>(fmm_plan_s*, int, float*, cudaStream_t);
+template int launch_transfer<double, 4, false>(fmm_plan_s*, int, double*, cudaStream_t);
+
+int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s) {
+  const Layout& L = P->lay;
+  double* scal = ws_ptr<double>(P, L.scal);
+  k_units<<<1, 32, 0, s>>>(ws_ptr<double>(P, L.nlo), ws_ptr<double>(P, L.nhi), scal);
+  FMM_LAUNCH_CHECK();
+  k_node_geo<<<(unsigned)div_up(P->C, 128), 128, 0, s>>>(ws_ptr<double>(P, L.nlo), ws_ptr<double>(P, L.nhi),
+                                                          P->C, scal, ws_ptr<double>(P, L.ncen),
+                                                          ws_ptr<double>(P, L.ndiam), ws_ptr<NodeGeo>(P, L.ngeo));
+  FMM_LAUNCH_CHECK();
+  const int gs = (int)std::min<int64_t>(8192, div_up(P->N, 256));
+  if (P->precision == FMM_FP32) {
+    k_prep<float><<<gs, 256, 0, s>>>(x, p, q, P->N, ws_ptr<int32_t>(P, L.perm), ws_ptr<int64_t>(P, L.nstart),
+                                      P->kappa, ws_ptr<double>(P, L.ncen), scal, ws_ptr<float4>(P, L.px),
+                                      ws_ptr<float4>(P, L.pb), ws_ptr<float4>(P, L.pl));
+  } else {
+    k_prep<double><<<gs, 256, 0, s>>>(x, p, q, P->N, ws_ptr<int32_t>(P, L.perm), ws_ptr<int64_t>(P, L.nstart),
+                                       P->kappa, ws_ptr<double>(P, L.ncen), scal, ws_ptr<double4>(P, L.px),
+                                       ws_ptr<double4>(P, L.pb), ws_ptr<double4>(P, L.pl));
+  }
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+int run_upward(fmm_plan_s* P, cudaStream_t s) {
+  return P->precision == FMM_FP32 ? upward_t<float>(P, s) : upward_t<double>(P, s);
+}
+
+int run_l2l(fmm_plan_s* P, cudaStream_t s) {
+  for (int l = 0; l < P->kappa; ++l) {
+    int rc = P->precision == FMM_FP32
+                 ? launch_transfer<float, 6, false>(P, l, ws_ptr<float>(P, P->lay.local), s)
+                 : launch_transfer<double, 6, false>(P, l, ws_ptr<double>(P, P->lay.local), s);
+    if (rc != FMM_OK) return rc;
+  }
+  return FMM_OK;
+}
+
+}  // namespace fmm

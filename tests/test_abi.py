@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every function include/fmm.h declares (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2302_07567_gb300 import build
+    return build.build()
+
+
+def test_every_declared_symbol_is_exported(libpath):
+    names = _declared()
+    assert "fmm_field" in names and "fmm_field_adjoint" in names and len(names) >= 12
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fmm_\w+)$", out, flags=re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_host_side_argument_checks(libpath):
+    """Plan creation validates its arguments without touching a GPU."""
+    lib = ctypes.CDLL(libpath)
+    lib.fmm_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_uint]
+    lib.fmm_strerror.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    bad = [(0, 4, 64, 0.5, 1), (100, 0, 64, 0.5, 1), (100, 13, 64, 0.5, 1), (100, 4, 1, 0.5, 1),
+           (100, 4, 64, 0.0, 1), (100, 4, 64, float("nan"), 1), (100, 4, 64, 0.5, 7), (100, 4, 5000, 0.5, 1)]
+    for N, n, leaf, eta, prec in bad:
+        assert lib.fmm_plan_create(ctypes.byref(h), N, n, leaf, eta, prec, 0) == 1
+    assert lib.fmm_plan_create(ctypes.byref(h), 4096, 4, 64, 0.5, 1, 0) == 0
+    lib.fmm_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    nb = ctypes.c_size_t()
+    assert lib.fmm_plan_workspace_bytes(h, ctypes.byref(nb)) == 0 and nb.value > 4096 * 100
+    lib.fmm_field.argtypes = [ctypes.c_void_p] * 7
+    one = ctypes.c_void_p(256)
+    assert lib.fmm_field(h, one, one, one, one, one, None) == 2  # no workspace attached
+    lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
+    lib.fmm_plan_destroy(h)
+    assert lib.fmm_strerror(3) == b"interaction-list capacity exceeded"
