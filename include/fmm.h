@@ -159,7 +159,8 @@ int fmm_plan_export(fmm_plan_t plan, int what, void* host_dst, size_t bytes);
 
 /* Brute force of Section 5 (Alg. 10 with S_t = S_s = S, i != j) in float64 for
  * the T target rows listed in `targets` (device int64[T]; NULL = all N, T = N).
- * gbar < 0 computes gbar from p as fmm_field does.  E, B: device float64 [T,3].
+ * gbar >= 1 is the stretch factor of Eq. 3.2, e.g. fmm_stats.gbar of a plan run
+ * on the same particles (FMM_EINVAL otherwise).  E, B: device float64 [T,3].
  * Work is O(T N); it is the reference the library's error reports use. */
 int fmm_direct_field(const double* x, const double* p, const double* q, int64_t N,
                      const int64_t* targets, int64_t T, double gbar, double* E, double* B,
