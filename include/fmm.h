@@ -175,6 +175,21 @@ int fmm_version(void);
  * (all plans, all threads); differences around a region count its launches. */
 int64_t fmm_kernel_launches(void);
 
+/* gbar of a beam without allocating anything (the paper has no counterpart;
+ * the value is the gbar of Eq. 3.2 that fmm_field computes, bit for bit).
+ * For callers that cannot allocate device memory or attach a workspace: code
+ * running during stream capture, allocation-free tracking loops, hosts whose
+ * device memory is owned by a pool.  The partial sums live in a fixed scratch
+ * array inside the library (~200 KB, held by every GPU that loads the library
+ * until exit).
+ *   p     device [N,3] float64 momenta;  gbar  device double[1] output
+ *   N     1 .. FMM_NOALLOC_MAX_N, else FMM_EINVAL (nothing is launched)
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls share the scratch array:
+ * calls whose work overlaps on the GPU race on it. */
+#define FMM_NOALLOC_MAX_N 16777216
+int fmm_gamma_bar_noalloc(const double* p, int64_t N, double* gbar, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

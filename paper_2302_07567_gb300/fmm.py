@@ -76,6 +76,7 @@ def lib():
         "fmm_last_cuda_error": (ctypes.c_char_p, []),
         "fmm_version": (I32, []),
         "fmm_kernel_launches": (I64, []),
+        "fmm_gamma_bar_noalloc": (I32, [P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
