@@ -124,10 +124,12 @@ typedef struct fmm_stats {
   double p2p_interactions;               /* sum |S_t||S_s| over P2P pairs minus N     */
   double m2l_interactions;               /* m2l_pairs * (n+1)^6                       */
   int64_t cap_p2p, cap_m2l, cap_frontier;
-  /* stage times of the last call in ms (FMM_TIMING only, else 0):
-     0 setup, 1 tree, 2 upward, 3 traversal, 4 list sort, 5 M2L, 6 L2L, 7 P2P+L2P,
-     8 adjoint upward (L2P^T, L2L^T), 9 adjoint M2L^T, 10 adjoint downward (M2M^T),
-     11 adjoint near field, 12 adjoint far field at particles, 13 whole call */
+  /* stage times of the last calls in ms (FMM_TIMING only, else 0):
+     forward: 0 setup, 1 tree, 2 upward, 3 traversal, 4 list sort, 5 M2L, 6 L2L,
+     7 P2P+L2P, 13 whole forward;  adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T,
+     11 target-side particle kernel (near + far), 12 source-side particle kernel
+     (near + far + chain rule), 14 whole adjoint, 15 source-major lists and any
+     recomputation */
   double stage_ms[16];
 } fmm_stats;
 

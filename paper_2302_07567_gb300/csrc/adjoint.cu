@@ -1,9 +1,818 @@
-// Adjoint of the FMM operator (placeholder until the adjoint kernels land).
+// Adjoint of the FMM operator (the paper has no adjoint).
+//
+// For the loss L = sum_i wE_i . E_i + wB_i . B_i the adjoint returns dL/dx,
+// dL/dp and dL/dq of the FMM of Alg. 12 with the tree, boxes, interaction
+// lists and gbar held at the values of the forward call.  In the library's
+// stretched, scaled units the forward is E'_i = sum_j a'_j K(R'_ij) and
+// B'_i = sum_j b~'_j x K(R'_ij) with K(R) = R/|R|^3 (plus the interpolated far
+// field), and L = sum_i wE^_i . E'_i + wB^_i . B'_i with the scaled weights
+// wE^ = kE diag(1,1,1/gbar) wE, wB^ = kB diag(1,1,gbar) wB.  With
+// u_ij = a'_j wE^_i + wB^_i x b~'_j and J(R) = dK/dR (symmetric):
+//   near field, pair (i, j):  dL/da'_j += wE^_i . K,  dL/db~'_j += K x wB^_i,
+//                             dL/dx'_i += J u_ij,     dL/dx'_j -= J u_ij,
+//                             J u = u/|R|^3 - 3 R (R.u)/|R|^5;
+//   far field, target side:   dL/dx'_i += sum_mu grad l_mu(x_i) (w^_i . Lc_mu),
+//                             Lc the forward's cumulative local of i's leaf;
+//   far field, source side:   W = L2P^T(w^) at the leaves, pushed up by the
+//                             transposed L2L (an M2M), M2L^T over the
+//                             source-major M2L list gives Lambda per source
+//                             cluster, pushed down by the transposed M2M (an
+//                             L2L); then dL/da'_j += sum_nu l_nu(x_j) Lambda^a_nu,
+//                             dL/db~'_j += sum_nu l_nu(x_j) Lambda^b_nu and
+//                             dL/dx'_j += sum_nu grad l_nu(x_j) (Lambda_nu . m'_j).
+// The basis derivative is l_k'(t) = sum_m l_m(t) D[m][k] (ChebD).  The chain
+// rule finally maps (a', b~', x') to (q, p, x) with a = q gamma, b = q p,
+// gamma = sqrt(1 + |p|^2).
+//
+// Buffer reuse: W is written into the forward's local buffer and Lambda into
+// its multipole buffer, so the target-side kernel (which reads the forward's
+// cumulative locals) runs first.  A second adjoint call for the same forward
+// recomputes the upward pass, M2L and L2L.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fmm {
-int run_adjoint(fmm_plan_s*, const double*, const double*, const double*, const void*, const void*, double*,
-                double*, double*, cudaStream_t) {
-  return FMM_EINVAL;
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void basis_deriv(T t, bool deg, const Cheb& ch, const ChebD& cd, T* l, T* dl) {
+  bary_basis<T>(t, deg, ch, l);
+  const int np1 = ch.np1;
+  for (int k = 0; k < np1; ++k) {
+    T s = T(0);
+    for (int mm = 0; mm < np1; ++mm) s += l[mm] * (T)cd.D[mm * np1 + k];
+    dl[k] = deg ? T(0) : s;
+  }
 }
+
+// Scaled loss weights in leaf order.
+template <typename T>
+__global__ void k_adj_prep(const T* __restrict__ wE, const T* __restrict__ wB, int64_t N,
+                           const int32_t* __restrict__ perm, const double* __restrict__ scal,
+                           typename Vec4<T>::type* __restrict__ wle, typename Vec4<T>::type* __restrict__ wlb) {
+  const double gbar = scal[0], kE = scal[4], kB = scal[5];
+  for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < N; pos += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[pos];
+    typename Vec4<T>::type e, b;
+    e.x = (T)(kE * (double)wE[3 * i]);
+    e.y = (T)(kE * (double)wE[3 * i + 1]);
+    e.z = (T)(kE * (double)wE[3 * i + 2] / gbar);
+    e.w = T(0);
+    b.x = (T)(kB * (double)wB[3 * i]);
+    b.y = (T)(kB * (double)wB[3 * i + 1]);
+    b.z = (T)(kB * (double)wB[3 * i + 2] * gbar);
+    b.w = T(0);
+    wle[pos] = e;
+    wlb[pos] = b;
+  }
+}
+
+// L2P^T: W[leaf][c][mu] = sum_{i in leaf} l_mu(x_i) w^_i[c], c = (wE^, wB^).
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __restrict__ px,
+                                              const typename Vec4<T>::type* __restrict__ pl,
+                                              const typename Vec4<T>::type* __restrict__ wle,
+                                              const typename Vec4<T>::type* __restrict__ wlb,
+                                              const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount,
+                                              int kappa, const NodeGeo* __restrict__ geo, Cheb ch, int m,
+                                              T* __restrict__ W) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  constexpr bool kSplit = std::is_same<T, float>::value;
+  const int np1 = ch.np1;
+  const int stride = 3 * np1 + 6;
+  const int64_t leaf = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[leaf], cnt = ncount[leaf];
+  const NodeGeo g = geo[leaf];
+  T invh[3];
+  bool deg[3];
+  for (int k = 0; k < 3; ++k) {
+    deg[k] = !(g.h[k] > 0.0);
+    invh[k] = deg[k] ? T(0) : (T)(1.0 / g.h[k]);
+  }
+  T acc[NV][6], cmp[NV][6];
+  int nu1[NV], nu2[NV], nu3[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int nu = threadIdx.x + v * blockDim.x;
+    nu1[v] = nu % np1;
+    nu2[v] = (nu / np1) % np1;
+    nu3[v] = nu / (np1 * np1);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[v][c] = cmp[v][c] = T(0);
+  }
+  for (int64_t base = 0; base < cnt; base += blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    T* row = sm + (size_t)threadIdx.x * stride;
+    if (j < cnt) {
+      const typename Vec4<T>::type u = px[st + j], e = wle[st + j], b = wlb[st + j];
+      T rel[3] = {u.x, u.y, u.z};
+      if (kSplit) {
+        const typename Vec4<T>::type l = pl[st + j];
+        rel[0] += l.x; rel[1] += l.y; rel[2] += l.z;
+      }
+      for (int k = 0; k < 3; ++k) bary_basis<T>(rel[k] * invh[k], deg[k], ch, row + k * np1);
+      row[3 * np1 + 0] = e.x; row[3 * np1 + 1] = e.y; row[3 * np1 + 2] = e.z;
+      row[3 * np1 + 3] = b.x; row[3 * np1 + 4] = b.y; row[3 * np1 + 5] = b.z;
+    }
+    __syncthreads();
+    const int nj = (int)min64(blockDim.x, cnt - base);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int nu = threadIdx.x + v * blockDim.x;
+      if (nu >= m) continue;
+      for (int j0 = 0; j0 < nj; j0 += 32) {
+        T part[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        const int j1 = min(nj, j0 + 32);
+        for (int jj = j0; jj < j1; ++jj) {
+          const T* r = sm + (size_t)jj * stride;
+          const T wgt = r[nu1[v]] * r[np1 + nu2[v]] * r[2 * np1 + nu3[v]];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) part[c] += wgt * r[3 * np1 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kahan_add(acc[v][c], cmp[v][c], part[c]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int nu = threadIdx.x + v * blockDim.x;
+    if (nu >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) W[((size_t)leaf * 6 + c) * m + nu] = acc[v][c];
+  }
+}
+
+// M2L^T: for source cluster s, Lambda[s][nu] = sum over target clusters S of
+// the source-major M2L list and their points mu of (W^E_{S,mu} . K(R),
+// K(R) x W^B_{S,mu}) with R = xi_{S,mu} - xi_{s,nu}.
+template <typename T, int KPT>
+__global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
+                                                 int shift, const NodeGeo* __restrict__ geo,
+                                                 const void* __restrict__ sdc, Cheb ch, int m,
+                                                 const T* __restrict__ W, T* __restrict__ Lam) {
+  using V4 = typename Vec4<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  V4* sm = reinterpret_cast<V4*>(smem_raw);  // [m][3]
+  const int64_t s = (int64_t)blockIdx.x + 1;
+  const int np1 = ch.np1;
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const int b = off[s], e = off[s + 1];
+  const NodeGeo gs = geo[s];
+  const int per_pass = KPT * blockDim.x;
+  for (int pass0 = 0; pass0 < m; pass0 += per_pass) {
+    T xh[KPT][3];
+    bool valid[KPT];
+    T acc[KPT][4], cmp[KPT][4];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int nu = pass0 + threadIdx.x + k * blockDim.x;
+      valid[k] = nu < m;
+      const int nn = valid[k] ? nu : 0;
+      xh[k][0] = (T)(gs.h[0] * ch.t[nn % np1]);
+      xh[k][1] = (T)(gs.h[1] * ch.t[(nn / np1) % np1]);
+      xh[k][2] = (T)(gs.h[2] * ch.t[nn / (np1 * np1)]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[k][c] = cmp[k][c] = T(0);
+    }
+    for (int it = b; it < e; ++it) {
+      const int64_t S = (int64_t)(keys[it] & mask);
+      T dc0, dc1, dc2;  // c_s - c_S
+      if constexpr (sizeof(T) == 4) {
+        const float4 dh = static_cast<const float4*>(sdc)[2 * it];
+        dc0 = dh.x; dc1 = dh.y; dc2 = dh.z;
+      } else {
+        const double4 dd = static_cast<const double4*>(sdc)[it];
+        dc0 = dd.x; dc1 = dd.y; dc2 = dd.z;
+      }
+      const NodeGeo gS = geo[S];
+      __syncthreads();
+      for (int o = threadIdx.x; o < m; o += blockDim.x) {
+        const T* w = W + (size_t)S * 6 * m + o;
+        V4 r0, r1, r2;
+        r0.x = (T)(gS.h[0] * ch.t[o % np1]);
+        r0.y = (T)(gS.h[1] * ch.t[(o / np1) % np1]);
+        r0.z = (T)(gS.h[2] * ch.t[o / (np1 * np1)]);
+        r0.w = w[0];
+        r1.x = w[m]; r1.y = w[2 * m]; r1.z = w[3 * m]; r1.w = w[4 * m];
+        r2.x = w[5 * m]; r2.y = T(0); r2.z = T(0); r2.w = T(0);
+        sm[3 * o] = r0;
+        sm[3 * o + 1] = r1;
+        sm[3 * o + 2] = r2;
+      }
+      __syncthreads();
+      T Z[KPT][3], part[KPT][4];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        Z[k][0] = xh[k][0] + dc0;
+        Z[k][1] = xh[k][1] + dc1;
+        Z[k][2] = xh[k][2] + dc2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[k][c] = T(0);
+      }
+      for (int mu = 0; mu < m; ++mu) {
+        const V4 r0 = sm[3 * mu], r1 = sm[3 * mu + 1], r2 = sm[3 * mu + 2];
+        // r0 = (Y, WE.x), r1 = (WE.y, WE.z, WB.x, WB.y), r2 = (WB.z, ...)
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          const T rx = r0.x - Z[k][0], ry = r0.y - Z[k][1], rz = r0.z - Z[k][2];
+          const T d = rx * rx + ry * ry + rz * rz;
+          const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+          const T r3 = inv * inv * inv;
+          part[k][0] += r3 * (rx * r0.w + ry * r1.x + rz * r1.y);
+          part[k][1] += r3 * (ry * r2.x - rz * r1.w);
+          part[k][2] += r3 * (rz * r1.z - rx * r2.x);
+          part[k][3] += r3 * (rx * r1.w - ry * r1.z);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int nu = pass0 + threadIdx.x + k * blockDim.x;
+      if (!valid[k]) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = acc[k][c];
+    }
+  }
+}
+
+// Near field at the targets (J u over the target-major P2P list) plus the far
+// field at the targets (grad of the forward's cumulative local); writes the
+// target-side dL/dx' of every particle (leaf order).
+template <typename T, int KPT>
+__global__ void __launch_bounds__(256) k_adj_target(
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
+    const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
+    const typename Vec4<T>::type* __restrict__ pb, const typename Vec4<T>::type* __restrict__ pl,
+    const void* __restrict__ pdc_raw, const typename Vec4<T>::type* __restrict__ wle,
+    const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lcum, Cheb ch, ChebD cd, int m,
+    typename Vec4<T>::type* __restrict__ gout) {
+  using V4 = typename Vec4<T>::type;
+  constexpr bool kSplit = std::is_same<T, float>::value;
+  constexpr int kRow = kSplit ? 3 : 2;
+  extern __shared__ unsigned char smem_raw[];
+  V4* sp = reinterpret_cast<V4*>(smem_raw);
+  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [6][m]
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[t], cnt = ncount[t];
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const NodeGeo gt = geo[t];
+  const int b = off[t], e = off[t + 1];
+  const int np1 = ch.np1;
+  T invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(gt.h[d] > 0.0);
+    invh[d] = deg[d] ? T(0) : (T)(1.0 / gt.h[d]);
+  }
+  if (kappa > 0) {
+    const T* Lt = Lcum + (size_t)t * 6 * m;
+    for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
+  }
+  const int64_t per_pass = (int64_t)KPT * blockDim.x;
+  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+    T ri[KPT][3], rl[KPT][3], we[KPT][3], wb[KPT][3];
+    bool valid[KPT];
+    T acc[KPT][3], cmp[KPT][3];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      valid[k] = j < cnt;
+      const int64_t jj = st + (valid[k] ? j : 0);
+      const V4 u = px[jj], a = wle[jj], c = wlb[jj];
+      ri[k][0] = u.x; ri[k][1] = u.y; ri[k][2] = u.z;
+      if constexpr (kSplit) {
+        const V4 l = pl[jj];
+        rl[k][0] = l.x; rl[k][1] = l.y; rl[k][2] = l.z;
+      } else {
+        rl[k][0] = rl[k][1] = rl[k][2] = T(0);
+      }
+      we[k][0] = a.x; we[k][1] = a.y; we[k][2] = a.z;
+      wb[k][0] = c.x; wb[k][1] = c.y; wb[k][2] = c.z;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) acc[k][d] = cmp[k][d] = T(0);
+    }
+    for (int it = b; it < e; ++it) {
+      const int64_t s = (int64_t)(keys[it] & mask);
+      const int64_t sst = nstart[s], scnt = ncount[s];
+      T X[KPT][3], XL[KPT][3], part[KPT][3];
+      if constexpr (kSplit) {
+        const float4* pdc = static_cast<const float4*>(pdc_raw);
+        const float4 dh = pdc[2 * it], dl = pdc[2 * it + 1];
+        const float dch[3] = {dh.x, dh.y, dh.z}, dcl[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float hs, he;
+            two_sum(ri[k][d], dch[d], hs, he);
+            const float lo = he + (rl[k][d] + dcl[d]);
+            X[k][d] = hs + lo;
+            XL[k][d] = lo - (X[k][d] - hs);
+          }
+      } else {
+        const double4 dd = static_cast<const double4*>(pdc_raw)[it];
+        const T dc[3] = {(T)dd.x, (T)dd.y, (T)dd.z};
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            X[k][d] = ri[k][d] + dc[d];
+            XL[k][d] = T(0);
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) part[k][d] = T(0);
+      for (int64_t base = 0; base < scnt; base += blockDim.x) {
+        __syncthreads();
+        const int64_t j = base + threadIdx.x;
+        if (j < scnt) {
+          sp[kRow * threadIdx.x] = px[sst + j];
+          sp[kRow * threadIdx.x + 1] = pb[sst + j];
+          if constexpr (kSplit) sp[kRow * threadIdx.x + 2] = pl[sst + j];
+        }
+        __syncthreads();
+        const int nj = (int)min64(blockDim.x, scnt - base);
+        for (int jj = 0; jj < nj; ++jj) {
+          const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
+          V4 ul;
+          if constexpr (kSplit) ul = sp[kRow * jj + 2];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            T rx, ry, rz;
+            if constexpr (kSplit) {
+              rx = (X[k][0] - u.x) + (XL[k][0] - ul.x);
+              ry = (X[k][1] - u.y) + (XL[k][1] - ul.y);
+              rz = (X[k][2] - u.z) + (XL[k][2] - ul.z);
+            } else {
+              rx = X[k][0] - u.x;
+              ry = X[k][1] - u.y;
+              rz = X[k][2] - u.z;
+            }
+            const T d = rx * rx + ry * ry + rz * rz;
+            const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+            const T r3 = inv * inv * inv;
+            const T r5 = r3 * inv * inv;
+            // u = a'_j wE^_i + wB^_i x b~'_j
+            const T ux = u.w * we[k][0] + (wb[k][1] * w.z - wb[k][2] * w.y);
+            const T uy = u.w * we[k][1] + (wb[k][2] * w.x - wb[k][0] * w.z);
+            const T uz = u.w * we[k][2] + (wb[k][0] * w.y - wb[k][1] * w.x);
+            const T c3 = T(3) * r5 * (rx * ux + ry * uy + rz * uz);
+            part[k][0] += r3 * ux - c3 * rx;
+            part[k][1] += r3 * uy - c3 * ry;
+            part[k][2] += r3 * uz - c3 * rz;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], part[k][d]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (!valid[k]) continue;
+      if (kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
+        T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
+        const T lof = kSplit ? T(1) : T(0);
+        basis_deriv<T>((ri[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, cd, lx, dx);
+        basis_deriv<T>((ri[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, cd, ly, dy);
+        basis_deriv<T>((ri[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, cd, lz, dz);
+        T G[3] = {T(0), T(0), T(0)};
+        int mu = 0;
+        for (int a3 = 0; a3 < np1; ++a3) {
+          for (int a2 = 0; a2 < np1; ++a2) {
+            T s0 = T(0), sx = T(0);
+            for (int a1 = 0; a1 < np1; ++a1, ++mu) {
+              const T phi = we[k][0] * sl[mu] + we[k][1] * sl[m + mu] + we[k][2] * sl[2 * m + mu] +
+                            wb[k][0] * sl[3 * m + mu] + wb[k][1] * sl[4 * m + mu] + wb[k][2] * sl[5 * m + mu];
+              s0 += lx[a1] * phi;
+              sx += dx[a1] * phi;
+            }
+            G[0] += ly[a2] * lz[a3] * sx;
+            G[1] += dy[a2] * lz[a3] * s0;
+            G[2] += ly[a2] * dz[a3] * s0;
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], G[d] * invh[d]);
+      }
+      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      V4 o;
+      o.x = acc[k][0]; o.y = acc[k][1]; o.z = acc[k][2]; o.w = T(0);
+      gout[pos] = o;
+    }
+  }
+}
+
+// Source side: near field over the source-major P2P list, far field from the
+// pushed-down Lambda, plus the target-side part; then the chain rule to
+// physical (x, p, q), written in input order.
+template <typename T, int KPT>
+__global__ void __launch_bounds__(256) k_adj_source(
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
+    const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
+    const typename Vec4<T>::type* __restrict__ pb, const typename Vec4<T>::type* __restrict__ pl,
+    const void* __restrict__ sdc_raw, const typename Vec4<T>::type* __restrict__ wle,
+    const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lam, Cheb ch, ChebD cd, int m,
+    const typename Vec4<T>::type* __restrict__ gtarget, const int32_t* __restrict__ perm,
+    const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q,
+    double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
+  using V4 = typename Vec4<T>::type;
+  constexpr bool kSplit = std::is_same<T, float>::value;
+  constexpr int kRow = kSplit ? 4 : 3;
+  extern __shared__ unsigned char smem_raw[];
+  V4* sp = reinterpret_cast<V4*>(smem_raw);
+  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [4][m]
+  const int64_t s = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[s], cnt = ncount[s];
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const NodeGeo gs = geo[s];
+  const int b = off[s], e = off[s + 1];
+  const int np1 = ch.np1;
+  T invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(gs.h[d] > 0.0);
+    invh[d] = deg[d] ? T(0) : (T)(1.0 / gs.h[d]);
+  }
+  if (kappa > 0) {
+    const T* Ls = Lam + (size_t)s * 4 * m;
+    for (int o = threadIdx.x; o < 4 * m; o += blockDim.x) sl[o] = Ls[o];
+  }
+  const int64_t per_pass = (int64_t)KPT * blockDim.x;
+  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+    T rj[KPT][3], rl[KPT][3], aj[KPT], bj[KPT][3];
+    bool valid[KPT];
+    T acc[KPT][7], cmp[KPT][7];  // (dL/da', dL/db~' x3, dL/dx' x3)
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      valid[k] = j < cnt;
+      const int64_t jj = st + (valid[k] ? j : 0);
+      const V4 u = px[jj], w = pb[jj];
+      rj[k][0] = u.x; rj[k][1] = u.y; rj[k][2] = u.z;
+      aj[k] = u.w;
+      bj[k][0] = w.x; bj[k][1] = w.y; bj[k][2] = w.z;
+      if constexpr (kSplit) {
+        const V4 l = pl[jj];
+        rl[k][0] = l.x; rl[k][1] = l.y; rl[k][2] = l.z;
+      } else {
+        rl[k][0] = rl[k][1] = rl[k][2] = T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) acc[k][c] = cmp[k][c] = T(0);
+    }
+    for (int it = b; it < e; ++it) {
+      const int64_t t = (int64_t)(keys[it] & mask);
+      const int64_t tst = nstart[t], tcnt = ncount[t];
+      T X[KPT][3], XL[KPT][3], part[KPT][7];
+      // X = x_j + (c_s - c_t): the source particle in the target leaf's frame
+      if constexpr (kSplit) {
+        const float4* sdc = static_cast<const float4*>(sdc_raw);
+        const float4 dh = sdc[2 * it], dl = sdc[2 * it + 1];
+        const float dch[3] = {dh.x, dh.y, dh.z}, dcl[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float hs, he;
+            two_sum(rj[k][d], dch[d], hs, he);
+            const float lo = he + (rl[k][d] + dcl[d]);
+            X[k][d] = hs + lo;
+            XL[k][d] = lo - (X[k][d] - hs);
+          }
+      } else {
+        const double4 dd = static_cast<const double4*>(sdc_raw)[it];
+        const T dc[3] = {(T)dd.x, (T)dd.y, (T)dd.z};
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            X[k][d] = rj[k][d] + dc[d];
+            XL[k][d] = T(0);
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) part[k][c] = T(0);
+      for (int64_t base = 0; base < tcnt; base += blockDim.x) {
+        __syncthreads();
+        const int64_t i = base + threadIdx.x;
+        if (i < tcnt) {
+          sp[kRow * threadIdx.x] = px[tst + i];
+          sp[kRow * threadIdx.x + 1] = wle[tst + i];
+          sp[kRow * threadIdx.x + 2] = wlb[tst + i];
+          if constexpr (kSplit) sp[kRow * threadIdx.x + 3] = pl[tst + i];
+        }
+        __syncthreads();
+        const int ni = (int)min64(blockDim.x, tcnt - base);
+        for (int ii = 0; ii < ni; ++ii) {
+          const V4 u = sp[kRow * ii], we = sp[kRow * ii + 1], wb = sp[kRow * ii + 2];
+          V4 ul;
+          if constexpr (kSplit) ul = sp[kRow * ii + 3];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            T rx, ry, rz;  // R = x_i - x_j
+            if constexpr (kSplit) {
+              rx = (u.x - X[k][0]) + (ul.x - XL[k][0]);
+              ry = (u.y - X[k][1]) + (ul.y - XL[k][1]);
+              rz = (u.z - X[k][2]) + (ul.z - XL[k][2]);
+            } else {
+              rx = u.x - X[k][0];
+              ry = u.y - X[k][1];
+              rz = u.z - X[k][2];
+            }
+            const T d = rx * rx + ry * ry + rz * rz;
+            const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+            const T r3 = inv * inv * inv;
+            const T r5 = r3 * inv * inv;
+            const T kx = r3 * rx, ky = r3 * ry, kz = r3 * rz;
+            part[k][0] += we.x * kx + we.y * ky + we.z * kz;
+            part[k][1] += ky * wb.z - kz * wb.y;
+            part[k][2] += kz * wb.x - kx * wb.z;
+            part[k][3] += kx * wb.y - ky * wb.x;
+            const T ux = aj[k] * we.x + (wb.y * bj[k][2] - wb.z * bj[k][1]);
+            const T uy = aj[k] * we.y + (wb.z * bj[k][0] - wb.x * bj[k][2]);
+            const T uz = aj[k] * we.z + (wb.x * bj[k][1] - wb.y * bj[k][0]);
+            const T c3 = T(3) * r5 * (rx * ux + ry * uy + rz * uz);
+            part[k][4] -= r3 * ux - c3 * rx;
+            part[k][5] -= r3 * uy - c3 * ry;
+            part[k][6] -= r3 * uz - c3 * rz;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
+    }
+    __syncthreads();
+    const double gbar = scal[0], mu_u = scal[1], ell = scal[2];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (!valid[k]) continue;
+      if (kappa > 0) {  // far field at the source: through the P2M basis of its leaf
+        T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
+        const T lof = kSplit ? T(1) : T(0);
+        basis_deriv<T>((rj[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, cd, lx, dx);
+        basis_deriv<T>((rj[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, cd, ly, dy);
+        basis_deriv<T>((rj[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, cd, lz, dz);
+        T F[4] = {T(0), T(0), T(0), T(0)}, G[3] = {T(0), T(0), T(0)};
+        int nu = 0;
+        for (int a3 = 0; a3 < np1; ++a3) {
+          for (int a2 = 0; a2 < np1; ++a2) {
+            T f[4] = {T(0), T(0), T(0), T(0)};
+            T s0 = T(0), sx = T(0);
+            for (int a1 = 0; a1 < np1; ++a1, ++nu) {
+              const T L0 = sl[nu], L1 = sl[m + nu], L2 = sl[2 * m + nu], L3 = sl[3 * m + nu];
+              const T psi = L0 * aj[k] + L1 * bj[k][0] + L2 * bj[k][1] + L3 * bj[k][2];
+              f[0] += lx[a1] * L0;
+              f[1] += lx[a1] * L1;
+              f[2] += lx[a1] * L2;
+              f[3] += lx[a1] * L3;
+              s0 += lx[a1] * psi;
+              sx += dx[a1] * psi;
+            }
+            const T wyz = ly[a2] * lz[a3];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) F[c] += wyz * f[c];
+            G[0] += wyz * sx;
+            G[1] += dy[a2] * lz[a3] * s0;
+            G[2] += ly[a2] * dz[a3] * s0;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) kahan_add(acc[k][c], cmp[k][c], F[c]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) kahan_add(acc[k][4 + d], cmp[k][4 + d], G[d] * invh[d]);
+      }
+      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      const V4 gt = gtarget[pos];
+      // internal (a', b~', x') -> physical (a, b, x)
+      const double dA = (double)acc[k][0] / mu_u;
+      const double dB[3] = {(double)acc[k][1] / (gbar * mu_u), (double)acc[k][2] / (gbar * mu_u),
+                            (double)acc[k][3] / mu_u};
+      const double dX[3] = {((double)acc[k][4] + (double)gt.x) / ell, ((double)acc[k][5] + (double)gt.y) / ell,
+                            gbar * ((double)acc[k][6] + (double)gt.z) / ell};
+      const int64_t i = perm[pos];
+      const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2], qi = q[i];
+      const double gam = sqrt(1.0 + ((p0 * p0 + p1 * p1) + p2 * p2));
+      // a = q gamma, b = q p:  dL/dq = gamma dL/da + p . dL/db,
+      //                        dL/dp = q (p/gamma) dL/da + q dL/db
+      dq_out[i] = gam * dA + (p0 * dB[0] + p1 * dB[1] + p2 * dB[2]);
+      dp_out[3 * i + 0] = qi * (p0 / gam) * dA + qi * dB[0];
+      dp_out[3 * i + 1] = qi * (p1 / gam) * dA + qi * dB[1];
+      dp_out[3 * i + 2] = qi * (p2 / gam) * dA + qi * dB[2];
+      dx_out[3 * i + 0] = dX[0];
+      dx_out[3 * i + 1] = dX[1];
+      dx_out[3 * i + 2] = dX[2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename K>
+int set_smem(K kernel) {
+  FMM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  return FMM_OK;
+}
+
+template <typename T, int NV>
+int launch_l2pt(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  static bool attr = false;
+  if (!attr) {
+    if (int rc = set_smem(k_l2pt<T, NV>)) return rc;
+    attr = true;
+  }
+  const size_t smem = (size_t)256 * (3 * P->np1 + 6) * sizeof(T);
+  using V4 = typename Vec4<T>::type;
+  k_l2pt<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pl), ws_ptr<V4>(P, L.wle),
+                                                        ws_ptr<V4>(P, L.wlb), ws_ptr<int64_t>(P, L.nstart),
+                                                        ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
+                                                        P->cheb, P->m, ws_ptr<T>(P, L.local));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int l2pt(fmm_plan_s* P, cudaStream_t s) {
+  switch (div_up(P->m, 256)) {
+    case 1: return launch_l2pt<T, 1>(P, s);
+    case 2: return launch_l2pt<T, 2>(P, s);
+    case 3: return launch_l2pt<T, 3>(P, s);
+    case 4: return launch_l2pt<T, 4>(P, s);
+    case 5: return launch_l2pt<T, 5>(P, s);
+    case 6: return launch_l2pt<T, 6>(P, s);
+    case 7: return launch_l2pt<T, 7>(P, s);
+    case 8: return launch_l2pt<T, 8>(P, s);
+    default: return launch_l2pt<T, 9>(P, s);
+  }
+}
+
+template <typename T, int KPT>
+int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
+  const Layout& L = P->lay;
+  static bool attr = false;
+  if (!attr) {
+    if (int rc = set_smem(k_adj_m2l<T, KPT>)) return rc;
+    attr = true;
+  }
+  const size_t smem = (size_t)3 * P->m * sizeof(typename Vec4<T>::type);
+  k_adj_m2l<T, KPT><<<(unsigned)P->C, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff),
+                                                      P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc,
+                                                      P->cheb, P->m, ws_ptr<T>(P, L.local), ws_ptr<T>(P, L.mpole));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int adj_m2l(fmm_plan_s* P, cudaStream_t s) {
+  // the same thread shape rule as the forward M2L
+  int best_nt = 256, best_k = 4;
+  int64_t best_waste = -1, best_passes = 0;
+  for (int k = 1; k <= 4; ++k) {
+    int t = (int)(div_up(div_up(P->m, k), 32) * 32);
+    if (t > 256) t = 256;
+    const int64_t passes = div_up(P->m, (int64_t)t * k);
+    const int64_t waste = passes * t * k - P->m;
+    if (best_waste < 0 || waste < best_waste || (waste == best_waste && passes < best_passes)) {
+      best_waste = waste;
+      best_passes = passes;
+      best_nt = t;
+      best_k = k;
+    }
+  }
+  switch (best_k) {
+    case 1: return launch_adj_m2l<T, 1>(P, best_nt, s);
+    case 2: return launch_adj_m2l<T, 2>(P, best_nt, s);
+    case 3: return launch_adj_m2l<T, 3>(P, best_nt, s);
+    default: return launch_adj_m2l<T, 4>(P, best_nt, s);
+  }
+}
+
+template <typename T>
+int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq,
+                  bool target_side, cudaStream_t s) {
+  const Layout& L = P->lay;
+  using V4 = typename Vec4<T>::type;
+  constexpr bool kSplit = std::is_same<T, float>::value;
+  const int kpt = P->leaf > 256 ? 2 : 1;
+  const int nt = (int)std::min<int64_t>(256, div_up(div_up(P->leaf, kpt), 32) * 32);
+  if (target_side) {
+    const size_t smem = sizeof(V4) * (kSplit ? 3 : 2) * nt + sizeof(T) * 6 * P->m;
+    static bool attr1 = false, attr2 = false;
+    if (kpt == 1) {
+      if (!attr1) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr1 = true; }
+      k_adj_target<T, 1><<<(unsigned)P->nleaves, nt, smem, s>>>(
+          ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
+          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part));
+    } else {
+      if (!attr2) { if (int rc = set_smem(k_adj_target<T, 2>)) return rc; attr2 = true; }
+      k_adj_target<T, 2><<<(unsigned)P->nleaves, nt, smem, s>>>(
+          ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
+          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part));
+    }
+  } else {
+    const size_t smem = sizeof(V4) * (kSplit ? 4 : 3) * nt + sizeof(T) * 4 * P->m;
+    static bool attr1 = false, attr2 = false;
+    if (kpt == 1) {
+      if (!attr1) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr1 = true; }
+      k_adj_source<T, 1><<<(unsigned)P->nleaves, nt, smem, s>>>(
+          ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
+          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
+          q, dx, dp, dq);
+    } else {
+      if (!attr2) { if (int rc = set_smem(k_adj_source<T, 2>)) return rc; attr2 = true; }
+      k_adj_source<T, 2><<<(unsigned)P->nleaves, nt, smem, s>>>(
+          ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
+          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
+          q, dx, dp, dq);
+    }
+  }
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+int record(fmm_plan_s* P, int k, cudaStream_t s) {
+  if (!(P->flags & FMM_TIMING) || !P->ev_made) return FMM_OK;
+  FMM_CUDA_TRY(cudaEventRecord(P->ev[k], s));
+  return FMM_OK;
+}
+
+template <typename T>
+int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE, const void* wB,
+              double* dx, double* dp, double* dq, cudaStream_t s) {
+  const Layout& L = P->lay;
+  using V4 = typename Vec4<T>::type;
+  int rc;
+  if ((rc = record(P, 15, s)) != FMM_OK) return rc;
+  if (!P->transposed_valid) {
+    if ((rc = run_list_transpose(P, s)) != FMM_OK) return rc;
+    P->transposed_valid = true;
+  }
+  if (!P->locals_valid || (P->flags & FMM_RECOMPUTE)) {  // the forward's multipoles and locals again
+    if ((rc = run_upward(P, s)) != FMM_OK) return rc;
+    if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
+    if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
+  }
+  if ((rc = record(P, 9, s)) != FMM_OK) return rc;
+  const int gs = (int)std::min<int64_t>(8192, div_up(P->N, 256));
+  k_adj_prep<T><<<gs, 256, 0, s>>>(static_cast<const T*>(wE), static_cast<const T*>(wB), P->N,
+                                    ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), ws_ptr<V4>(P, L.wle),
+                                    ws_ptr<V4>(P, L.wlb));
+  FMM_LAUNCH_CHECK();
+  if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, true, s)) != FMM_OK) return rc;
+  P->locals_valid = false;  // the local buffer now receives W
+  if ((rc = record(P, 10, s)) != FMM_OK) return rc;
+  if (P->kappa > 0) {
+    if ((rc = l2pt<T>(P, s)) != FMM_OK) return rc;
+    for (int l = P->kappa - 1; l >= 0; --l)  // L2L^T: W up the tree (M2M form)
+      if ((rc = launch_transfer<T, 6, true>(P, l, ws_ptr<T>(P, L.local), s)) != FMM_OK) return rc;
+  }
+  if ((rc = record(P, 11, s)) != FMM_OK) return rc;
+  if (P->kappa > 0 && (rc = adj_m2l<T>(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 12, s)) != FMM_OK) return rc;
+  if (P->kappa > 0) {
+    for (int l = 0; l < P->kappa; ++l)  // M2M^T: Lambda down the tree (L2L form)
+      if ((rc = launch_transfer<T, 4, false>(P, l, ws_ptr<T>(P, L.mpole), s)) != FMM_OK) return rc;
+  }
+  if ((rc = record(P, 13, s)) != FMM_OK) return rc;
+  if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, false, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 14, s)) != FMM_OK) return rc;
+  (void)x;
+  if (P->flags & FMM_TIMING) P->flags |= 0x100u;
+  return FMM_OK;
+}
+
+}  // namespace
+
+int run_adjoint(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE, const void* wB,
+                double* dx, double* dp, double* dq, cudaStream_t s) {
+  return P->precision == FMM_FP32 ? adjoint_t<float>(P, x, p, q, wE, wB, dx, dp, dq, s)
+                                  : adjoint_t<double>(P, x, p, q, wE, wB, dx, dp, dq, s);
+}
+
 }  // namespace fmm

@@ -55,6 +55,13 @@ struct Cheb {
   double w[kMaxNp1];
 };
 
+// Differentiation matrix of the Lagrange basis on the Chebyshev points:
+// D[m][k] = l_k'(t_m), so l_k'(t) = sum_m l_m(t) D[m][k] exactly (l_k' has
+// degree n - 1 and is reproduced by the interpolation, Theorem 1).
+struct ChebD {
+  double D[kMaxNp1 * kMaxNp1];
+};
+
 // Per-node geometry in stretched, scaled coordinates (FP64).
 struct NodeGeo {
   double c[3];  // box centre
@@ -73,7 +80,9 @@ struct Layout {
   size_t p2p_dc, m2l_dc;           // per list pair: centre offset c_t - c_s as (hi, lo)
   size_t mpole, local, srct;
   size_t front0, front1, p2p, m2l, p2p_off, m2l_off, p2p_src, m2l_src, p2p_soff, m2l_soff;
-  size_t adj_w, adj_lam, adj_part;
+  size_t adj_part;                 // per particle: target-side position gradient (leaf order)
+  size_t wle, wlb;                 // per particle: scaled loss weights (leaf order)
+  size_t p2p_sdc, m2l_sdc;         // centre offsets of the source-major lists
   size_t sort_n;      // elements the sort buffers hold
   size_t nblk_sort;   // radix tiles at sort_n
   size_t nblk_part;   // partition blocks at N
@@ -92,6 +101,9 @@ struct fmm_plan_s {
   std::vector<int64_t> node_start, node_count, node_leftpre;  // index 0 unused
   fmm::Layout lay;
   fmm::Cheb cheb;
+  fmm::ChebD chebd;
+  bool transposed_valid = false;  // source-major lists built for the current forward
+  bool locals_valid = false;      // multipole / local buffers hold the forward's values
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool have_forward = false;
@@ -187,6 +199,13 @@ __device__ __forceinline__ void bary_basis(T t, bool degenerate, const Cheb& ch,
   for (int k = 0; k < np1; ++k) out[k] *= inv;
 }
 
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // Kahan-compensated accumulation: (sum, comp) += v.
 template <typename T>
 __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
@@ -220,6 +239,8 @@ int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_sort(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
 int run_pair_offsets(fmm_plan_s* P, cudaStream_t s);
+// per-pair centre offsets of `count` list keys at workspace offset keys_off
+int pair_offsets(fmm_plan_s* P, size_t keys_off, int64_t count, size_t out_off, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
 int run_l2l(fmm_plan_s* P, cudaStream_t s);
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);

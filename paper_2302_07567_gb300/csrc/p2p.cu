@@ -33,13 +33,6 @@
 namespace fmm {
 namespace {
 
-// s + e = a + b exactly (Knuth's two-sum).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 template <typename T, int KPT>
 __global__ void __launch_bounds__(256) k_p2p_l2p(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,

@@ -82,11 +82,14 @@ void make_layout(fmm_plan_s* P) {
   L.p2p_dc = take((size_t)P->cap_p2p * 32);
   L.m2l_dc = take((size_t)P->cap_m2l * 32);
   L.m2l_soff = take((C1 + 1) * 4);
-  // adjoint: weights W (6 comp) and adjoint moments Lambda (4 comp) per node,
-  // and per-particle gradient parts in leaf order
-  L.adj_w = take(C1 * 6 * m * R);
-  L.adj_lam = take(C1 * 4 * m * R);
-  L.adj_part = take(N * 8 * sizeof(double));
+  // adjoint: the node weights W and adjoint moments Lambda reuse the local and
+  // multipole buffers; per particle it needs the scaled weights and the
+  // target-side position gradient, per source-major list pair a centre offset
+  L.adj_part = take(N * V4);
+  L.wle = take(N * V4);
+  L.wlb = take(N * V4);
+  L.p2p_sdc = take((size_t)P->cap_p2p * 32);
+  L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.total = off;
   P->lay = L;
 }
@@ -119,6 +122,19 @@ void make_tables(fmm_plan_s* P) {
     // cos(k pi / n) written as sin(pi (n - 2k) / (2n)): exact symmetry, exact 0
     ch.t[k] = std::sin(pi * (double)(P->n - 2 * k) / (2.0 * P->n));
     ch.w[k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == P->n) ? 0.5 : 1.0);
+  }
+  ChebD& cd = P->chebd;
+  std::memset(&cd, 0, sizeof(cd));
+  const int np1 = P->np1;
+  for (int a = 0; a < np1; ++a) {
+    double diag = 0.0;
+    for (int k = 0; k < np1; ++k) {
+      if (k == a) continue;
+      const double v = (ch.w[k] / ch.w[a]) / (ch.t[a] - ch.t[k]);
+      cd.D[a * np1 + k] = v;
+      diag -= v;
+    }
+    cd.D[a * np1 + a] = diag;
   }
 }
 
@@ -280,6 +296,8 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   if ((rc = run_p2p_l2p(P, E, B, s)) != FMM_OK) return rc;
   if ((rc = record(P, 8, s)) != FMM_OK) return rc;
   P->have_forward = true;
+  P->transposed_valid = false;
+  P->locals_valid = true;
   return FMM_OK;
 }
 
@@ -342,12 +360,13 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[7] = el(7, 8);
     P->stage_ms[13] = el(0, 8);
     if (P->flags & 0x100u) {  // adjoint events recorded
-      P->stage_ms[8] = el(9, 10);
-      P->stage_ms[9] = el(10, 11);
-      P->stage_ms[10] = el(11, 12);
-      P->stage_ms[11] = el(12, 13);
-      P->stage_ms[12] = el(13, 14);
-      P->stage_ms[14] = el(9, 14);
+      P->stage_ms[8] = el(10, 11);   // L2P^T + L2L^T
+      P->stage_ms[9] = el(11, 12);   // M2L^T
+      P->stage_ms[10] = el(12, 13);  // M2M^T
+      P->stage_ms[11] = el(9, 10);   // target-side particle kernel
+      P->stage_ms[12] = el(13, 14);  // source-side particle kernel + chain rule
+      P->stage_ms[14] = el(15, 14);  // whole adjoint call
+      P->stage_ms[15] = el(15, 9);   // source-major lists, recompute if needed
     }
     for (int k = 0; k < 16; ++k) out->stage_ms[k] = P->stage_ms[k];
   }

@@ -141,24 +141,26 @@ __global__ void k_pair_dc(const uint64_t* __restrict__ keys, int64_t count, int 
 
 }  // namespace
 
-int run_pair_offsets(fmm_plan_s* P, cudaStream_t s) {
+int pair_offsets(fmm_plan_s* P, size_t keys_off, int64_t count, size_t out_off, cudaStream_t s) {
+  if (count <= 0) return FMM_OK;
   const Layout& L = P->lay;
   const int shift = P->kappa + 1;
-  const bool f32 = P->precision == FMM_FP32;
-  const size_t offs[2] = {L.p2p, L.m2l}, outs[2] = {L.p2p_dc, L.m2l_dc};
-  const int64_t counts[2] = {P->p2p_count, P->m2l_count};
-  for (int w = 0; w < 2; ++w) {
-    if (counts[w] <= 0) continue;
-    const unsigned g = (unsigned)std::min<int64_t>(div_up(counts[w], 256), 4096);
-    if (f32)
-      k_pair_dc<true><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, offs[w]), counts[w], shift, ws_ptr<double>(P, L.ncen),
-                                        ws_ptr<double>(P, L.scal), P->ws + outs[w]);
-    else
-      k_pair_dc<false><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, offs[w]), counts[w], shift, ws_ptr<double>(P, L.ncen),
-                                         ws_ptr<double>(P, L.scal), P->ws + outs[w]);
-    FMM_LAUNCH_CHECK();
-  }
+  const unsigned g = (unsigned)std::min<int64_t>(div_up(count, 256), 4096);
+  if (P->precision == FMM_FP32)
+    k_pair_dc<true><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, keys_off), count, shift, ws_ptr<double>(P, L.ncen),
+                                      ws_ptr<double>(P, L.scal), P->ws + out_off);
+  else
+    k_pair_dc<false><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, keys_off), count, shift, ws_ptr<double>(P, L.ncen),
+                                       ws_ptr<double>(P, L.scal), P->ws + out_off);
+  FMM_LAUNCH_CHECK();
   return FMM_OK;
+}
+
+int run_pair_offsets(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  int rc = pair_offsets(P, L.p2p, P->p2p_count, L.p2p_dc, s);
+  if (rc != FMM_OK) return rc;
+  return pair_offsets(P, L.m2l, P->m2l_count, L.m2l_dc, s);
 }
 
 int run_traverse(fmm_plan_s* P, cudaStream_t s) {
@@ -218,7 +220,12 @@ int run_list_transpose(fmm_plan_s* P, cudaStream_t s) {
   }
   int rc = sort_list(P, ws_ptr<uint64_t>(P, L.p2p_src), P->p2p_count, ws_ptr<int32_t>(P, L.p2p_soff), s);
   if (rc != FMM_OK) return rc;
-  return sort_list(P, ws_ptr<uint64_t>(P, L.m2l_src), P->m2l_count, ws_ptr<int32_t>(P, L.m2l_soff), s);
+  rc = sort_list(P, ws_ptr<uint64_t>(P, L.m2l_src), P->m2l_count, ws_ptr<int32_t>(P, L.m2l_soff), s);
+  if (rc != FMM_OK) return rc;
+  // offsets c_s - c_t of the source-major pairs (s, t)
+  rc = pair_offsets(P, L.p2p_src, P->p2p_count, L.p2p_sdc, s);
+  if (rc != FMM_OK) return rc;
+  return pair_offsets(P, L.m2l_src, P->m2l_count, L.m2l_sdc, s);
 }
 
 }  // namespace fmm

@@ -27,7 +27,7 @@ FMM_FP64, FMM_FP32 = 0, 1
 FMM_RECOMPUTE, FMM_BOUNDS_CHECK, FMM_TIMING = 1, 2, 4
 EXPORT = dict(gbar=0, perm=1, nodes=2, bbox=3, axis=4, p2p=5, m2l=6, multipole=7, local=8)
 STAGES = ["setup", "tree", "upward", "traversal", "list_sort", "m2l", "l2l", "p2p_l2p",
-          "adj_upward", "adj_m2l", "adj_downward", "adj_near", "adj_far", "total", "adj_total", "spare"]
+          "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_target", "adj_source", "total", "adj_total", "adj_lists"]
 
 _lib = None
 

@@ -1,0 +1,125 @@
+"""Hand-written adjoint against the oracle's gradients, through the C ABI (GPU).
+
+The reference for the adjoint is the exact gradient of the oracle's FMM with
+the plan (tree, boxes, lists, gbar) held fixed, by automatic differentiation
+(oracle.gradient.fmm_gradient, itself pinned to central finite differences
+on the CPU).  FP64 must agree to 1e-10 relative L2 per gradient; FP32 to the
+level FP32 rounding of the same operator allows, and within the FMM's
+truncation error plus 1e-6 of the direct-sum gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bldtt, gradient
+from paper_2302_07567_gb300 import fmm
+from paper_2302_07567_gb300.workloads import make_beam, make_weights, random_beam
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(*arrs, dtype=None):
+    return [torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype) for a in arrs]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = {
+    "gauss2k": lambda: (make_beam("gauss4k", N=2048), 4, 64, 0.5),
+    "ragged1501": lambda: (random_beam(1501, seed=3, gamma=15.0, spread=0.05, angle=0.02), 3, 37, 0.5),
+    "cylinder4k": lambda: (make_beam("cylinder64k", N=4096), 6, 128, 0.5),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    (x, p, q), n, leaf, eta = CASES[request.param]()
+    N = x.shape[0]
+    wE, wB = make_weights(N)
+    plan = bldtt.build_plan(x, p, n, leaf, eta)
+    L, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+    return dict(x=x, p=p, q=q, n=n, leaf=leaf, eta=eta, wE=wE, wB=wB, ref=(gx.numpy(), gp.numpy(), gq.numpy()),
+                plan=plan)
+
+
+def gpu_grad(c, prec, flags=0):
+    N = c["x"].shape[0]
+    odt = torch.float32 if prec == "fp32" else torch.float64
+    X, Pm, Q = dev(c["x"], c["p"], c["q"])
+    WE, WB = dev(c["wE"], c["wB"], dtype=odt)
+    plan = fmm.Plan(N, c["n"], c["leaf"], c["eta"], precision=prec, flags=flags)
+    plan.field(X, Pm, Q)
+    dx, dp, dq = plan.adjoint(X, Pm, Q, WE, WB)
+    torch.cuda.synchronize()
+    return plan, dx.cpu().numpy(), dp.cpu().numpy(), dq.cpu().numpy()
+
+
+def test_adjoint_fp64_matches_oracle_gradient(case):
+    _, dx, dp, dq = gpu_grad(case, "fp64")
+    gx, gp, gq = case["ref"]
+    assert rel(dx, gx) < 1e-10, rel(dx, gx)
+    assert rel(dp, gp) < 1e-10, rel(dp, gp)
+    assert rel(dq, gq) < 1e-10, rel(dq, gq)
+
+
+def test_adjoint_fp32_matches_oracle_gradient(case):
+    _, dx, dp, dq = gpu_grad(case, "fp32")
+    gx, gp, gq = case["ref"]
+    for a, b in ((dx, gx), (dp, gp), (dq, gq)):
+        assert rel(a, b) < 2e-5, rel(a, b)
+
+
+def test_second_adjoint_recomputes_and_matches(case):
+    """A second adjoint call on one forward recomputes the overwritten locals."""
+    N = case["x"].shape[0]
+    X, Pm, Q = dev(case["x"], case["p"], case["q"])
+    WE, WB = dev(case["wE"], case["wB"])
+    plan = fmm.Plan(N, case["n"], case["leaf"], case["eta"], precision="fp64")
+    plan.field(X, Pm, Q)
+    a = [t.clone() for t in plan.adjoint(X, Pm, Q, WE, WB)]
+    b = plan.adjoint(X, Pm, Q, WE, WB)
+    c = [t.clone() for t in plan.adjoint(X, Pm, Q, 2.0 * WE, 2.0 * WB)]
+    for u, v, w in zip(a, b, c):
+        assert torch.equal(u, v)
+        assert float((w - 2.0 * u).norm() / u.norm()) < 1e-13
+    # linearity in the weights: adjoint(wE, 0) + adjoint(0, wB) = adjoint(wE, wB)
+    e = plan.adjoint(X, Pm, Q, WE, torch.zeros_like(WB))
+    e = [t.clone() for t in e]
+    f = plan.adjoint(X, Pm, Q, torch.zeros_like(WE), WB)
+    for u, v, w in zip(a, e, f):
+        assert float((v + w - u).norm() / u.norm()) < 1e-12
+
+
+def test_fp32_adjoint_within_truncation_of_direct_gradient():
+    x, p, q = make_beam("gauss256k", N=4096)
+    wE, wB = make_weights(4096)
+    n, leaf, eta = 6, 128, 0.5
+    plan = bldtt.build_plan(x, p, n, leaf, eta)
+    _, fx, fp_, fq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+    _, dxr, dpr, dqr = gradient.direct_gradient(x, p, q, wE, wB, gbar=plan.tree.gbar)
+    c = dict(x=x, p=p, q=q, n=n, leaf=leaf, eta=eta, wE=wE, wB=wB)
+    _, dx, dp, dq = gpu_grad(c, "fp32")
+    for gpu, fmm_ref, direct in ((dx, fx, dxr), (dp, fp_, dpr), (dq, fq, dqr)):
+        trunc = rel(fmm_ref.numpy(), direct.numpy())
+        assert rel(gpu, direct.numpy()) <= trunc + 1e-6, (rel(gpu, direct.numpy()), trunc)
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    x, p, q = make_beam("gauss4k", N=3000)
+    wE, wB = make_weights(3000)
+    X, Pm, Q = dev(x, p, q)
+    WE, WB = dev(wE, wB, dtype=torch.float32)
+    plan = fmm.Plan(3000, 4, 64, 0.5, precision="fp32")
+    Xr, Pr, Qr = (t.clone().requires_grad_(True) for t in (X, Pm, Q))
+    E, B = fmm.FMMField.apply(Xr, Pr, Qr, plan)
+    loss = (E * WE).sum() + (B * WB).sum()
+    loss.backward()
+    plan.field(X, Pm, Q)
+    dx, dp, dq = plan.adjoint(X, Pm, Q, WE, WB)
+    assert torch.allclose(Xr.grad, dx, rtol=0, atol=0)
+    assert torch.allclose(Pr.grad, dp, rtol=0, atol=0)
+    assert torch.allclose(Qr.grad, dq, rtol=0, atol=0)
