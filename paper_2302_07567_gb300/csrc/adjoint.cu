@@ -243,6 +243,150 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
   }
 }
 
+// FP32 M2L^T specialised on NP1 = n + 1 (eta <= 1/2), the counterpart of
+// k_m2l_fast: a thread owns source points nu with fixed (nu1, nu2), keeps
+// R_x[mu1], R_x^2 and R_y[mu2], R_y^2 for R = xi_S,mu - xi_s,nu in registers
+// and regroups the sums inside the mu1 loop (R_y, R_z constant there):
+//   Lambda^a  += sum r3 W^E_x R_x + R_y sum r3 W^E_y + R_z sum r3 W^E_z
+//   Lambda^b  += (R_y sum r3 W^B_z - R_z sum r3 W^B_y,
+//                 R_z sum r3 W^B_x - sum r3 W^B_z R_x,
+//                 sum r3 W^B_y R_x - R_y sum r3 W^B_x)
+template <int NP1, int G>
+__global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_adj_m2l_fast(const uint64_t* __restrict__ keys,
+                                                                  const int32_t* __restrict__ off, int shift,
+                                                                  const NodeGeo* __restrict__ geo,
+                                                                  const float4* __restrict__ sdc, Cheb ch,
+                                                                  const float* __restrict__ W, float* __restrict__ Lam) {
+  constexpr int KPT = (NP1 + G - 1) / G;
+  constexpr int NT = NP1 * NP1 * G;
+  constexpr int m = NP1 * NP1 * NP1;
+  __shared__ float4 swa[m];            // (W^E_x, W^E_y, W^E_z, W^B_x)
+  __shared__ float2 swb[m];            // (W^B_y, W^B_z)
+  __shared__ float syz[NP1];           // target-cluster point offsets along z
+  __shared__ float sacc[KPT][8][NT];   // Kahan sums and compensations
+  const int64_t s = (int64_t)blockIdx.x + 1;
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const int b = off[s], e = off[s + 1];
+  const NodeGeo gs = geo[s];
+  const int tid = threadIdx.x;
+  const int nu12 = tid % (NP1 * NP1), g = tid / (NP1 * NP1);
+  const int nu1 = nu12 % NP1, nu2 = nu12 / NP1;
+  const float xs = (float)(gs.h[0] * ch.t[nu1]), ys = (float)(gs.h[1] * ch.t[nu2]);
+  float zs[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int nu3 = g + k * G;
+    zs[k] = (float)(gs.h[2] * ch.t[nu3 < NP1 ? nu3 : 0]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sacc[k][c][tid] = 0.f;
+  }
+  for (int it = b; it < e; ++it) {
+    const int64_t S = (int64_t)(keys[it] & mask);
+    const float4 dh = sdc[2 * it];  // c_s - c_S
+    const NodeGeo gS = geo[S];
+    const float hx = (float)gS.h[0], hy = (float)gS.h[1];
+    __syncthreads();
+    const float* Ws = W + (size_t)S * 6 * m;
+    for (int o = tid; o < m; o += NT) {
+      swa[o] = make_float4(Ws[o], Ws[m + o], Ws[2 * m + o], Ws[3 * m + o]);
+      swb[o] = make_float2(Ws[4 * m + o], Ws[5 * m + o]);
+    }
+    if (tid < NP1) syz[tid] = (float)(gS.h[2] * ch.t[tid]);
+    __syncthreads();
+    const float X = dh.x + xs, Y = dh.y + ys;  // this point relative to the target-cluster centre
+    float Rx[NP1], Dx[NP1], Ry[NP1], Dy[NP1];
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) {
+      Rx[k] = hx * (float)ch.t[k] - X;
+      Dx[k] = Rx[k] * Rx[k];
+      Ry[k] = hy * (float)ch.t[k] - Y;
+      Dy[k] = Ry[k] * Ry[k];
+    }
+    float Z[KPT], part[KPT][4];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      Z[k] = dh.z + zs[k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[k][c] = 0.f;
+    }
+    for (int m3 = 0; m3 < NP1; ++m3) {
+      const float yz = syz[m3];
+      float rz[KPT], dz[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        rz[k] = yz - Z[k];
+        dz[k] = rz[k] * rz[k];
+      }
+      const int row = m3 * NP1 * NP1;
+#pragma unroll
+      for (int m2 = 0; m2 < NP1; ++m2) {
+        float dyz[KPT], T1[KPT], T2[KPT], T3[KPT], T4[KPT], T5[KPT], T5R[KPT], T6[KPT], T6R[KPT];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          dyz[k] = Dy[m2] + dz[k];
+          T1[k] = T2[k] = T3[k] = T4[k] = T5[k] = T5R[k] = T6[k] = T6R[k] = 0.f;
+        }
+#pragma unroll
+        for (int m1 = 0; m1 < NP1; ++m1) {
+          const float4 wa = swa[row + m2 * NP1 + m1];
+          const float2 wb = swb[row + m2 * NP1 + m1];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            const float d = fmaxf(Dx[m1] + dyz[k], 5.169878828456423e-26f);
+            const float inv = rsqrtf(d);
+            const float r3 = inv * inv * inv;
+            T1[k] = fmaf(wa.x * Rx[m1], r3, T1[k]);
+            T2[k] = fmaf(wa.y, r3, T2[k]);
+            T3[k] = fmaf(wa.z, r3, T3[k]);
+            T4[k] = fmaf(wa.w, r3, T4[k]);
+            const float w5 = wb.x * r3;
+            T5[k] += w5;
+            T5R[k] = fmaf(w5, Rx[m1], T5R[k]);
+            const float w6 = wb.y * r3;
+            T6[k] += w6;
+            T6R[k] = fmaf(w6, Rx[m1], T6R[k]);
+          }
+        }
+        const float ry = Ry[m2];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          part[k][0] += T1[k] + ry * T2[k] + rz[k] * T3[k];
+          part[k][1] += ry * T6[k] - rz[k] * T5[k];
+          part[k][2] += rz[k] * T4[k] - T6R[k];
+          part[k][3] += T5R[k] - ry * T4[k];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float sum = sacc[k][c][tid], comp = sacc[k][4 + c][tid];
+        kahan_add(sum, comp, part[k][c]);
+        sacc[k][c][tid] = sum;
+        sacc[k][4 + c][tid] = comp;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int nu3 = g + k * G;
+    if (nu3 >= NP1) continue;
+    const int nu = nu1 + NP1 * (nu2 + NP1 * nu3);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = sacc[k][c][tid];
+  }
+}
+
+template <int NP1, int G>
+int launch_adj_m2l_fast(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  k_adj_m2l_fast<NP1, G><<<(unsigned)P->C, NP1 * NP1 * G, 0, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.m2l_sdc), P->cheb, ws_ptr<float>(P, L.local), ws_ptr<float>(P, L.mpole));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
 // Near field at the targets (J u over the target-major P2P list) plus the far
 // field at the targets (grad of the forward's cumulative local); writes the
 // target-side dL/dx' of every particle (leaf order).
@@ -682,6 +826,15 @@ int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
 
 template <typename T>
 int adj_m2l(fmm_plan_s* P, cudaStream_t s) {
+  if (std::is_same<T, float>::value && P->eta <= 0.5) {
+    switch (P->np1) {
+      case 3: return launch_adj_m2l_fast<3, 3>(P, s);
+      case 5: return launch_adj_m2l_fast<5, 5>(P, s);
+      case 7: return launch_adj_m2l_fast<7, 4>(P, s);
+      case 9: return launch_adj_m2l_fast<9, 3>(P, s);
+      default: break;
+    }
+  }
   // the same thread shape rule as the forward M2L
   int best_nt = 256, best_k = 4;
   int64_t best_waste = -1, best_passes = 0;
@@ -789,15 +942,13 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
   if (P->kappa > 0) {
     if ((rc = l2pt<T>(P, s)) != FMM_OK) return rc;
-    for (int l = P->kappa - 1; l >= 0; --l)  // L2L^T: W up the tree (M2M form)
-      if ((rc = launch_transfer<T, 6, true>(P, l, ws_ptr<T>(P, L.local), s)) != FMM_OK) return rc;
+    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.local), s)) != FMM_OK) return rc;  // L2L^T: W up
   }
   if ((rc = record(P, 11, s)) != FMM_OK) return rc;
   if (P->kappa > 0 && (rc = adj_m2l<T>(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 12, s)) != FMM_OK) return rc;
   if (P->kappa > 0) {
-    for (int l = 0; l < P->kappa; ++l)  // M2M^T: Lambda down the tree (L2L form)
-      if ((rc = launch_transfer<T, 4, false>(P, l, ws_ptr<T>(P, L.mpole), s)) != FMM_OK) return rc;
+    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.mpole), s)) != FMM_OK) return rc;  // M2M^T: Lambda down
   }
   if ((rc = record(P, 13, s)) != FMM_OK) return rc;
   if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, false, s)) != FMM_OK) return rc;

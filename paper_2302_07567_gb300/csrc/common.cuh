@@ -78,7 +78,7 @@ struct Layout {
   size_t nstart, ncount, nleftpre, nlo, nhi, naxis, nmed, ncen, ndiam, ngeo;
   size_t perm, px, pb, pl;         // leaf-order particles (pl: low parts, FP32 only)
   size_t p2p_dc, m2l_dc;           // per list pair: centre offset c_t - c_s as (hi, lo)
-  size_t mpole, local, srct;
+  size_t mpole, local, srct, tmat;
   size_t front0, front1, p2p, m2l, p2p_off, m2l_off, p2p_src, m2l_src, p2p_soff, m2l_soff;
   size_t adj_part;                 // per particle: target-side position gradient (leaf order)
   size_t wle, wlb;                 // per particle: scaled loss weights (leaf order)
@@ -253,9 +253,11 @@ int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* val
                int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
                cudaStream_t s, bool* in_alt);
 int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
-// separable transfer between the nodes of `level` and their children (see upward.cu)
+// per-node 1-D transfer matrices, and the separable transfers over all
+// levels (see transfer.cu)
+int run_tmats(fmm_plan_s* P, cudaStream_t s);
 template <typename T, int NC, bool UP>
-int launch_transfer(fmm_plan_s* P, int level, T* buf, cudaStream_t s);
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
 int64_t scan_tmp_words(int64_t n);
 }  // namespace fmm

@@ -100,6 +100,155 @@ __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, 
   }
 }
 
+// FP32 M2L specialised on the points per axis NP1 = n + 1 (for eta <= 1/2).
+//
+// A thread owns the target points mu = (mu1, mu2, mu3) with fixed (mu1, mu2)
+// and mu3 = g, g + G, ... (KPT of them).  For a source s the separation
+// R = xi_t,mu - xi_s,nu splits per axis: R_x depends on (mu1, nu1) only, so
+// the thread keeps R_x[nu1], R_x^2 and R_y[nu2], R_y^2 in registers, and
+// |R|^2 = R_x^2[nu1] + (R_y^2[nu2] + R_z^2[nu3]) costs one add per point
+// pair.  Inside the nu1 loop R_y and R_z are constant, so the sums regroup:
+//   E  += (sum a r3 R_x,  R_y sum a r3,  R_z sum a r3)
+//   B  += (R_z sum b_y r3 - R_y sum b_z r3,  sum b_z r3 R_x - R_z sum b_x r3,
+//          R_y sum b_x r3 - sum b_y r3 R_x)
+// with seven running sums per target point (13 FP32 operations and one
+// rsqrt per point pair instead of 21).  The same terms are added, in the same
+// per-source groups, as in the generic kernel.  For eta <= 1/2 admissible
+// boxes are disjoint (r_t + r_s < d), so |R|^2 > 0 and a clamp replaces the
+// zero mask.  The running Kahan sums across sources live in shared memory.
+template <int NP1, int G>
+__global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_m2l_fast(const uint64_t* __restrict__ keys,
+                                                              const int32_t* __restrict__ off, int shift,
+                                                              const NodeGeo* __restrict__ geo,
+                                                              const float4* __restrict__ pdc, Cheb ch,
+                                                              const float* __restrict__ M, float* __restrict__ Lout) {
+  constexpr int KPT = (NP1 + G - 1) / G;
+  constexpr int NT = NP1 * NP1 * G;
+  constexpr int m = NP1 * NP1 * NP1;
+  __shared__ float4 sm[m];              // source effective masses (a, b~x, b~y, b~z)
+  __shared__ float syz[NP1];            // source point offsets along z
+  __shared__ float sacc[KPT][12][NT];   // Kahan sums and compensations
+  const int64_t t = (int64_t)blockIdx.x + 1;
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const int b = off[t], e = off[t + 1];
+  const NodeGeo gt = geo[t];
+  const int tid = threadIdx.x;
+  const int mu12 = tid % (NP1 * NP1), g = tid / (NP1 * NP1);
+  const int mu1 = mu12 % NP1, mu2 = mu12 / NP1;
+  const float xt = (float)(gt.h[0] * ch.t[mu1]), yt = (float)(gt.h[1] * ch.t[mu2]);
+  float zt[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int mu3 = g + k * G;
+    zt[k] = (float)(gt.h[2] * ch.t[mu3 < NP1 ? mu3 : 0]);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) sacc[k][c][tid] = 0.f;
+  }
+  for (int it = b; it < e; ++it) {
+    const int64_t s = (int64_t)(keys[it] & mask);
+    const float4 dh = pdc[2 * it];
+    const NodeGeo gs = geo[s];
+    const float hsx = (float)gs.h[0], hsy = (float)gs.h[1];
+    __syncthreads();
+    const float* Ms = M + (size_t)s * 4 * m;
+    for (int o = tid; o < m; o += NT) sm[o] = make_float4(Ms[o], Ms[m + o], Ms[2 * m + o], Ms[3 * m + o]);
+    if (tid < NP1) syz[tid] = (float)(gs.h[2] * ch.t[tid]);
+    __syncthreads();
+    const float X = dh.x + xt, Y = dh.y + yt;
+    float Rx[NP1], Dx[NP1], Ry[NP1], Dy[NP1];
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) {
+      Rx[k] = X - hsx * (float)ch.t[k];
+      Dx[k] = Rx[k] * Rx[k];
+      Ry[k] = Y - hsy * (float)ch.t[k];
+      Dy[k] = Ry[k] * Ry[k];
+    }
+    float Z[KPT], part[KPT][6];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      Z[k] = dh.z + zt[k];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) part[k][c] = 0.f;
+    }
+    for (int n3 = 0; n3 < NP1; ++n3) {
+      const float yz = syz[n3];
+      float rz[KPT], dz[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        rz[k] = Z[k] - yz;
+        dz[k] = rz[k] * rz[k];
+      }
+      const float4* row = sm + n3 * NP1 * NP1;
+#pragma unroll
+      for (int n2 = 0; n2 < NP1; ++n2) {
+        float dyz[KPT], Ta[KPT], TaR[KPT], Tbx[KPT], Tby[KPT], TbyR[KPT], Tbz[KPT], TbzR[KPT];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          dyz[k] = Dy[n2] + dz[k];
+          Ta[k] = TaR[k] = Tbx[k] = Tby[k] = TbyR[k] = Tbz[k] = TbzR[k] = 0.f;
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < NP1; ++n1) {
+          const float4 src = row[n2 * NP1 + n1];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            const float d = fmaxf(Dx[n1] + dyz[k], 5.169878828456423e-26f);
+            const float inv = rsqrtf(d);
+            const float r3 = inv * inv * inv;
+            const float ar3 = src.x * r3;
+            Ta[k] += ar3;
+            TaR[k] = fmaf(ar3, Rx[n1], TaR[k]);
+            Tbx[k] = fmaf(src.y, r3, Tbx[k]);
+            const float byr3 = src.z * r3;
+            Tby[k] += byr3;
+            TbyR[k] = fmaf(byr3, Rx[n1], TbyR[k]);
+            const float bzr3 = src.w * r3;
+            Tbz[k] += bzr3;
+            TbzR[k] = fmaf(bzr3, Rx[n1], TbzR[k]);
+          }
+        }
+        const float ry = Ry[n2];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          part[k][0] += TaR[k];
+          part[k][1] += ry * Ta[k];
+          part[k][2] += rz[k] * Ta[k];
+          part[k][3] += rz[k] * Tby[k] - ry * Tbz[k];
+          part[k][4] += TbzR[k] - rz[k] * Tbx[k];
+          part[k][5] += ry * Tbx[k] - TbyR[k];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float sum = sacc[k][c][tid], comp = sacc[k][6 + c][tid];
+        kahan_add(sum, comp, part[k][c]);
+        sacc[k][c][tid] = sum;
+        sacc[k][6 + c][tid] = comp;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int mu3 = g + k * G;
+    if (mu3 >= NP1) continue;
+    const int mu = mu1 + NP1 * (mu2 + NP1 * mu3);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + mu] = sacc[k][c][tid];
+  }
+}
+
+template <int NP1, int G>
+int launch_fast(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  k_m2l_fast<NP1, G><<<(unsigned)P->C, NP1 * NP1 * G, 0, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.m2l_dc), P->cheb, ws_ptr<float>(P, L.mpole), ws_ptr<float>(P, L.local));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
 // Block shape: threads nt <= 256 (a multiple of 32) owning KPT points each,
 // chosen to waste the fewest thread slots, then to need the fewest passes.
 void pick_shape(int m, int* nt, int* kpt) {
@@ -152,6 +301,15 @@ int m2l_t(fmm_plan_s* P, cudaStream_t s) {
 }  // namespace
 
 int run_m2l(fmm_plan_s* P, cudaStream_t s) {
+  if (P->precision == FMM_FP32 && P->eta <= 0.5) {
+    switch (P->np1) {
+      case 3: return launch_fast<3, 3>(P, s);
+      case 5: return launch_fast<5, 5>(P, s);
+      case 7: return launch_fast<7, 4>(P, s);
+      case 9: return launch_fast<9, 3>(P, s);
+      default: break;
+    }
+  }
   return P->precision == FMM_FP32 ? m2l_t<float>(P, s) : m2l_t<double>(P, s);
 }
 

@@ -70,6 +70,7 @@ void make_layout(fmm_plan_s* P) {
   L.mpole = take(C1 * 4 * m * R);
   L.local = take(C1 * 6 * m * R);
   L.srct = take(C1 * m * 2 * V4);
+  L.tmat = take(C1 * 3 * (size_t)P->np1 * P->np1 * R);
   L.front0 = take((size_t)P->cap_frontier * 8);
   L.front1 = take((size_t)P->cap_frontier * 8);
   L.p2p = take((size_t)P->cap_p2p * 8);

@@ -1,13 +1,10 @@
-// Node geometry, particle preparation, upward pass (P2M Alg. 3, M2M Alg. 4 /
-// Eq. 2.7, Alg. 5) and the separable transfer that also serves L2L (Alg. 13 /
-// Eq. 2.9).
+// Node geometry, particle preparation and the upward pass (P2M Alg. 3, then
+// M2M Alg. 4 / Eq. 2.7 over all levels, Alg. 5).
 //
 // The interpolation points of a box side [a, b] are xi_k = c + h t_k with
 // t_k the Chebyshev points of the second kind; the Lagrange basis is
 // evaluated in the barycentric form in the normalised variable t = (x - c)/h.
-// A side of zero width carries the basis l_0 = 1.  The transfer matrices
-// T_d[nu][nu'] = l^d_{parent, nu}(xi^d_{child, nu'}) are formed in FP64 and
-// applied one axis at a time, (n+1)^4 multiply-adds per axis and component.
+// A side of zero width carries the basis l_0 = 1.
 #include "common.cuh"
 
 namespace fmm {
@@ -176,96 +173,6 @@ __global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __res
   }
 }
 
-// out[a,b,c] = sum_{a',b',c'} Mx[a][a'] My[b][b'] Mz[c][c'] in[a',b',c'] (x fastest),
-// matrices stored row-major [np1][np1] in shared memory.
-template <typename T>
-__device__ void apply3(const T* Mx, const T* My, const T* Mz, const T* in, T* tmp1, T* tmp2,
-                       T* out, int np1, int m, bool accumulate) {
-  for (int o = threadIdx.x; o < m; o += blockDim.x) {
-    const int a = o % np1, r = o / np1;
-    T s = T(0);
-    for (int k = 0; k < np1; ++k) s += Mx[a * np1 + k] * in[r * np1 + k];
-    tmp1[o] = s;
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < m; o += blockDim.x) {
-    const int a = o % np1, b = (o / np1) % np1, c = o / (np1 * np1);
-    T s = T(0);
-    for (int k = 0; k < np1; ++k) s += My[b * np1 + k] * tmp1[(c * np1 + k) * np1 + a];
-    tmp2[o] = s;
-  }
-  __syncthreads();
-  const int pl = np1 * np1;
-  for (int o = threadIdx.x; o < m; o += blockDim.x) {
-    const int ab = o % pl, c = o / pl;
-    T s = T(0);
-    for (int k = 0; k < np1; ++k) s += Mz[c * np1 + k] * tmp2[k * pl + ab];
-    out[o] = accumulate ? out[o] + s : s;
-  }
-  __syncthreads();
-}
-
-// Transfer between a parent at `level` and its two children, NC components.
-// UP (M2M, Eq. 2.7):   parent[nu]  = sum_children sum_nu' T[nu][nu'] child[nu']
-// DOWN (L2L, Eq. 2.9): child[mu'] += sum_mu T[mu][mu'] parent[mu]
-// with T = T_x (x) T_y (x) T_z, T_d[nu][nu'] = l^d_{parent,nu}(xi^d_{child,nu'}),
-// formed in FP64 from the physical boxes: xi = c + h t_k, t = (xi - c_p) / h_p.
-template <typename T, int NC, bool UP>
-__global__ void k_transfer(int level, const double* __restrict__ nlo, const double* __restrict__ nhi, Cheb ch,
-                           int m, T* __restrict__ buf) {
-  extern __shared__ unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int np1 = ch.np1, q = np1 * np1;
-  T* mat = sm;                 // [2 children][3 axes][np1][np1], stored as used by apply3
-  T* in = mat + 6 * q;
-  T* t1 = in + m;
-  T* t2 = t1 + m;
-  T* acc = t2 + m;
-  const int64_t parent = ((int64_t)1 << level) + blockIdx.x;
-  for (int job = threadIdx.x; job < 6 * np1; job += blockDim.x) {
-    const int child = job / (3 * np1), d = (job / np1) % 3, nup = job % np1;
-    const int64_t cn = 2 * parent + child;
-    const double clo = nlo[3 * cn + d], chi = nhi[3 * cn + d];
-    const double plo = nlo[3 * parent + d], phi = nhi[3 * parent + d];
-    const double xc = chi > clo ? (clo + chi) / 2.0 + ((chi - clo) / 2.0) * ch.t[nup] : clo;
-    const bool deg = !(phi > plo);
-    const double t = deg ? 0.0 : (xc - (plo + phi) / 2.0) / ((phi - plo) / 2.0);
-    double b[kMaxNp1];
-    bary_basis<double>(t, deg, ch, b);
-    T* Md = mat + (child * 3 + d) * q;
-    for (int nu = 0; nu < np1; ++nu) {
-      // UP contracts over nu' (second index); DOWN over nu: store the transpose
-      if (UP) Md[nu * np1 + nup] = (T)b[nu];
-      else Md[nup * np1 + nu] = (T)b[nu];
-    }
-  }
-  __syncthreads();
-  for (int c = 0; c < NC; ++c) {
-    for (int child = 0; child < 2; ++child) {
-      const int64_t cn = 2 * parent + child;
-      const T* src = buf + ((size_t)(UP ? cn : parent) * NC + c) * m;
-      for (int o = threadIdx.x; o < m; o += blockDim.x) in[o] = src[o];
-      __syncthreads();
-      const T* Mx = mat + (child * 3 + 0) * q;
-      const T* My = mat + (child * 3 + 1) * q;
-      const T* Mz = mat + (child * 3 + 2) * q;
-      if (UP) {
-        apply3<T>(Mx, My, Mz, in, t1, t2, acc, np1, m, child == 1);
-      } else {
-        T* dst = buf + ((size_t)cn * NC + c) * m;
-        apply3<T>(Mx, My, Mz, in, t1, t2, acc, np1, m, false);
-        for (int o = threadIdx.x; o < m; o += blockDim.x) dst[o] += acc[o];
-        __syncthreads();
-      }
-    }
-    if (UP) {
-      T* dst = buf + ((size_t)parent * NC + c) * m;
-      for (int o = threadIdx.x; o < m; o += blockDim.x) dst[o] = acc[o];
-      __syncthreads();
-    }
-  }
-}
-
 // M2L source table: per node and proxy point, (Y, a) and (b~, 0) with
 // Y = h o t_nu the point's offset from the box centre.
 template <typename T>
@@ -328,10 +235,8 @@ int upward_t(fmm_plan_s* P, cudaStream_t s) {
   }
   if (rc != FMM_OK) return rc;
   const Layout& L = P->lay;
-  for (int l = P->kappa - 1; l >= 0; --l) {
-    rc = launch_transfer<T, 4, true>(P, l, ws_ptr<T>(P, L.mpole), s);
-    if (rc != FMM_OK) return rc;
-  }
+  rc = run_transfer<T, 4, true>(P, ws_ptr<T>(P, L.mpole), s);  // M2M, all levels
+  if (rc != FMM_OK) return rc;
   const int64_t total = (P->C + 1) * (int64_t)P->m;
   k_srctab<T><<<(unsigned)std::min<int64_t>(div_up(total, 256), 8192), 256, 0, s>>>(
       ws_ptr<T>(P, L.mpole), ws_ptr<NodeGeo>(P, L.ngeo), P->C, P->cheb, P->m,
@@ -342,30 +247,6 @@ int upward_t(fmm_plan_s* P, cudaStream_t s) {
 
 }  // namespace
 
-template <typename T, int NC, bool UP>
-int launch_transfer(fmm_plan_s* P, int level, T* buf, cudaStream_t s) {
-  const size_t smem = (size_t)(6 * P->np1 * P->np1 + 4 * P->m) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_transfer<T, NC, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      200 * 1024));
-    attr_set = true;
-  }
-  k_transfer<T, NC, UP><<<(unsigned)(1u << level), 256, smem, s>>>(
-      level, ws_ptr<double>(P, P->lay.nlo), ws_ptr<double>(P, P->lay.nhi), P->cheb, P->m, buf);
-  FMM_LAUNCH_CHECK();
-  return FMM_OK;
-}
-
-template int launch_transfer<float, 4, true>(fmm_plan_s*, int, float*, cudaStream_t);
-template int launch_transfer<double, 4, true>(fmm_plan_s*, int, double*, cudaStream_t);
-template int launch_transfer<float, 6, false>(fmm_plan_s*, int, float*, cudaStream_t);
-template int launch_transfer<double, 6, false>(fmm_plan_s*, int, double*, cudaStream_t);
-template int launch_transfer<float, 6, true>(fmm_plan_s*, int, float*, cudaStream_t);
-template int launch_transfer<double, 6, true>(fmm_plan_s*, int, double*, cudaStream_t);
-template int launch_transfer<float, 4, false>(fmm_plan_s*, int, float*, cudaStream_t);
-template int launch_transfer<double, 4, false>(fmm_plan_s*, int, double*, cudaStream_t);
-
 int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s) {
   const Layout& L = P->lay;
   double* scal = ws_ptr<double>(P, L.scal);
@@ -375,6 +256,8 @@ int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, c
                                                           P->C, scal, ws_ptr<double>(P, L.ncen),
                                                           ws_ptr<double>(P, L.ndiam), ws_ptr<NodeGeo>(P, L.ngeo));
   FMM_LAUNCH_CHECK();
+  int rc = run_tmats(P, s);
+  if (rc != FMM_OK) return rc;
   const int gs = (int)std::min<int64_t>(8192, div_up(P->N, 256));
   if (P->precision == FMM_FP32) {
     k_prep<float><<<gs, 256, 0, s>>>(x, p, q, P->N, ws_ptr<int32_t>(P, L.perm), ws_ptr<int64_t>(P, L.nstart),
@@ -394,13 +277,8 @@ int run_upward(fmm_plan_s* P, cudaStream_t s) {
 }
 
 int run_l2l(fmm_plan_s* P, cudaStream_t s) {
-  for (int l = 0; l < P->kappa; ++l) {
-    int rc = P->precision == FMM_FP32
-                 ? launch_transfer<float, 6, false>(P, l, ws_ptr<float>(P, P->lay.local), s)
-                 : launch_transfer<double, 6, false>(P, l, ws_ptr<double>(P, P->lay.local), s);
-    if (rc != FMM_OK) return rc;
-  }
-  return FMM_OK;
+  return P->precision == FMM_FP32 ? run_transfer<float, 6, false>(P, ws_ptr<float>(P, P->lay.local), s)
+                                  : run_transfer<double, 6, false>(P, ws_ptr<double>(P, P->lay.local), s);
 }
 
 }  // namespace fmm
