@@ -252,6 +252,10 @@ int run_adjoint(fmm_plan_s* P, const double* x, const double* p, const double* q
 int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
                int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
                cudaStream_t s, bool* in_alt);
+// nbatch independent sorts of n keys each, batch k at keys + k * stride
+int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t stride,
+                       int nbatch, int64_t n, int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp,
+                       int64_t max_tiles, cudaStream_t s, bool* in_alt);
 int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
 // per-node 1-D transfer matrices, and the separable transfers over all
 // levels (see transfer.cu)

@@ -32,8 +32,8 @@ void make_layout(fmm_plan_s* P) {
   const size_t N = (size_t)P->N, C1 = (size_t)P->C + 1, m = (size_t)P->m;
   const size_t R = P->precision == FMM_FP32 ? sizeof(float) : sizeof(double);
   const size_t V4 = 4 * R;
-  const int64_t sort_n = std::max<int64_t>({P->N, P->cap_p2p, P->cap_m2l, 1});
-  const int64_t tiles = radix_tiles(sort_n);
+  const int64_t sort_n = std::max<int64_t>({3 * P->N, P->cap_p2p, P->cap_m2l, 1});
+  const int64_t tiles = radix_tiles(sort_n) + 3 * radix_tiles(P->N);  // batched presort or one list
   const int64_t nblk_part = div_up(P->N, 2048);
   L.sort_n = (size_t)sort_n;
   L.nblk_sort = (size_t)tiles;
@@ -45,8 +45,8 @@ void make_layout(fmm_plan_s* P) {
   L.qmax_part = take(1024 * sizeof(double));
   L.keys = take(sort_n * 8);
   L.keys_alt = take(sort_n * 8);
-  L.vals = take(N * 4);
-  L.vals_alt = take(N * 4);
+  L.vals = take(3 * N * 4);
+  L.vals_alt = take(3 * N * 4);
   L.hist = take((size_t)256 * tiles * 4);
   L.scan_tmp = take((size_t)scan_tmp_words(std::max<int64_t>(256 * tiles, nblk_part)) * 4 + 1024);
   L.A = take(3 * N * 4);

@@ -18,6 +18,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
+// up to this many tiles the scatter kernel forms its digit offsets itself
+constexpr int64_t kFusedTiles = 64;
 
 // Exclusive prefix of `v` over the block (blocked arrangement); returns the
 // block total through `total`.
@@ -88,10 +90,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* __restrict__ keys,
+// Digit histogram of one tile of one batch: hist[batch][digit][tile].
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* __restrict__ keys, int64_t stride,
                                                                int64_t n, int shift, int64_t ntiles,
                                                                uint32_t* __restrict__ hist) {
   __shared__ uint32_t cnt[256];
+  keys += blockIdx.y * stride;
+  hist += (int64_t)blockIdx.y * 256 * ntiles;
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -106,17 +111,41 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* 
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Stable scatter of one tile by its digit.  With `fused` the tile's digit
+// offsets are formed here from the raw histogram (few tiles); otherwise
+// `hist` already holds the exclusive scan over (digit, tile).
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
-    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, int shift,
-    int64_t ntiles, const uint32_t* __restrict__ hist, uint64_t* __restrict__ keys_out,
+    const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t stride, int64_t n, int shift,
+    int64_t ntiles, const uint32_t* __restrict__ hist, bool fused, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t wcnt[kSortWarps][256];
   __shared__ uint32_t run[256];
   __shared__ uint32_t gbase[256];
+  __shared__ uint32_t wt[33];
+  const int64_t boff = blockIdx.y * stride;
+  keys += boff;
+  keys_out += boff;
+  if (vals) {
+    vals += boff;
+    vals_out += boff;
+  }
+  hist += (int64_t)blockIdx.y * 256 * ntiles;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
   run[threadIdx.x] = 0;
-  gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  if (fused) {
+    const uint32_t* h = hist + (int64_t)threadIdx.x * ntiles;
+    uint32_t tot = 0, before = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const uint32_t c = h[t];
+      tot += c;
+      before += t < (int64_t)blockIdx.x ? c : 0u;
+    }
+    uint32_t all;
+    gbase[threadIdx.x] = block_exclusive_scan(tot, wt, all) + before;
+  } else {
+    gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  }
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   for (int r = 0; r < kSortRounds; ++r) {
@@ -177,21 +206,35 @@ int64_t radix_tiles(int64_t n) { return div_up(n > 0 ? n : 1, kSortTile); }
 int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
                int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
                cudaStream_t s, bool* in_alt) {
+  return radix_sort_batched(keys, keys_alt, vals, vals_alt, 0, 1, n, begin_bit, end_bit, hist, scan_tmp, max_tiles,
+                            s, in_alt);
+}
+
+int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t stride,
+                       int nbatch, int64_t n, int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp,
+                       int64_t max_tiles, cudaStream_t s, bool* in_alt) {
   *in_alt = false;
-  if (n <= 1) return FMM_OK;
-  int64_t nt = radix_tiles(n);
-  if (nt > max_tiles) return FMM_EINVAL;
+  if (n <= 1 || nbatch < 1) return FMM_OK;
+  const int64_t nt = radix_tiles(n);
+  if (nt * nbatch > max_tiles) return FMM_EINVAL;
+  const bool fused = nt <= kFusedTiles;
   uint64_t* k_in = keys;
   uint64_t* k_out = keys_alt;
   uint32_t* v_in = vals;
   uint32_t* v_out = vals_alt;
   bool alt = false;
+  const dim3 grid((unsigned)nt, (unsigned)nbatch);
   for (int b = begin_bit; b < end_bit; b += 8) {
-    k_radix_upsweep<<<(unsigned)nt, kSortThreads, 0, s>>>(k_in, n, b, nt, hist);
+    k_radix_upsweep<<<grid, kSortThreads, 0, s>>>(k_in, stride, n, b, nt, hist);
     FMM_LAUNCH_CHECK();
-    int rc = scan_exclusive(hist, hist, 256 * nt, scan_tmp, s);
-    if (rc != FMM_OK) return rc;
-    k_radix_downsweep<<<(unsigned)nt, kSortThreads, 0, s>>>(k_in, v_in, n, b, nt, hist, k_out, v_out);
+    if (!fused) {
+      for (int k = 0; k < nbatch; ++k) {
+        uint32_t* h = hist + (int64_t)k * 256 * nt;
+        int rc = scan_exclusive(h, h, 256 * nt, scan_tmp, s);
+        if (rc != FMM_OK) return rc;
+      }
+    }
+    k_radix_downsweep<<<grid, kSortThreads, 0, s>>>(k_in, v_in, stride, n, b, nt, hist, fused, k_out, v_out);
     FMM_LAUNCH_CHECK();
     uint64_t* tk = k_in; k_in = k_out; k_out = tk;
     uint32_t* tv = v_in; v_in = v_out; v_out = tv;

@@ -99,22 +99,25 @@ __device__ __forceinline__ uint64_t dkey(double v) {
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-__global__ void k_make_keys(const double* __restrict__ x, int64_t N, int axis,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Sort keys of all three axes (grid.y = axis): keys[axis][i], vals[axis][i] = i.
+__global__ void k_make_keys(const double* __restrict__ x, int64_t N, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+  const int axis = blockIdx.y;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    keys[i] = dkey(x[3 * i + axis]);
-    vals[i] = (uint32_t)i;
+    keys[axis * N + i] = dkey(x[3 * i + axis]);
+    vals[axis * N + i] = (uint32_t)i;
   }
 }
 
 __global__ void k_store_axis(const uint32_t* __restrict__ sorted, int64_t N, int32_t* __restrict__ A,
                              int32_t* __restrict__ rank) {
+  const int64_t o = (int64_t)blockIdx.y * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t v = sorted[i];
-    A[i] = (int32_t)v;
-    rank[v] = (int32_t)i;
+    uint32_t v = sorted[o + i];
+    A[o + i] = (int32_t)v;
+    rank[o + v] = (int32_t)i;
   }
 }
 
@@ -198,9 +201,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
     const int32_t* __restrict__ A, const int32_t* __restrict__ rank, int64_t N,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount,
     const int64_t* __restrict__ nleftpre, int level, const int32_t* __restrict__ naxis,
-    const int32_t* __restrict__ nmed, int64_t nblk, const uint32_t* __restrict__ bscan,
+    const int32_t* __restrict__ nmed, int64_t nblk, const uint32_t* __restrict__ bscan, bool fused,
     int32_t* __restrict__ Aout) {
   __shared__ uint32_t wt[33];
+  __shared__ uint32_t sbase;
   const int k = blockIdx.y;
   const int32_t* Ak = A + (int64_t)k * N;
   int32_t* Ok = Aout + (int64_t)k * N;
@@ -224,8 +228,19 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
     c += f[j] ? 1u : 0u;
   }
   uint32_t tot;
-  // this function has __syncthreads inside; every thread reaches it
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {  // first-child elements before this chunk
+    uint32_t b0;
+    if (fused) {     // raw per-chunk counts: sum those of the earlier chunks
+      b0 = 0;
+      for (int64_t j = lane; j < (int64_t)blockIdx.x; j += 32) b0 += bscan[(int64_t)k * nblk + j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+    } else {         // already an exclusive scan
+      b0 = bscan[(int64_t)k * nblk + blockIdx.x];
+    }
+    if (lane == 0) sbase = b0;
+  }
   uint32_t inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
   __syncthreads();
   tot = wt[32];
   (void)tot;
-  int64_t P = (int64_t)bscan[(int64_t)k * nblk + blockIdx.x] + wt[warp] + (inc - c);
+  int64_t P = (int64_t)sbase + wt[warp] + (inc - c);
   for (int j = 0; j < kPartItems; ++j) {
     int64_t pos = base + j;
     if (pos >= N) break;
@@ -322,13 +337,14 @@ int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
   int32_t* nmed = ws_ptr<int32_t>(P, L.nmed);
   const int gs = (int)std::min<int64_t>(4096, div_up(N, 256));
 
-  for (int k = 0; k < 3; ++k) {
-    k_make_keys<<<gs, 256, 0, s>>>(x, N, k, keys, vals);
+  {  // the three presorts by (coordinate, input index), batched
+    k_make_keys<<<dim3(gs, 3), 256, 0, s>>>(x, N, keys, vals);
     FMM_LAUNCH_CHECK();
     bool alt = false;
-    int rc = radix_sort(keys, keys_alt, vals, vals_alt, N, 0, 64, hist, stmp, (int64_t)L.nblk_sort, s, &alt);
+    int rc = radix_sort_batched(keys, keys_alt, vals, vals_alt, N, 3, N, 0, 64, hist, stmp, (int64_t)L.nblk_sort, s,
+                                &alt);
     if (rc != FMM_OK) return rc;
-    k_store_axis<<<gs, 256, 0, s>>>(alt ? vals_alt : vals, N, A + (int64_t)k * N, rank + (int64_t)k * N);
+    k_store_axis<<<dim3(gs, 3), 256, 0, s>>>(alt ? vals_alt : vals, N, A, rank);
     FMM_LAUNCH_CHECK();
   }
 
@@ -345,12 +361,15 @@ int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
     dim3 g((unsigned)nblk, 3);
     k_part_count<<<g, kPartThreads, 0, s>>>(cur, rank, N, nstart, l, naxis, nmed, nblk, bsum);
     FMM_LAUNCH_CHECK();
-    for (int k = 0; k < 3; ++k) {
-      int rc = scan_exclusive(bsum + k * nblk, bsum + k * nblk, nblk, stmp, s);
-      if (rc != FMM_OK) return rc;
+    const bool fused = nblk <= 64;  // the scatter sums the earlier chunk counts itself
+    if (!fused) {
+      for (int k = 0; k < 3; ++k) {
+        int rc = scan_exclusive(bsum + k * nblk, bsum + k * nblk, nblk, stmp, s);
+        if (rc != FMM_OK) return rc;
+      }
     }
     k_part_scatter<<<g, kPartThreads, 0, s>>>(cur, rank, N, nstart, ncount, nleftpre, l, naxis, nmed, nblk,
-                                              bsum, nxt);
+                                              bsum, fused, nxt);
     FMM_LAUNCH_CHECK();
     int32_t* t = cur; cur = nxt; nxt = t;
   }
