@@ -1,0 +1,174 @@
+"""Parity at the full sizes of the measured beams, in the bench's plan shape (GPU).
+
+* cylinder64k (65,536 particles, n = 6, N0 = 128): the whole field against
+  the oracle's serial FMM (FP64 within 1e-12, FP32 within 1e-5) and the FP32
+  error against the brute force within the FMM's truncation error + 1e-6;
+  the FP32 adjoint against the FP64 adjoint, and both against the exact
+  direct-sum gradient of sampled particles.
+* chirp1m (1,048,576, n = 8, N0 = 256): tree boxes, leaf membership and both
+  interaction lists bit for bit against the oracle; fields on sampled
+  targets against the brute force.
+* gauss256k (262,144, n = 6, N0 = 128): forward + adjoint, FP32 against FP64
+  and against sampled brute-force fields and gradients.
+* corehalo16m (16,777,216, n = 8, N0 = 256): properties that hold at any
+  size (every ordered pair covered once, finite results) and sampled
+  brute-force fields and gradients; the same beam at 2^20 particles FP32
+  against FP64 (an FP64 run at the full size takes over a minute).
+The truncation error of the FMM at n = 6-8, eta = 0.5 on these beams is
+~1e-4 (FP64 against the brute force), which bounds the sampled checks.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bldtt, gradient, metrics, physics
+from paper_2302_07567_gb300 import fmm
+from paper_2302_07567_gb300.workloads import WORKLOADS, make_beam, make_weights, sample_targets
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(*arrs, dtype=None):
+    return [torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype) for a in arrs]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run(name, prec, adjoint=False):
+    w = WORKLOADS[name]
+    x, p, q = make_beam(name)
+    X, Pm, Q = dev(x, p, q)
+    plan = fmm.Plan(w.N, w.n, w.leaf, w.eta, precision=prec)
+    E, B = plan.field(X, Pm, Q)
+    out = dict(plan=plan, E=E.double().cpu().numpy(), B=B.double().cpu().numpy(), x=x, p=p, q=q, w=w)
+    if adjoint:
+        wE, wB = make_weights(w.N)
+        WE, WB = dev(wE, wB, dtype=plan.out_dtype)
+        dx, dp, dq = plan.adjoint(X, Pm, Q, WE, WB)
+        out.update(wE=wE, wB=wB, dx=dx.cpu().numpy(), dp=dp.cpu().numpy(), dq=dq.cpu().numpy())
+    torch.cuda.synchronize()
+    return out
+
+
+def check_gradients(r32, r64, n_sample, seed_tag):
+    """FP32 adjoint vs FP64 adjoint, and both vs the sampled direct-sum gradient."""
+    for k in ("dx", "dp", "dq"):
+        assert np.all(np.isfinite(r32[k]))
+        assert rel(r32[k], r64[k]) < 2e-5, (k, rel(r32[k], r64[k]))
+    idx = sample_targets(r32["w"].N, n_sample, tag=seed_tag)
+    gb = r64["plan"].stats()["gbar"]
+    sx, sp, sq = gradient.direct_gradient_at(r32["x"], r32["p"], r32["q"], r32["wE"], r32["wB"], idx, gb)
+    for k, ref in (("dx", sx), ("dp", sp), ("dq", sq)):
+        e64 = rel(r64[k][idx], ref.numpy())
+        e32 = rel(r32[k][idx], ref.numpy())
+        assert e64 < 1e-3, (k, e64)
+        assert e32 <= e64 + 1e-6 + 2e-5 * e64, (k, e32, e64)
+
+
+def test_cylinder64k_forward_matches_oracle_fmm():
+    r64 = run("cylinder64k", "fp64")
+    r32 = run("cylinder64k", "fp32")
+    x, p, q, w = r64["x"], r64["p"], r64["q"], r64["w"]
+    E, B = bldtt.fmm_fields(x, p, q, w.n, w.leaf, w.eta)
+    E, B = E.numpy(), B.numpy()
+    assert metrics.field_error(r64["E"], r64["B"], E, B) < 1e-12
+    assert metrics.field_error(r32["E"], r32["B"], E, B) < 1e-5
+    tg = sample_targets(w.N, 1024, tag=1)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    trunc = metrics.field_error(E[tg], B[tg], Ed.numpy(), Bd.numpy())
+    e32 = metrics.field_error(r32["E"][tg], r32["B"][tg], Ed.numpy(), Bd.numpy())
+    assert e32 <= trunc + 1e-6, (e32, trunc)
+
+
+def test_cylinder64k_adjoint():
+    r64 = run("cylinder64k", "fp64", adjoint=True)
+    r32 = run("cylinder64k", "fp32", adjoint=True)
+    check_gradients(r32, r64, 32, 2)
+
+
+def test_chirp1m_tree_and_lists_exact_and_fields():
+    r32 = run("chirp1m", "fp32")
+    x, p, q, w = r32["x"], r32["p"], r32["q"], r32["w"]
+    plan = r32["plan"]
+    ref = bldtt.build_plan(x, p, w.n, w.leaf, w.eta)
+    tr = ref.tree
+    assert plan.export("gbar")[0] == tr.gbar
+    bbox = plan.export("bbox")
+    np.testing.assert_array_equal(bbox[:, :3], tr.lo[1:])
+    np.testing.assert_array_equal(bbox[:, 3:], tr.hi[1:])
+    nodes, perm = plan.export("nodes"), plan.export("perm")
+    for i in tr.leaves():
+        st, cnt = nodes[i - 1]
+        np.testing.assert_array_equal(np.sort(perm[st:st + cnt]), np.sort(tr.members[i]))
+    np.testing.assert_array_equal(plan.export("p2p"), np.array(sorted(ref.p2p), dtype=np.int32))
+    np.testing.assert_array_equal(plan.export("m2l"), np.array(sorted(ref.m2l), dtype=np.int32))
+    r64 = run("chirp1m", "fp64")
+    tg = sample_targets(w.N, 128, tag=3)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    e64 = metrics.field_error(r64["E"][tg], r64["B"][tg], Ed.numpy(), Bd.numpy())
+    e32 = metrics.field_error(r32["E"][tg], r32["B"][tg], Ed.numpy(), Bd.numpy())
+    assert e64 < 1e-3, e64
+    assert e32 <= e64 + 1e-6, (e32, e64)
+
+
+def test_gauss256k_forward_and_adjoint():
+    r64 = run("gauss256k", "fp64", adjoint=True)
+    r32 = run("gauss256k", "fp32", adjoint=True)
+    x, p, q, w = r32["x"], r32["p"], r32["q"], r32["w"]
+    tg = sample_targets(w.N, 256, tag=4)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    e64 = metrics.field_error(r64["E"][tg], r64["B"][tg], Ed.numpy(), Bd.numpy())
+    e32 = metrics.field_error(r32["E"][tg], r32["B"][tg], Ed.numpy(), Bd.numpy())
+    assert e64 < 1e-3 and e32 <= e64 + 1e-6, (e32, e64)
+    check_gradients(r32, r64, 16, 5)
+
+
+def test_corehalo16m_properties():
+    r = run("corehalo16m", "fp32", adjoint=True)
+    plan, x, p, q, w = r["plan"], r["x"], r["p"], r["q"], r["w"]
+    for k in ("E", "B", "dx", "dp", "dq"):
+        assert np.all(np.isfinite(r[k])), k
+    sizes = plan.export("nodes")[:, 1].astype(np.float64)
+    assert sizes.min() >= 1 and sizes[-(1 << plan.stats()["kappa"]):].max() <= w.leaf
+    pairs = np.concatenate([plan.export("p2p"), plan.export("m2l")]).astype(np.int64)
+    cover = float(np.sum(sizes[pairs[:, 0] - 1] * sizes[pairs[:, 1] - 1]))
+    assert cover == float(w.N) ** 2
+    tg = sample_targets(w.N, 16, tag=6)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    err = metrics.field_error(r["E"][tg], r["B"][tg], Ed.numpy(), Bd.numpy())
+    assert err < 1e-3, err
+    # gradients: the loss weights have random signs, so dL/da_j is a field of
+    # cancelling sources and its FMM error, relative to that small total, is
+    # much larger than the field error (measured ~1e-2 on four particles)
+    idx = sample_targets(w.N, 4, tag=7)
+    sx, sp, sq = gradient.direct_gradient_at(x, p, q, r["wE"], r["wB"], idx, plan.stats()["gbar"])
+    for k, ref in (("dx", sx), ("dp", sp), ("dq", sq)):
+        assert rel(r[k][idx], ref.numpy()) < 5e-2, (k, rel(r[k][idx], ref.numpy()))
+
+
+def test_corehalo_shape_fp32_against_fp64_at_1m():
+    """The config-5 beam at 2^20 particles: FP32 within FP64's own error + 1e-6."""
+    w = WORKLOADS["corehalo16m"]
+    N = 1 << 20
+    x, p, q = make_beam("corehalo16m", N=N)
+    X, Pm, Q = dev(x, p, q)
+    wE, wB = make_weights(N)
+    res, grads = {}, {}
+    for prec in ("fp64", "fp32"):
+        plan = fmm.Plan(N, w.n, w.leaf, w.eta, precision=prec)
+        E, B = plan.field(X, Pm, Q)
+        res[prec] = (E.double().cpu().numpy(), B.double().cpu().numpy())
+        WE, WB = dev(wE, wB, dtype=plan.out_dtype)
+        grads[prec] = [t.cpu().numpy() for t in plan.adjoint(X, Pm, Q, WE, WB)]
+    for a, b in zip(grads["fp32"], grads["fp64"]):
+        assert rel(a, b) < 2e-5, rel(a, b)
+    tg = sample_targets(N, 128, tag=8)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    e64 = metrics.field_error(res["fp64"][0][tg], res["fp64"][1][tg], Ed.numpy(), Bd.numpy())
+    e32 = metrics.field_error(res["fp32"][0][tg], res["fp32"][1][tg], Ed.numpy(), Bd.numpy())
+    assert e64 < 1e-3 and e32 <= e64 + 1e-6, (e32, e64)
+    assert metrics.field_error(*res["fp32"], *res["fp64"]) < 1e-5

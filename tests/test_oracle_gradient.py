@@ -61,3 +61,17 @@ def test_fmm_gradient_approaches_direct_gradient():
         _, dx, dp, dq = gradient.direct_gradient(x, p, q, wE, wB, gbar=plan.tree.gbar)
         errs.append(max(float((gx - dx).norm() / dx.norm()), float((gq - dq).norm() / dq.norm())))
     assert errs[1] < errs[0] < 0.1
+
+
+def test_sampled_direct_gradient_matches_full_autograd():
+    """The per-particle O(N) gradient equals the full direct-sum gradient rows."""
+    N = 150
+    x, p, q = random_beam(N, seed=14, gamma=7.0, spread=0.05, angle=0.05)
+    wE, wB = make_weights(N)
+    gb = physics.gamma_bar(p)
+    _, gx, gp, gq = gradient.direct_gradient(x, p, q, wE, wB, gbar=gb)
+    idx = [0, 17, 88, 149]
+    sx, sp, sq = gradient.direct_gradient_at(x, p, q, wE, wB, idx, gb)
+    np.testing.assert_allclose(sx.numpy(), gx.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gx.abs().max()))
+    np.testing.assert_allclose(sp.numpy(), gp.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gp.abs().max()))
+    np.testing.assert_allclose(sq.numpy(), gq.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gq.abs().max()))
