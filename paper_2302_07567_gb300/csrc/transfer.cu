@@ -127,6 +127,111 @@ __global__ void __launch_bounds__(256) k_transfer_all(int level_first, int level
   }
 }
 
+// The same transfer specialised on the number of points per axis, with one
+// (parent, component) pair per work item: compile-time extents turn the index
+// arithmetic into shifts and multiplies, and the extra items shorten the
+// per-level critical path near the root where only a few parents exist.
+template <typename T, int NP1, bool UP>
+__global__ void __launch_bounds__(256) k_transfer_np(int level_first, int level_last, int nc, const T* __restrict__ tm,
+                                                     T* __restrict__ buf) {
+  constexpr int Q = NP1 * NP1, M = Q * NP1;
+  __shared__ T mats[6 * Q];  // [2 children][3 axes][Q]
+  __shared__ T in[2 * M];    // UP: both children; DOWN: the parent in the first M
+  __shared__ T t1[2 * M];
+  __shared__ T t2[2 * M];
+  cg::grid_group grid = cg::this_grid();
+  const int step = UP ? -1 : 1;
+  for (int level = level_first;; level += step) {
+    const int64_t nparents = (int64_t)1 << level;
+    const int64_t items = nparents * nc;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      const int64_t parent = nparents + it / nc;
+      const int comp = (int)(it % nc);
+      __syncthreads();
+      for (int o = threadIdx.x; o < 6 * Q; o += blockDim.x) mats[o] = tm[(size_t)(2 * parent) * 3 * Q + o];
+      if (UP) {
+        for (int o = threadIdx.x; o < 2 * M; o += blockDim.x) {
+          const int c = o / M, idx = o - c * M;
+          in[o] = buf[((size_t)(2 * parent + c) * nc + comp) * M + idx];
+        }
+      } else {
+        for (int o = threadIdx.x; o < M; o += blockDim.x) in[o] = buf[((size_t)parent * nc + comp) * M + o];
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < 2 * M; o += blockDim.x) {  // x axis
+        const int c = o / M, idx = o - c * M;
+        const int a = idx % NP1, rest = idx / NP1;
+        const T* Mx = mats + (c * 3 + 0) * Q;
+        const T* src = (UP ? in + c * M : in) + rest * NP1;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NP1; ++k) s += (UP ? Mx[a * NP1 + k] : Mx[k * NP1 + a]) * src[k];
+        t1[o] = s;
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < 2 * M; o += blockDim.x) {  // y axis
+        const int c = o / M, idx = o - c * M;
+        const int a = idx % NP1, bb = (idx / NP1) % NP1, cz = idx / Q;
+        const T* My = mats + (c * 3 + 1) * Q;
+        const T* src = t1 + c * M + cz * Q + a;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < NP1; ++k) s += (UP ? My[bb * NP1 + k] : My[k * NP1 + bb]) * src[k * NP1];
+        t2[o] = s;
+      }
+      __syncthreads();
+      if (UP) {  // z axis, summed over the two children into the parent
+        for (int o = threadIdx.x; o < M; o += blockDim.x) {
+          const int ab = o % Q, cz = o / Q;
+          T s = T(0);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const T* Mz = mats + (c * 3 + 2) * Q;
+            const T* src = t2 + c * M + ab;
+#pragma unroll
+            for (int k = 0; k < NP1; ++k) s += Mz[cz * NP1 + k] * src[k * Q];
+          }
+          buf[((size_t)parent * nc + comp) * M + o] = s;
+        }
+      } else {  // z axis, added into each child
+        for (int o = threadIdx.x; o < 2 * M; o += blockDim.x) {
+          const int c = o / M, idx = o - c * M;
+          const int ab = idx % Q, cz = idx / Q;
+          const T* Mz = mats + (c * 3 + 2) * Q;
+          const T* src = t2 + c * M + ab;
+          T s = T(0);
+#pragma unroll
+          for (int k = 0; k < NP1; ++k) s += Mz[k * NP1 + cz] * src[k * Q];
+          buf[((size_t)(2 * parent + c) * nc + comp) * M + idx] += s;
+        }
+      }
+    }
+    if (level == level_last) break;
+    grid.sync();
+  }
+}
+
+template <typename T, int NP1, bool UP>
+int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s) {
+  static int per_sm = 0, sms = 0;
+  auto kern = k_transfer_np<T, NP1, UP>;
+  if (per_sm == 0) {
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    if (per_sm < 1) return FMM_EINVAL;
+  }
+  const int64_t most = ((int64_t)1 << (P->kappa - 1)) * nc;
+  const int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, most);
+  int first = UP ? P->kappa - 1 : 0, last = UP ? 0 : P->kappa - 1;
+  const T* tm = ws_ptr<T>(P, P->lay.tmat);
+  void* args[] = {&first, &last, &nc, (void*)&tm, &buf};
+  FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, 0, s));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
 template <typename T, int NC, bool UP>
 int launch_all(fmm_plan_s* P, T* buf, cudaStream_t s) {
   if (P->kappa == 0) return FMM_OK;
@@ -179,7 +284,14 @@ int run_tmats(fmm_plan_s* P, cudaStream_t s) {
 
 template <typename T, int NC, bool UP>
 int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s) {
-  return launch_all<T, NC, UP>(P, buf, s);
+  if (P->kappa == 0) return FMM_OK;
+  switch (P->np1) {
+    case 3: return launch_np<T, 3, UP>(P, NC, buf, s);
+    case 5: return launch_np<T, 5, UP>(P, NC, buf, s);
+    case 7: return launch_np<T, 7, UP>(P, NC, buf, s);
+    case 9: return launch_np<T, 9, UP>(P, NC, buf, s);
+    default: return launch_all<T, NC, UP>(P, buf, s);
+  }
 }
 
 template int run_transfer<float, 4, true>(fmm_plan_s*, float*, cudaStream_t);
