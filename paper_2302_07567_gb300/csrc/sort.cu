@@ -100,10 +100,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* 
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint64_t kk[kSortRounds];  // all loads of the tile in flight at once
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    kk[r] = i < n ? keys[i] : 0ull;
+  }
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
     bool valid = i < n;
-    unsigned d = valid ? (unsigned)((keys[i] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
+    unsigned d = valid ? (unsigned)((kk[r] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
     unsigned peers = __match_any_sync(0xffffffffu, d);
     if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
   }
@@ -133,13 +140,27 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
   run[threadIdx.x] = 0;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint64_t kk[kSortRounds];  // the tile's keys and values, loaded before any use
+  uint32_t vv[kSortRounds];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    kk[r] = i < n ? keys[i] : 0ull;
+    vv[r] = (i < n && vals) ? vals[i] : 0u;
+  }
   if (fused) {
     const uint32_t* h = hist + (int64_t)threadIdx.x * ntiles;
     uint32_t tot = 0, before = 0;
-    for (int64_t t = 0; t < ntiles; ++t) {
-      const uint32_t c = h[t];
-      tot += c;
-      before += t < (int64_t)blockIdx.x ? c : 0u;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 16) {
+      uint32_t c[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) c[u] = t0 + u < ntiles ? h[t0 + u] : 0u;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        tot += c[u];
+        before += t0 + u < (int64_t)blockIdx.x ? c[u] : 0u;
+      }
     }
     uint32_t all;
     gbase[threadIdx.x] = block_exclusive_scan(tot, wt, all) + before;
@@ -147,12 +168,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   }
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
     bool valid = i < n;
-    uint64_t key = valid ? keys[i] : 0ull;
-    uint32_t val = (valid && vals) ? vals[i] : 0u;
+    const uint64_t key = kk[r];
+    const uint32_t val = vv[r];
     unsigned d = valid ? (unsigned)((key >> shift) & 0xffu) : 0x100u + lane;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     unsigned wr = __popc(peers & lanemask_lt());

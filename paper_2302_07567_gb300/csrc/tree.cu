@@ -82,13 +82,15 @@ __global__ void k_check_inputs(const double* __restrict__ x, const double* __res
 __global__ void k_gbar(const double* __restrict__ sx, const double* __restrict__ sy,
                        const double* __restrict__ sz, int64_t N, const double* __restrict__ qmax,
                        int nq, double* __restrict__ scal) {
+  double m = 0.0;  // max|q| over the partials, one warp
+  for (int i = threadIdx.x; i < nq; i += 32) m = fmax(m, qmax[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double dn = (double)N;
   double px = __ddiv_rn(sx[0], dn), py = __ddiv_rn(sy[0], dn), pz = __ddiv_rn(sz[0], dn);
   double pp = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
   scal[0] = __dsqrt_rn(__dadd_rn(1.0, pp));
-  double m = 0.0;
-  for (int i = 0; i < nq; ++i) m = fmax(m, qmax[i]);
   scal[1] = (m > 0.0 && isfinite(m)) ? ldexp(1.0, (int)rint(log2(m))) : 1.0;
 }
 
@@ -276,6 +278,183 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
   }
 }
 
+// Deep levels in one block per subtree.  Once a node holds at most
+// kSubSlots slots, one block finishes every level below it in shared memory:
+// the node's members get local ids (their slot in the x-array), the three
+// slot arrays hold local ids, and a level is one box/axis/median step per
+// node followed by the stable partition of every node's slot ranges.  Inside
+// a node the split axis' array is in rank order, so "rank <= median rank" is
+// "slot among the first ceil(c/2) of that array": each member's flag is read
+// off the split axis' array and no rank is looked up but the median's.
+constexpr int kSubSlots = 4096;
+constexpr int kSubThreads = 1024;
+constexpr int kSubItems = 3 * kSubSlots / kSubThreads;
+constexpr int kSubNodes = kSubSlots / 2;  // a node above the leaves has >= 2 members
+static_assert(kSubItems <= 32, "flags are kept in one 32-bit mask per thread");
+static_assert(3 * 2 * kSubSlots >= 4 * kSubSlots, "x-ranks fit in the second slot buffer");
+
+struct SubtreeSmem {
+  uint16_t arr[2][3][kSubSlots];  // (arr[1] holds 4-byte x-ranks before the first level)  // local ids by slot, current and next level
+  int32_t gid[kSubSlots];         // local id -> input index
+  uint16_t seg[kSubSlots];        // slot -> node of the current level (relative)
+  uint8_t flag[kSubSlots];        // local id -> goes to the first child
+  uint16_t nst[kSubNodes], ncnt[kSubNodes];
+  uint8_t nax[kSubNodes];
+  uint32_t npre[3][kSubNodes];    // first-child elements before each node's start
+  uint32_t wt[33];
+};
+
+__device__ __forceinline__ uint32_t sub_block_scan(uint32_t v, uint32_t* wt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wt[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = wt[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    wt[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t r = wt[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kSubThreads) k_subtree(
+    const double* __restrict__ x, int32_t* A, const int32_t* __restrict__ rank, int64_t N,
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int ls, int kappa,
+    const double* __restrict__ scal, double* __restrict__ nlo, double* __restrict__ nhi,
+    int32_t* __restrict__ naxis, int32_t* __restrict__ nmed) {
+  extern __shared__ __align__(16) unsigned char sub_raw[];
+  SubtreeSmem& S = *reinterpret_cast<SubtreeSmem*>(sub_raw);
+  const int64_t root = ((int64_t)1 << ls) + blockIdx.x;
+  const int64_t st0 = nstart[root];
+  const int c = (int)ncount[root];
+  const double sz = scal[0];
+  // local ids: slot in the x-array; the y- and z-arrays find theirs by the
+  // x-rank, which increases along the x-array's slots
+  int32_t* xr = reinterpret_cast<int32_t*>(&S.arr[1][0][0]);  // x-ranks by slot, until level ls
+  for (int j = threadIdx.x; j < c; j += blockDim.x) {
+    const int32_t e = A[st0 + j];
+    S.gid[j] = e;
+    xr[j] = rank[e];
+    S.arr[0][0][j] = (uint16_t)j;
+    S.seg[j] = 0;
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < 2 * c; g += blockDim.x) {
+    const int k = 1 + g / c, j = g - (k - 1) * c;
+    const int32_t rx = rank[A[(int64_t)k * N + st0 + j]];
+    int lo = 0, hi = c - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (xr[mid] < rx) lo = mid + 1; else hi = mid;
+    }
+    S.arr[0][k][j] = (uint16_t)lo;
+  }
+  int cur = 0;
+  for (int l = ls;; ++l) {
+    __syncthreads();
+    const int64_t first = root << (l - ls);
+    const int nodes = 1 << (l - ls);
+    for (int u = threadIdx.x; u < nodes; u += blockDim.x) {  // boxes, Alg. 1 axis, Appendix B median
+      const int64_t g = first + u;
+      const int st = (int)(nstart[g] - st0), cnt = (int)ncount[g];
+      double w[3];
+      for (int k = 0; k < 3; ++k) {
+        const double lo = x[3 * (int64_t)S.gid[S.arr[cur][k][st]] + k];
+        const double hi = x[3 * (int64_t)S.gid[S.arr[cur][k][st + cnt - 1]] + k];
+        nlo[3 * g + k] = lo;
+        nhi[3 * g + k] = hi;
+        w[k] = __dmul_rn(k == 2 ? sz : 1.0, __dsub_rn(hi, lo));
+      }
+      if (l == kappa) {
+        naxis[g] = -1;
+        nmed[g] = -1;
+        continue;
+      }
+      int ax = 0;
+      if (w[1] > w[ax]) ax = 1;
+      if (w[2] > w[ax]) ax = 2;
+      const int h1 = (cnt + 1) / 2;
+      naxis[g] = ax;
+      nmed[g] = rank[(int64_t)ax * N + S.gid[S.arr[cur][ax][st + h1 - 1]]];
+      S.nst[u] = (uint16_t)st;
+      S.ncnt[u] = (uint16_t)cnt;
+      S.nax[u] = (uint8_t)ax;
+    }
+    if (l == kappa) break;
+    __syncthreads();
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+      const int u = S.seg[j];
+      S.flag[S.arr[cur][S.nax[u]][j]] = (uint8_t)(j - S.nst[u] < (S.ncnt[u] + 1) / 2);
+    }
+    __syncthreads();
+    // stable partition of the three arrays: one scan over their concatenation
+    const int g0 = threadIdx.x * kSubItems;
+    uint32_t fm = 0, cntf = 0;
+#pragma unroll
+    for (int i = 0; i < kSubItems; ++i) {
+      const int g = g0 + i;
+      if (g < 3 * c) {
+        const int k = g / c, j = g - k * c;
+        const uint32_t f = S.flag[S.arr[cur][k][j]];
+        fm |= f << i;
+        cntf += f;
+      }
+    }
+    const uint32_t pre = sub_block_scan(cntf, S.wt);
+    uint32_t run = pre;
+#pragma unroll
+    for (int i = 0; i < kSubItems; ++i) {
+      const int g = g0 + i;
+      if (g < 3 * c) {
+        const int k = g / c, j = g - k * c;
+        const int u = S.seg[j];
+        if (j == S.nst[u]) S.npre[k][u] = run;
+        run += (fm >> i) & 1u;
+      }
+    }
+    __syncthreads();
+    run = pre;
+#pragma unroll
+    for (int i = 0; i < kSubItems; ++i) {
+      const int g = g0 + i;
+      if (g < 3 * c) {
+        const int k = g / c, j = g - k * c;
+        const int u = S.seg[j];
+        const int st = S.nst[u], h1 = (S.ncnt[u] + 1) / 2;
+        const int lb = (int)(run - S.npre[k][u]);
+        const bool f = (fm >> i) & 1u;
+        const int dst = f ? st + lb : st + h1 + ((j - st) - lb);
+        S.arr[cur ^ 1][k][dst] = S.arr[cur][k][j];
+        run += f ? 1u : 0u;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+      const int u = S.seg[j];
+      S.seg[j] = (uint16_t)(2 * u + (j - S.nst[u] >= (S.ncnt[u] + 1) / 2 ? 1 : 0));
+    }
+    cur ^= 1;
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < 3 * c; g += blockDim.x) {
+    const int k = g / c, j = g - k * c;
+    A[(int64_t)k * N + st0 + j] = S.gid[S.arr[cur][k][j]];
+  }
+}
+
 }  // namespace
 
 int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s) {
@@ -352,12 +531,15 @@ int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
   uint32_t* bsum = ws_ptr<uint32_t>(P, L.blocksum);
   int32_t* cur = A;
   int32_t* nxt = Aalt;
-  for (int l = 0; l <= P->kappa; ++l) {
+  // first level whose nodes one block finishes alone (the leftmost node of a
+  // level is its largest)
+  int ls = 0;
+  while (ls < P->kappa && P->node_count[(size_t)1 << ls] > kSubSlots) ++ls;
+  for (int l = 0; l < ls; ++l) {
     const int64_t nodes = (int64_t)1 << l;
     k_node_split<<<(unsigned)div_up(nodes, 128), 128, 0, s>>>(x, cur, rank, N, nstart, ncount, l, P->kappa,
                                                              scal, nlo, nhi, naxis, nmed);
     FMM_LAUNCH_CHECK();
-    if (l == P->kappa) break;
     dim3 g((unsigned)nblk, 3);
     k_part_count<<<g, kPartThreads, 0, s>>>(cur, rank, N, nstart, l, naxis, nmed, nblk, bsum);
     FMM_LAUNCH_CHECK();
@@ -372,6 +554,17 @@ int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
                                               bsum, fused, nxt);
     FMM_LAUNCH_CHECK();
     int32_t* t = cur; cur = nxt; nxt = t;
+  }
+  {
+    static bool attr = false;
+    if (!attr) {
+      FMM_CUDA_TRY(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(SubtreeSmem)));
+      attr = true;
+    }
+    k_subtree<<<(unsigned)((int64_t)1 << ls), kSubThreads, sizeof(SubtreeSmem), s>>>(
+        x, cur, rank, N, nstart, ncount, ls, P->kappa, scal, nlo, nhi, naxis, nmed);
+    FMM_LAUNCH_CHECK();
   }
   // leaf order: the x-array's slot order (members of each leaf sorted by x)
   FMM_CUDA_TRY(cudaMemcpyAsync(ws_ptr<int32_t>(P, L.perm), cur, sizeof(int32_t) * N,
