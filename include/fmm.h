@@ -99,8 +99,8 @@ int fmm_plan_set_workspace(fmm_plan_t plan, void* device_ptr, size_t bytes);
  *   x, p  device, [N,3] float64;  q  device, [N] float64
  *   E, B  device, [N,3]; float64 for FMM_FP64 plans, float32 for FMM_FP32 plans
  * Rows of E and B follow the input order.  The call queues work on `stream`,
- * waits once on it after the traversal (to size the list sort and read the
- * device error flags) and returns; the remaining kernels may still be running.
+ * waits once on it after the traversal (to read the list sizes and the device
+ * error flags) and returns; the remaining kernels may still be running.
  * On FMM_EOVERFLOW / FMM_ENONFINITE nothing is written to E and B. */
 int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q,
               void* E, void* B, void* stream);
@@ -125,7 +125,8 @@ typedef struct fmm_stats {
   double m2l_interactions;               /* m2l_pairs * (n+1)^6                       */
   int64_t cap_p2p, cap_m2l, cap_frontier;
   /* stage times of the last calls in ms (FMM_TIMING only, else 0):
-     forward: 0 setup, 1 tree, 2 upward, 3 traversal, 4 list sort, 5 M2L, 6 L2L,
+     forward: 0 setup, 1 tree, 2 upward, 3 traversal with the ordering of the
+     lists and the host wait after it, 4 none (0), 5 M2L, 6 L2L,
      7 P2P+L2P, 13 whole forward;  adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T,
      11 target-side particle kernel (near + far), 12 source-side particle kernel
      (near + far + chain rule), 14 whole adjoint, 15 source-major lists and any

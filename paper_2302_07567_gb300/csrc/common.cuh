@@ -37,6 +37,9 @@ enum : unsigned {
 };
 
 // Device-resident counters of one call (first bytes of the workspace).
+// Blocks a cooperative traversal launch may use (scan partials reserved per list).
+constexpr int64_t kTravPartials = 4096;
+
 struct Counters {
   unsigned long long p2p_count;
   unsigned long long m2l_count;
@@ -83,8 +86,8 @@ struct Layout {
   size_t adj_part;                 // per particle: target-side position gradient (leaf order)
   size_t wle, wlb;                 // per particle: scaled loss weights (leaf order)
   size_t p2p_sdc, m2l_sdc;         // centre offsets of the source-major lists
-  size_t sort_n;      // elements the sort buffers hold
-  size_t nblk_sort;   // radix tiles at sort_n
+  size_t tcnt, tpart;               // list ordering: per-node counts and fills, scan partials
+  size_t nblk_sort;   // radix tiles of the three presorts
   size_t nblk_part;   // partition blocks at N
 };
 
@@ -235,24 +238,18 @@ int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, 
 int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s);
 int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
 int run_upward(fmm_plan_s* P, cudaStream_t s);
+// traversal and both target-major lists (sorted, CSR, centre offsets), one launch
 int run_traverse(fmm_plan_s* P, cudaStream_t s);
-int run_list_sort(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
-int run_pair_offsets(fmm_plan_s* P, cudaStream_t s);
-// per-pair centre offsets of `count` list keys at workspace offset keys_off
-int pair_offsets(fmm_plan_s* P, size_t keys_off, int64_t count, size_t out_off, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
 int run_l2l(fmm_plan_s* P, cudaStream_t s);
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);
 int run_adjoint(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE,
                 const void* wB, double* dx, double* dp, double* dq, cudaStream_t s);
-// radix sort of 64-bit keys (optionally with 32-bit values) over bits
-// [begin_bit, end_bit); returns in `*in_alt` whether the result sits in the
+// stable LSD radix sort of 64-bit keys with 32-bit values over bits
+// [begin_bit, end_bit): nbatch independent sorts of n keys each, batch k at
+// keys + k * stride; returns in `*in_alt` whether the result sits in the
 // alternate buffers.
-int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
-               int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
-               cudaStream_t s, bool* in_alt);
-// nbatch independent sorts of n keys each, batch k at keys + k * stride
 int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t stride,
                        int nbatch, int64_t n, int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp,
                        int64_t max_tiles, cudaStream_t s, bool* in_alt);

@@ -32,10 +32,12 @@ void make_layout(fmm_plan_s* P) {
   const size_t N = (size_t)P->N, C1 = (size_t)P->C + 1, m = (size_t)P->m;
   const size_t R = P->precision == FMM_FP32 ? sizeof(float) : sizeof(double);
   const size_t V4 = 4 * R;
-  const int64_t sort_n = std::max<int64_t>({3 * P->N, P->cap_p2p, P->cap_m2l, 1});
-  const int64_t tiles = radix_tiles(sort_n) + 3 * radix_tiles(P->N);  // batched presort or one list
+  // keys: the three presorts; keys_alt: their alternate buffer, then the
+  // interaction lists grouped by major node while they are ordered
+  const int64_t sort_n = std::max<int64_t>(3 * P->N, 1);
+  const int64_t alt_n = std::max<int64_t>({3 * P->N, P->cap_p2p + P->cap_m2l, 1});
+  const int64_t tiles = 3 * radix_tiles(P->N);
   const int64_t nblk_part = div_up(P->N, 2048);
-  L.sort_n = (size_t)sort_n;
   L.nblk_sort = (size_t)tiles;
   L.nblk_part = (size_t)nblk_part;
   L.counters = take(sizeof(Counters));
@@ -44,7 +46,7 @@ void make_layout(fmm_plan_s* P) {
   L.psum_part = take(3 * 2 * (np0 + 2) * sizeof(double));
   L.qmax_part = take(1024 * sizeof(double));
   L.keys = take(sort_n * 8);
-  L.keys_alt = take(sort_n * 8);
+  L.keys_alt = take(alt_n * 8);
   L.vals = take(3 * N * 4);
   L.vals_alt = take(3 * N * 4);
   L.hist = take((size_t)256 * tiles * 4);
@@ -89,6 +91,8 @@ void make_layout(fmm_plan_s* P) {
   L.adj_part = take(N * V4);
   L.wle = take(N * V4);
   L.wlb = take(N * V4);
+  L.tcnt = take(4 * (C1 + 1) * 4);
+  L.tpart = take(2 * (size_t)kTravPartials * 4);
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.total = off;
@@ -287,8 +291,6 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   P->munit = hs[1];
   P->lunit = hs[2];
   if ((rc = record(P, 4, s)) != FMM_OK) return rc;
-  if ((rc = run_list_sort(P, s)) != FMM_OK) return rc;
-  if ((rc = run_pair_offsets(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 5, s)) != FMM_OK) return rc;
   if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 6, s)) != FMM_OK) return rc;

@@ -1,10 +1,8 @@
 // Device-wide exclusive scan and stable LSD radix sort (64-bit keys).
 //
-// Used by the tree build (one presort of the particles along each axis, so
+// Used by the tree build: one presort of the particles along each axis, so
 // that equal coordinates stay in input-index order, which is the tie rule of
-// the median split) and by the traversal (interaction lists sorted by
-// (target, source), which groups every target's pairs as Section 10 asks and
-// makes the lists deterministic).
+// the median split.
 #include "common.cuh"
 
 namespace fmm {
@@ -223,13 +221,6 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, 
 }
 
 int64_t radix_tiles(int64_t n) { return div_up(n > 0 ? n : 1, kSortTile); }
-
-int radix_sort(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
-               int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp, int64_t max_tiles,
-               cudaStream_t s, bool* in_alt) {
-  return radix_sort_batched(keys, keys_alt, vals, vals_alt, 0, 1, n, begin_bit, end_bit, hist, scan_tmp, max_tiles,
-                            s, in_alt);
-}
 
 int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t stride,
                        int nbatch, int64_t n, int begin_bit, int end_bit, uint32_t* hist, uint32_t* scan_tmp,

@@ -1,5 +1,6 @@
 // Dual tree traversal (Algs. 11 and 17) producing the P2P and M2L interaction
-// lists, sorted by (target, source) and indexed by target (Section 10).
+// lists, sorted by (target, source) and indexed by target (Section 10), and
+// the source-major lists the adjoint reads.
 //
 // The recursion of Alg. 17 is run level-synchronously: a frontier of node
 // pairs starts at (1, 1); every step classifies each pair exactly as Alg. 17
@@ -7,27 +8,68 @@
 // or the pair member with the larger stretched diameter, the source on a
 // tie) and appends the two child pairs to the next frontier.  Each step adds
 // one level to one member of a pair, so 2 kappa + 1 steps empty the frontier.
-// Appends go through atomic counters (order unspecified); the radix sort by
-// (target << bits | source) afterwards makes the lists deterministic.
+// All steps run in one cooperative launch with a grid-wide barrier between
+// them.  Appends go through atomic counters (order unspecified); the same
+// launch then orders both lists: pairs are counted per target, the counts
+// scanned into the CSR offsets, the pairs scattered into their target's
+// segment, and every segment ranked by source (a pair's rank is the number of
+// smaller keys in its segment, the keys being distinct).  The result is the
+// order a sort by (target << bits | source) gives, whatever the append order.
+// The centre offset of each pair is written as it reaches its final slot.
 //
 // The admissibility test is Alg. 8 with diam and dist of Algs. 6-7 in FP64
 // with round-to-nearest operations in a fixed order and no contraction:
 // max(r_t, r_s) / d < eta, d = sqrt((v_x^2 + v_y^2) + v_z^2), v = s o (c_t - c_s).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace fmm {
 namespace {
 
-__global__ void k_trav_init(Counters* cnt, int2* f0) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    f0[0] = make_int2(1, 1);
-    cnt->frontier_count[0] = 1;
-    cnt->frontier_count[1] = 0;
-    cnt->frontier_count[2] = 0;
-    cnt->p2p_count = 0;
-    cnt->m2l_count = 0;
-  }
-}
+namespace cg = cooperative_groups;
+
+constexpr int kTravThreads = 256;
+constexpr int kSegStage = 128;  // keys of one segment a warp ranks from shared memory
+
+// One list to order: pairs key = (major << shift | minor), optionally swapped
+// from (minor << shift | major), grouped and sorted by key.  Arrays written
+// earlier in the same launch are read through L2 (__ldcg).
+struct ListJob {
+  const uint64_t* in;               // pairs to order
+  const unsigned long long* n;      // their number (device counter)
+  int64_t cap;                      // capacity of in, tmp, out and dc
+  uint32_t* cnt;                    // [C + 2] pairs per major node
+  uint32_t* fill;                   // [C + 2] pairs placed per major node
+  int32_t* off;                     // [C + 2] CSR: first pair whose major is >= t
+  uint64_t* tmp;                    // pairs grouped by major
+  uint64_t* out;                    // pairs sorted by key
+  void* dc;                         // s o (c_major - c_minor) / ell per pair
+};
+
+struct ListArgs {
+  ListJob job[2];
+  bool swap;                        // order by source: key = (s << shift | t)
+  int shift;
+  int64_t C;
+  const double* ncen;
+  const double* scal;
+  uint32_t* partial;                // [2][gridDim.x] scan partials
+};
+
+struct TravArgs {
+  Counters* cnt;
+  int2* front[2];
+  int64_t cap_front;
+  uint64_t* p2p;                    // unordered appends
+  int64_t cap_p2p;
+  uint64_t* m2l;
+  int64_t cap_m2l;
+  const double* ndiam;
+  double eta;
+  int kappa;
+  ListArgs lists;
+};
 
 __device__ __forceinline__ void push(unsigned long long* counter, int64_t cap, uint64_t* list, uint64_t key,
                                      unsigned int* err, unsigned flag) {
@@ -36,196 +78,316 @@ __device__ __forceinline__ void push(unsigned long long* counter, int64_t cap, u
   else atomicOr(err, flag);
 }
 
-__global__ void k_trav_step(const int2* __restrict__ fin, int it, int2* __restrict__ fout, Counters* cnt,
-                            int64_t cap_front, uint64_t* __restrict__ p2p, int64_t cap_p2p,
-                            uint64_t* __restrict__ m2l, int64_t cap_m2l, const double* __restrict__ ncen,
-                            const double* __restrict__ ndiam, const double* __restrict__ scal, double eta,
-                            int kappa, int shift) {
-  const unsigned long long nin = cnt->frontier_count[it % 3];
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->frontier_count[(it + 2) % 3] = 0;
-  unsigned long long* nout = &cnt->frontier_count[(it + 1) % 3];
-  const int64_t n = min64((int64_t)nin, cap_front);
-  const int leaf0 = 1 << kappa;
-  const double s[3] = {1.0, 1.0, scal[0]};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int2 pr = fin[e];
-    const int t = pr.x, u = pr.y;
-    const bool lt = t >= leaf0, lu = u >= leaf0;
-    if (lt && lu) {
-      push(&cnt->p2p_count, cap_p2p, p2p, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfP2P);
-      continue;
-    }
-    const double rt = ndiam[t], ru = ndiam[u];
-    double v[3];
+__device__ __forceinline__ uint64_t list_key(const ListArgs& a, const uint64_t* in, int64_t e) {
+  const uint64_t k = __ldcg(reinterpret_cast<const unsigned long long*>(in) + e);
+  if (!a.swap) return k;
+  const uint64_t mask = ((uint64_t)1 << a.shift) - 1;
+  return ((k & mask) << a.shift) | (k >> a.shift);
+}
+
+__device__ __forceinline__ int64_t list_count(const ListJob& j) {
+  const int64_t n = (int64_t)__ldcg(j.n);
+  return n < j.cap ? n : j.cap;
+}
+
+// Exclusive scan of one value per thread over the block; returns the block total.
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wt, uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = v;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = __dmul_rn(s[k], __dsub_rn(ncen[3 * t + k], ncen[3 * u + k]));
-    const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
-                                          __dmul_rn(v[2], v[2])));
-    const double ratio = __ddiv_rn(rt >= ru ? rt : ru, d);
-    if (ratio < eta) {
-      push(&cnt->m2l_count, cap_m2l, m2l, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfM2L);
-      continue;
-    }
-    int2 c0, c1;
-    if (lt || (!lu && !(rt > ru))) {  // split the source
-      c0 = make_int2(t, 2 * u);
-      c1 = make_int2(t, 2 * u + 1);
-    } else {                          // split the target
-      c0 = make_int2(2 * t, u);
-      c1 = make_int2(2 * t + 1, u);
-    }
-    unsigned long long at = atomicAdd(nout, 2ull);
-    if ((int64_t)at + 1 < cap_front) {
-      fout[at] = c0;
-      fout[at + 1] = c1;
-    } else {
-      atomicOr(&cnt->err, kErrOvfFrontier);
-    }
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
   }
+  if (lane == 31) wt[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < nw ? wt[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) wt[lane] = wi - w;
+    if (lane == nw - 1) wt[32] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = wt[warp] + inc - v;
+  total = wt[32];
+  __syncthreads();
+  return r;
 }
 
-// off[t] = first list index whose target is >= t, for t = 0 .. C+1.
-__global__ void k_csr(const uint64_t* __restrict__ keys, int64_t count, int shift, int64_t C,
-                      int32_t* __restrict__ off) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t > C + 1) return;
-  const uint64_t key = (uint64_t)t << shift;
-  int64_t lo = 0, hi = count;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (keys[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  off[t] = (int32_t)lo;
-}
-
-// Source-major copy of a list: (t << shift | s) -> (s << shift | t).
-__global__ void k_swap_pairs(const uint64_t* __restrict__ in, int64_t count, int shift,
-                             uint64_t* __restrict__ out) {
-  const uint64_t mask = ((uint64_t)1 << shift) - 1;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = in[e];
-    out[e] = ((k & mask) << shift) | (k >> shift);
-  }
-}
-
-// Centre offset c_t - c_s of every list pair in stretched, scaled units,
-// s o (c_t - c_s) / ell with the difference taken in physical FP64
-// coordinates.  FP32 plans store it as an unevaluated sum hi + lo of two
-// float4 rows, FP64 plans as one double4.
+// Count, scan, scatter and rank both lists of `a` (every block of the grid).
 template <bool kFP32>
-__global__ void k_pair_dc(const uint64_t* __restrict__ keys, int64_t count, int shift,
-                          const double* __restrict__ ncen, const double* __restrict__ scal, void* __restrict__ out) {
-  const uint64_t mask = ((uint64_t)1 << shift) - 1;
-  const double s[3] = {1.0, 1.0, scal[0]};
-  const double inv = scal[3];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[e];
-    const double* ct = ncen + 3 * (k >> shift);
-    const double* cs = ncen + 3 * (k & mask);
-    double dc[3];
-    for (int d = 0; d < 3; ++d) dc[d] = (s[d] * (ct[d] - cs[d])) * inv;
-    if (kFP32) {
-      float h[3], l[3];
-      for (int d = 0; d < 3; ++d) {
-        h[d] = (float)dc[d];
-        l[d] = (float)(dc[d] - (double)h[d]);
-      }
-      float4* o = static_cast<float4*>(out);
-      o[2 * e] = make_float4(h[0], h[1], h[2], 0.f);
-      o[2 * e + 1] = make_float4(l[0], l[1], l[2], 0.f);
-    } else {
-      static_cast<double4*>(out)[e] = make_double4(dc[0], dc[1], dc[2], 0.0);
+__device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
+  __shared__ uint32_t wt[33];
+  __shared__ uint64_t stage[kTravThreads / 32][kSegStage];
+  const int64_t M = a.C + 2;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < 2; ++j)
+    for (int64_t i = gtid; i < M; i += gstride) {
+      a.job[j].cnt[i] = 0;
+      a.job[j].fill[i] = 0;
+    }
+  grid.sync();
+  for (int j = 0; j < 2; ++j) {
+    const ListJob& J = a.job[j];
+    const int64_t n = list_count(J);
+    for (int64_t e = gtid; e < n; e += gstride) atomicAdd(&J.cnt[list_key(a, J.in, e) >> a.shift], 1u);
+  }
+  grid.sync();
+  // CSR offsets: block b scans the chunk [b chunk, (b + 1) chunk) after the
+  // partial sums of the chunks before it
+  const int64_t chunk = (M + gridDim.x - 1) / gridDim.x;
+  const int64_t c0 = (int64_t)blockIdx.x * chunk, c1 = min64(M, c0 + chunk);
+  for (int j = 0; j < 2; ++j) {
+    uint32_t v = 0;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) v += __ldcg(a.job[j].cnt + i);
+    uint32_t tot;
+    block_scan_excl(v, wt, tot);
+    if (threadIdx.x == 0) a.partial[j * gridDim.x + blockIdx.x] = tot;
+  }
+  grid.sync();
+  for (int j = 0; j < 2; ++j) {
+    const ListJob& J = a.job[j];
+    uint32_t v = 0;
+    for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) v += __ldcg(a.partial + j * gridDim.x + b);
+    uint32_t base;
+    block_scan_excl(v, wt, base);
+    for (int64_t i0 = c0; i0 < c1; i0 += blockDim.x) {
+      const int64_t i = i0 + threadIdx.x;
+      const uint32_t c = i < c1 ? __ldcg(J.cnt + i) : 0u;
+      uint32_t t;
+      const uint32_t ex = block_scan_excl(c, wt, t);
+      if (i < c1) J.off[i] = (int32_t)(base + ex);
+      base += t;
     }
   }
+  grid.sync();
+  for (int j = 0; j < 2; ++j) {
+    const ListJob& J = a.job[j];
+    const int64_t n = list_count(J);
+    for (int64_t e = gtid; e < n; e += gstride) {
+      const uint64_t k = list_key(a, J.in, e);
+      const int64_t t = (int64_t)(k >> a.shift);
+      const int64_t pos = (int64_t)__ldcg(J.off + t) + atomicAdd(&J.fill[t], 1u);
+      J.tmp[pos] = k;
+    }
+  }
+  grid.sync();
+  // rank every segment by key; one warp per major node
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = gtid >> 5, nwarps = gstride >> 5;
+  const uint64_t mask = ((uint64_t)1 << a.shift) - 1;
+  const double s3[3] = {1.0, 1.0, a.scal[0]};
+  const double inv = a.scal[3];
+  for (int64_t w = gw; w < 2 * M; w += nwarps) {
+    const int j = w >= M ? 1 : 0;
+    const int64_t t = w - j * M;
+    if (t >= M - 1) continue;
+    const ListJob& J = a.job[j];
+    const int64_t lo = __ldcg(J.off + t), hi = __ldcg(J.off + t + 1);
+    const int n = (int)(hi - lo);
+    if (n <= 0) continue;
+    const unsigned long long* seg = reinterpret_cast<const unsigned long long*>(J.tmp) + lo;
+    const bool staged = n <= kSegStage;
+    if (staged)
+      for (int i = lane; i < n; i += 32) stage[wib][i] = __ldcg(seg + i);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint64_t ki = staged ? stage[wib][i] : __ldcg(seg + i);
+      int r = 0;
+      for (int q = 0; q < n; ++q) r += (staged ? stage[wib][q] : __ldcg(seg + q)) < ki ? 1 : 0;
+      const int64_t dst = lo + r;
+      J.out[dst] = ki;
+      const double* ca = a.ncen + 3 * (ki >> a.shift);
+      const double* cb = a.ncen + 3 * (ki & mask);
+      double dc[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dc[d] = (s3[d] * (ca[d] - cb[d])) * inv;
+      if (kFP32) {
+        float h[3], l[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          h[d] = (float)dc[d];
+          l[d] = (float)(dc[d] - (double)h[d]);
+        }
+        float4* o = static_cast<float4*>(J.dc);
+        o[2 * dst] = make_float4(h[0], h[1], h[2], 0.f);
+        o[2 * dst + 1] = make_float4(l[0], l[1], l[2], 0.f);
+      } else {
+        static_cast<double4*>(J.dc)[dst] = make_double4(dc[0], dc[1], dc[2], 0.0);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <bool kFP32>
+__global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  Counters* cnt = a.cnt;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.front[0][0] = make_int2(1, 1);
+    cnt->frontier_count[0] = 1;
+    cnt->frontier_count[1] = 0;
+    cnt->frontier_count[2] = 0;
+    cnt->p2p_count = 0;
+    cnt->m2l_count = 0;
+  }
+  grid.sync();
+  const int leaf0 = 1 << a.kappa;
+  const int shift = a.lists.shift;
+  const double* ncen = a.lists.ncen;
+  const double s[3] = {1.0, 1.0, a.lists.scal[0]};
+  const int steps = 2 * a.kappa + 1;
+  for (int it = 0; it < steps; ++it) {
+    const int2* fin = a.front[it & 1];
+    int2* fout = a.front[(it + 1) & 1];
+    const int64_t nin = (int64_t)__ldcg(&cnt->frontier_count[it % 3]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt->frontier_count[(it + 2) % 3] = 0;
+    unsigned long long* nout = &cnt->frontier_count[(it + 1) % 3];
+    const int64_t n = min64(nin, a.cap_front);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const int2 pr = __ldcg(fin + e);
+      const int t = pr.x, u = pr.y;
+      const bool lt = t >= leaf0, lu = u >= leaf0;
+      if (lt && lu) {
+        push(&cnt->p2p_count, a.cap_p2p, a.p2p, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfP2P);
+        continue;
+      }
+      const double rt = a.ndiam[t], ru = a.ndiam[u];
+      double v[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = __dmul_rn(s[k], __dsub_rn(ncen[3 * t + k], ncen[3 * u + k]));
+      const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
+                                            __dmul_rn(v[2], v[2])));
+      const double ratio = __ddiv_rn(rt >= ru ? rt : ru, d);
+      if (ratio < a.eta) {
+        push(&cnt->m2l_count, a.cap_m2l, a.m2l, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfM2L);
+        continue;
+      }
+      int2 c0, c1;
+      if (lt || (!lu && !(rt > ru))) {  // split the source
+        c0 = make_int2(t, 2 * u);
+        c1 = make_int2(t, 2 * u + 1);
+      } else {                          // split the target
+        c0 = make_int2(2 * t, u);
+        c1 = make_int2(2 * t + 1, u);
+      }
+      unsigned long long at = atomicAdd(nout, 2ull);
+      if ((int64_t)at + 1 < a.cap_front) {
+        fout[at] = c0;
+        fout[at + 1] = c1;
+      } else {
+        atomicOr(&cnt->err, kErrOvfFrontier);
+      }
+    }
+    grid.sync();
+  }
+  // every block sees the same final flags: on any error no list is ordered
+  if (__ldcg(&cnt->err) != 0u) return;
+  order_lists<kFP32>(grid, a.lists);
+}
+
+template <bool kFP32>
+__global__ void __launch_bounds__(kTravThreads) k_lists_src(ListArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  order_lists<kFP32>(grid, a);
+}
+
+// Blocks of a cooperative launch of `kern`: all co-resident, at most `cap`.
+template <typename K>
+int coop_grid(K kern, int64_t cap, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTravThreads, 0));
+  if (per_sm < 1) return FMM_EINVAL;
+  *grid = (int)std::min<int64_t>((int64_t)per_sm * sms, cap);
+  return FMM_OK;
+}
+
+ListArgs list_args(fmm_plan_s* P, bool swap) {
+  const Layout& L = P->lay;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  ListArgs a;
+  a.swap = swap;
+  a.shift = P->kappa + 1;
+  a.C = P->C;
+  a.ncen = ws_ptr<double>(P, L.ncen);
+  a.scal = ws_ptr<double>(P, L.scal);
+  a.partial = ws_ptr<uint32_t>(P, L.tpart);
+  uint32_t* tc = ws_ptr<uint32_t>(P, L.tcnt);
+  const int64_t M = P->C + 2;
+  uint64_t* tmp = ws_ptr<uint64_t>(P, L.keys_alt);
+  for (int j = 0; j < 2; ++j) {
+    ListJob& J = a.job[j];
+    const bool p2p = j == 0;
+    J.n = p2p ? &cnt->p2p_count : &cnt->m2l_count;
+    J.cap = p2p ? P->cap_p2p : P->cap_m2l;
+    J.cnt = tc + (2 * j) * M;
+    J.fill = tc + (2 * j + 1) * M;
+    J.tmp = tmp + (p2p ? 0 : P->cap_p2p);
+    if (!swap) {  // forward: raw appends (in the source-major buffers) -> target-major lists
+      J.in = ws_ptr<uint64_t>(P, p2p ? L.p2p_src : L.m2l_src);
+      J.out = ws_ptr<uint64_t>(P, p2p ? L.p2p : L.m2l);
+      J.off = ws_ptr<int32_t>(P, p2p ? L.p2p_off : L.m2l_off);
+      J.dc = P->ws + (p2p ? L.p2p_dc : L.m2l_dc);
+    } else {      // adjoint: target-major lists -> source-major lists
+      J.in = ws_ptr<uint64_t>(P, p2p ? L.p2p : L.m2l);
+      J.out = ws_ptr<uint64_t>(P, p2p ? L.p2p_src : L.m2l_src);
+      J.off = ws_ptr<int32_t>(P, p2p ? L.p2p_soff : L.m2l_soff);
+      J.dc = P->ws + (p2p ? L.p2p_sdc : L.m2l_sdc);
+    }
+  }
+  return a;
 }
 
 }  // namespace
 
-int pair_offsets(fmm_plan_s* P, size_t keys_off, int64_t count, size_t out_off, cudaStream_t s) {
-  if (count <= 0) return FMM_OK;
-  const Layout& L = P->lay;
-  const int shift = P->kappa + 1;
-  const unsigned g = (unsigned)std::min<int64_t>(div_up(count, 256), 4096);
-  if (P->precision == FMM_FP32)
-    k_pair_dc<true><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, keys_off), count, shift, ws_ptr<double>(P, L.ncen),
-                                      ws_ptr<double>(P, L.scal), P->ws + out_off);
-  else
-    k_pair_dc<false><<<g, 256, 0, s>>>(ws_ptr<uint64_t>(P, keys_off), count, shift, ws_ptr<double>(P, L.ncen),
-                                       ws_ptr<double>(P, L.scal), P->ws + out_off);
-  FMM_LAUNCH_CHECK();
-  return FMM_OK;
-}
-
-int run_pair_offsets(fmm_plan_s* P, cudaStream_t s) {
-  const Layout& L = P->lay;
-  int rc = pair_offsets(P, L.p2p, P->p2p_count, L.p2p_dc, s);
-  if (rc != FMM_OK) return rc;
-  return pair_offsets(P, L.m2l, P->m2l_count, L.m2l_dc, s);
-}
-
 int run_traverse(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
-  Counters* cnt = ws_ptr<Counters>(P, L.counters);
-  int2* f[2] = {ws_ptr<int2>(P, L.front0), ws_ptr<int2>(P, L.front1)};
-  k_trav_init<<<1, 32, 0, s>>>(cnt, f[0]);
-  FMM_LAUNCH_CHECK();
-  const int shift = P->kappa + 1;
-  const int steps = 2 * P->kappa + 1;
-  for (int it = 0; it < steps; ++it) {
-    k_trav_step<<<152 * 4, 256, 0, s>>>(f[it & 1], it, f[(it + 1) & 1], cnt, P->cap_frontier,
-                                         ws_ptr<uint64_t>(P, L.p2p), P->cap_p2p, ws_ptr<uint64_t>(P, L.m2l),
-                                         P->cap_m2l, ws_ptr<double>(P, L.ncen), ws_ptr<double>(P, L.ndiam),
-                                         ws_ptr<double>(P, L.scal), P->eta, P->kappa, shift);
-    FMM_LAUNCH_CHECK();
-  }
-  return FMM_OK;
-}
-
-// Sort one list in place (keys sorted by the packed pair), build its CSR.
-static int sort_list(fmm_plan_s* P, uint64_t* list, int64_t count, int32_t* off, cudaStream_t s) {
-  const Layout& L = P->lay;
-  const int shift = P->kappa + 1;
-  bool alt = false;
-  int rc = radix_sort(list, ws_ptr<uint64_t>(P, L.keys_alt), nullptr, nullptr, count, 0, 2 * shift,
-                      ws_ptr<uint32_t>(P, L.hist), ws_ptr<uint32_t>(P, L.scan_tmp), (int64_t)L.nblk_sort, s, &alt);
+  TravArgs a;
+  a.cnt = ws_ptr<Counters>(P, L.counters);
+  a.front[0] = ws_ptr<int2>(P, L.front0);
+  a.front[1] = ws_ptr<int2>(P, L.front1);
+  a.cap_front = P->cap_frontier;
+  a.p2p = ws_ptr<uint64_t>(P, L.p2p_src);
+  a.cap_p2p = P->cap_p2p;
+  a.m2l = ws_ptr<uint64_t>(P, L.m2l_src);
+  a.cap_m2l = P->cap_m2l;
+  a.ndiam = ws_ptr<double>(P, L.ndiam);
+  a.eta = P->eta;
+  a.kappa = P->kappa;
+  a.lists = list_args(P, false);
+  const bool f32 = P->precision == FMM_FP32;
+  void* kern = f32 ? (void*)k_traverse<true> : (void*)k_traverse<false>;
+  int grid = 0;
+  int rc = f32 ? coop_grid(k_traverse<true>, kTravPartials, &grid) : coop_grid(k_traverse<false>, kTravPartials, &grid);
   if (rc != FMM_OK) return rc;
-  if (alt && count > 0) {
-    FMM_CUDA_TRY(cudaMemcpyAsync(list, ws_ptr<uint64_t>(P, L.keys_alt), sizeof(uint64_t) * count,
-                                 cudaMemcpyDeviceToDevice, s));
-  }
-  k_csr<<<(unsigned)div_up(P->C + 2, 256), 256, 0, s>>>(list, count, shift, P->C, off);
+  void* args[] = {&a};
+  FMM_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTravThreads), args, 0, s));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
 
-int run_list_sort(fmm_plan_s* P, cudaStream_t s) {
-  const Layout& L = P->lay;
-  int rc = sort_list(P, ws_ptr<uint64_t>(P, L.p2p), P->p2p_count, ws_ptr<int32_t>(P, L.p2p_off), s);
-  if (rc != FMM_OK) return rc;
-  return sort_list(P, ws_ptr<uint64_t>(P, L.m2l), P->m2l_count, ws_ptr<int32_t>(P, L.m2l_off), s);
-}
-
-// Source-major lists for the adjoint: the transposed pairs, sorted, with CSR by source.
+// Source-major lists for the adjoint: pairs (s, t) sorted by (source,
+// target), CSR by source, offsets c_s - c_t.
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s) {
-  const Layout& L = P->lay;
-  const int shift = P->kappa + 1;
-  const int gs = 1024;
-  if (P->p2p_count > 0) {
-    k_swap_pairs<<<gs, 256, 0, s>>>(ws_ptr<uint64_t>(P, L.p2p), P->p2p_count, shift, ws_ptr<uint64_t>(P, L.p2p_src));
-    FMM_LAUNCH_CHECK();
-  }
-  if (P->m2l_count > 0) {
-    k_swap_pairs<<<gs, 256, 0, s>>>(ws_ptr<uint64_t>(P, L.m2l), P->m2l_count, shift, ws_ptr<uint64_t>(P, L.m2l_src));
-    FMM_LAUNCH_CHECK();
-  }
-  int rc = sort_list(P, ws_ptr<uint64_t>(P, L.p2p_src), P->p2p_count, ws_ptr<int32_t>(P, L.p2p_soff), s);
+  ListArgs a = list_args(P, true);
+  const bool f32 = P->precision == FMM_FP32;
+  void* kern = f32 ? (void*)k_lists_src<true> : (void*)k_lists_src<false>;
+  int grid = 0;
+  int rc = f32 ? coop_grid(k_lists_src<true>, kTravPartials, &grid) : coop_grid(k_lists_src<false>, kTravPartials, &grid);
   if (rc != FMM_OK) return rc;
-  rc = sort_list(P, ws_ptr<uint64_t>(P, L.m2l_src), P->m2l_count, ws_ptr<int32_t>(P, L.m2l_soff), s);
-  if (rc != FMM_OK) return rc;
-  // offsets c_s - c_t of the source-major pairs (s, t)
-  rc = pair_offsets(P, L.p2p_src, P->p2p_count, L.p2p_sdc, s);
-  if (rc != FMM_OK) return rc;
-  return pair_offsets(P, L.m2l_src, P->m2l_count, L.m2l_sdc, s);
+  void* args[] = {&a};
+  FMM_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTravThreads), args, 0, s));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
 }
 
 }  // namespace fmm

@@ -158,12 +158,37 @@ __global__ void k_node_split(const double* __restrict__ x, const int32_t* __rest
   nmed[i] = rank[ax * N + A[ax * N + st + h1 - 1]];
 }
 
-__device__ __forceinline__ bool part_flag(const int32_t* __restrict__ Ak, const int32_t* __restrict__ rank,
-                                          int64_t N, int64_t pos, int64_t node,
-                                          const int32_t* __restrict__ naxis,
-                                          const int32_t* __restrict__ nmed) {
-  const int ax = naxis[node];
-  return rank[ax * N + Ak[pos]] <= nmed[node];
+// Flags "goes to the first child" (rank along the node's split axis <= the
+// median's rank) of the kPartItems slots from `base` on, and their nodes.
+// The loads of one phase are independent, so they are all in flight at once.
+__device__ __forceinline__ uint32_t part_flags(const int32_t* __restrict__ Ak, const int32_t* __restrict__ rank,
+                                               int64_t N, const int64_t* __restrict__ nstart, int64_t first,
+                                               const int32_t* __restrict__ naxis, const int32_t* __restrict__ nmed,
+                                               int64_t base, int64_t (&nd)[kPartItems]) {
+  int32_t id[kPartItems];
+#pragma unroll
+  for (int j = 0; j < kPartItems; ++j) id[j] = base + j < N ? Ak[base + j] : 0;
+  int64_t node = -1, node_end = -1;
+#pragma unroll
+  for (int j = 0; j < kPartItems; ++j) {
+    const int64_t pos = base + j;
+    if (pos < N && pos >= node_end) {
+      node = find_node(nstart, first, first, pos);
+      node_end = (node + 1 < 2 * first) ? nstart[node + 1] : N;
+    }
+    nd[j] = pos < N ? node : -1;
+  }
+  int ax[kPartItems], med[kPartItems];
+#pragma unroll
+  for (int j = 0; j < kPartItems; ++j) {
+    ax[j] = nd[j] >= 0 ? naxis[nd[j]] : 0;
+    med[j] = nd[j] >= 0 ? nmed[nd[j]] : -1;
+  }
+  uint32_t f = 0;
+#pragma unroll
+  for (int j = 0; j < kPartItems; ++j)
+    if (nd[j] >= 0 && rank[(int64_t)ax[j] * N + id[j]] <= med[j]) f |= 1u << j;
+  return f;
 }
 
 // Per-chunk count of elements going to the first child (grid.y = array k).
@@ -176,17 +201,8 @@ __global__ void __launch_bounds__(kPartThreads) k_part_count(
   const int32_t* Ak = A + (int64_t)k * N;
   const int64_t first = (int64_t)1 << level;
   const int64_t base = (int64_t)blockIdx.x * kPartChunk + (int64_t)threadIdx.x * kPartItems;
-  uint32_t c = 0;
-  int64_t node = -1, node_end = -1;
-  for (int j = 0; j < kPartItems; ++j) {
-    int64_t pos = base + j;
-    if (pos >= N) break;
-    if (pos >= node_end) {
-      node = find_node(nstart, first, first, pos);
-      node_end = (node + 1 < 2 * first) ? nstart[node + 1] : N;
-    }
-    c += part_flag(Ak, rank, N, pos, node, naxis, nmed) ? 1u : 0u;
-  }
+  int64_t nd[kPartItems];
+  uint32_t c = __popc(part_flags(Ak, rank, N, nstart, first, naxis, nmed, base, nd));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -212,24 +228,9 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
   int32_t* Ok = Aout + (int64_t)k * N;
   const int64_t first = (int64_t)1 << level;
   const int64_t base = (int64_t)blockIdx.x * kPartChunk + (int64_t)threadIdx.x * kPartItems;
-  bool f[kPartItems];
   int64_t nd[kPartItems];
-  uint32_t c = 0;
-  int64_t node = -1, node_end = -1;
-  for (int j = 0; j < kPartItems; ++j) {
-    int64_t pos = base + j;
-    f[j] = false;
-    nd[j] = -1;
-    if (pos >= N) continue;
-    if (pos >= node_end) {
-      node = find_node(nstart, first, first, pos);
-      node_end = (node + 1 < 2 * first) ? nstart[node + 1] : N;
-    }
-    nd[j] = node;
-    f[j] = part_flag(Ak, rank, N, pos, node, naxis, nmed);
-    c += f[j] ? 1u : 0u;
-  }
-  uint32_t tot;
+  const uint32_t fm = part_flags(Ak, rank, N, nstart, first, naxis, nmed, base, nd);
+  const uint32_t c = __popc(fm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {  // first-child elements before this chunk
     uint32_t b0;
@@ -260,21 +261,20 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
       if (lane >= o) wi += t;
     }
     if (lane < nw) wt[lane] = wi - w;
-    if (lane == nw - 1) wt[32] = wi;
   }
   __syncthreads();
-  tot = wt[32];
-  (void)tot;
   int64_t P = (int64_t)sbase + wt[warp] + (inc - c);
+#pragma unroll
   for (int j = 0; j < kPartItems; ++j) {
-    int64_t pos = base + j;
+    const int64_t pos = base + j;
     if (pos >= N) break;
     const int64_t n0 = nd[j];
+    const bool f = (fm >> j) & 1u;
     const int64_t st = nstart[n0], cnt = ncount[n0], h1 = (cnt + 1) / 2;
     const int64_t lb = P - nleftpre[n0];  // first-child elements before pos inside the node
-    const int64_t dst = f[j] ? st + lb : st + h1 + ((pos - st) - lb);
+    const int64_t dst = f ? st + lb : st + h1 + ((pos - st) - lb);
     Ok[dst] = Ak[pos];
-    P += f[j] ? 1 : 0;
+    P += f ? 1 : 0;
   }
 }
 
@@ -285,49 +285,49 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(
 // node followed by the stable partition of every node's slot ranges.  Inside
 // a node the split axis' array is in rank order, so "rank <= median rank" is
 // "slot among the first ceil(c/2) of that array": each member's flag is read
-// off the split axis' array and no rank is looked up but the median's.
+// off the split axis' array and no rank is looked up but the median's.  The
+// children's slot ranges follow from the parent's by the same halving rule
+// as the plan's node tables (first child ceil(c/2)).
 constexpr int kSubSlots = 4096;
 constexpr int kSubThreads = 1024;
-constexpr int kSubItems = 3 * kSubSlots / kSubThreads;
-constexpr int kSubNodes = kSubSlots / 2;  // a node above the leaves has >= 2 members
-static_assert(kSubItems <= 32, "flags are kept in one 32-bit mask per thread");
-static_assert(3 * 2 * kSubSlots >= 4 * kSubSlots, "x-ranks fit in the second slot buffer");
+constexpr int kSubPer = kSubSlots / kSubThreads;  // consecutive slots per thread, in each array
+constexpr int kSubNodes = kSubSlots / 2;          // a node above the leaves has >= 2 members
 
 struct SubtreeSmem {
-  uint16_t arr[2][3][kSubSlots];  // (arr[1] holds 4-byte x-ranks before the first level)  // local ids by slot, current and next level
+  uint16_t arr[2][3][kSubSlots];  // local ids by slot, current and next level
+                                  // (arr[1] holds 4-byte x-ranks before the first level)
   int32_t gid[kSubSlots];         // local id -> input index
   uint16_t seg[kSubSlots];        // slot -> node of the current level (relative)
   uint8_t flag[kSubSlots];        // local id -> goes to the first child
-  uint16_t nst[kSubNodes], ncnt[kSubNodes];
+  uint16_t nst[2][kSubNodes], ncnt[2][kSubNodes];  // node slot ranges, current and previous level
   uint8_t nax[kSubNodes];
-  uint32_t npre[3][kSubNodes];    // first-child elements before each node's start
-  uint32_t wt[33];
+  uint64_t npre[kSubNodes];       // first-child elements before each node's start, 16 bits per array
+  uint64_t wt[33];
 };
+static_assert(sizeof(uint16_t) * 3 * kSubSlots >= sizeof(int32_t) * kSubSlots, "x-ranks fit in arr[1]");
 
-__device__ __forceinline__ uint32_t sub_block_scan(uint32_t v, uint32_t* wt) {
+__device__ __forceinline__ uint64_t sub_block_scan(uint64_t v, uint64_t* wt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t inc = v;
+  uint64_t inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += t;
   }
   if (lane == 31) wt[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    const uint32_t w = wt[lane];
-    uint32_t wi = w;
+    const uint64_t w = wt[lane];
+    uint64_t wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      const uint64_t t = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += t;
     }
     wt[lane] = wi - w;
   }
   __syncthreads();
-  const uint32_t r = wt[warp] + inc - v;
-  __syncthreads();
-  return r;
+  return wt[warp] + inc - v;
 }
 
 __global__ void __launch_bounds__(kSubThreads) k_subtree(
@@ -343,34 +343,50 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
   const double sz = scal[0];
   // local ids: slot in the x-array; the y- and z-arrays find theirs by the
   // x-rank, which increases along the x-array's slots
-  int32_t* xr = reinterpret_cast<int32_t*>(&S.arr[1][0][0]);  // x-ranks by slot, until level ls
-  for (int j = threadIdx.x; j < c; j += blockDim.x) {
+  int32_t* xr = reinterpret_cast<int32_t*>(&S.arr[1][0][0]);
+  for (int j = threadIdx.x; j < c; j += kSubThreads) {
     const int32_t e = A[st0 + j];
     S.gid[j] = e;
     xr[j] = rank[e];
     S.arr[0][0][j] = (uint16_t)j;
     S.seg[j] = 0;
   }
-  __syncthreads();
-  for (int g = threadIdx.x; g < 2 * c; g += blockDim.x) {
-    const int k = 1 + g / c, j = g - (k - 1) * c;
-    const int32_t rx = rank[A[(int64_t)k * N + st0 + j]];
-    int lo = 0, hi = c - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (xr[mid] < rx) lo = mid + 1; else hi = mid;
-    }
-    S.arr[0][k][j] = (uint16_t)lo;
+  if (threadIdx.x == 0) {
+    S.nst[1][0] = 0;
+    S.ncnt[1][0] = (uint16_t)c;
   }
-  int cur = 0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    for (int j = threadIdx.x; j < c; j += kSubThreads) {
+      const int32_t rx = rank[A[(int64_t)k * N + st0 + j]];
+      int lo = 0, hi = c - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (xr[mid] < rx) lo = mid + 1; else hi = mid;
+      }
+      S.arr[0][k][j] = (uint16_t)lo;
+    }
+  }
+  const int j0 = threadIdx.x * kSubPer;  // this thread's slots j0 .. j0 + kSubPer - 1
+  int cur = 0, pb = 1;                   // slot buffer; node buffer of the previous level
   for (int l = ls;; ++l) {
     __syncthreads();
     const int64_t first = root << (l - ls);
     const int nodes = 1 << (l - ls);
-    for (int u = threadIdx.x; u < nodes; u += blockDim.x) {  // boxes, Alg. 1 axis, Appendix B median
+    for (int u = threadIdx.x; u < nodes; u += kSubThreads) {  // boxes, Alg. 1 axis, Appendix B median
+      int st, cnt;
+      if (l == ls) {
+        st = 0;
+        cnt = c;
+      } else {
+        const int pst = S.nst[pb][u >> 1], pc = S.ncnt[pb][u >> 1], ph = (pc + 1) / 2;
+        st = (u & 1) ? pst + ph : pst;
+        cnt = (u & 1) ? pc - ph : ph;
+      }
       const int64_t g = first + u;
-      const int st = (int)(nstart[g] - st0), cnt = (int)ncount[g];
       double w[3];
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         const double lo = x[3 * (int64_t)S.gid[S.arr[cur][k][st]] + k];
         const double hi = x[3 * (int64_t)S.gid[S.arr[cur][k][st + cnt - 1]] + k];
@@ -389,70 +405,74 @@ __global__ void __launch_bounds__(kSubThreads) k_subtree(
       const int h1 = (cnt + 1) / 2;
       naxis[g] = ax;
       nmed[g] = rank[(int64_t)ax * N + S.gid[S.arr[cur][ax][st + h1 - 1]]];
-      S.nst[u] = (uint16_t)st;
-      S.ncnt[u] = (uint16_t)cnt;
+      S.nst[pb ^ 1][u] = (uint16_t)st;
+      S.ncnt[pb ^ 1][u] = (uint16_t)cnt;
       S.nax[u] = (uint8_t)ax;
     }
     if (l == kappa) break;
+    pb ^= 1;
+    const uint16_t* nst = S.nst[pb];
+    const uint16_t* ncnt = S.ncnt[pb];
     __syncthreads();
-    for (int j = threadIdx.x; j < c; j += blockDim.x) {
-      const int u = S.seg[j];
-      S.flag[S.arr[cur][S.nax[u]][j]] = (uint8_t)(j - S.nst[u] < (S.ncnt[u] + 1) / 2);
-    }
-    __syncthreads();
-    // stable partition of the three arrays: one scan over their concatenation
-    const int g0 = threadIdx.x * kSubItems;
-    uint32_t fm = 0, cntf = 0;
+    int su[kSubPer];
 #pragma unroll
-    for (int i = 0; i < kSubItems; ++i) {
-      const int g = g0 + i;
-      if (g < 3 * c) {
-        const int k = g / c, j = g - k * c;
-        const uint32_t f = S.flag[S.arr[cur][k][j]];
-        fm |= f << i;
-        cntf += f;
+    for (int i = 0; i < kSubPer; ++i) {
+      const int j = j0 + i;
+      su[i] = j < c ? S.seg[j] : 0;
+      if (j < c) {
+        const int u = su[i];
+        S.flag[S.arr[cur][S.nax[u]][j]] = (uint8_t)(j - nst[u] < (ncnt[u] + 1) / 2);
       }
     }
-    const uint32_t pre = sub_block_scan(cntf, S.wt);
-    uint32_t run = pre;
+    __syncthreads();
+    // stable partition of the three arrays; one scan, 16 bits per array
+    uint32_t fm = 0;
+    uint64_t cnt3 = 0;
 #pragma unroll
-    for (int i = 0; i < kSubItems; ++i) {
-      const int g = g0 + i;
-      if (g < 3 * c) {
-        const int k = g / c, j = g - k * c;
-        const int u = S.seg[j];
-        if (j == S.nst[u]) S.npre[k][u] = run;
-        run += (fm >> i) & 1u;
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < kSubPer; ++i) {
+        const int j = j0 + i;
+        const uint32_t f = j < c ? S.flag[S.arr[cur][k][j]] : 0u;
+        fm |= f << (k * kSubPer + i);
+        cnt3 += (uint64_t)f << (16 * k);
       }
+    const uint64_t pre = sub_block_scan(cnt3, S.wt);
+    uint64_t run = pre;
+#pragma unroll
+    for (int i = 0; i < kSubPer; ++i) {
+      const int j = j0 + i;
+      if (j < c && j == nst[su[i]]) S.npre[su[i]] = run;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) run += (uint64_t)((fm >> (k * kSubPer + i)) & 1u) << (16 * k);
     }
     __syncthreads();
     run = pre;
 #pragma unroll
-    for (int i = 0; i < kSubItems; ++i) {
-      const int g = g0 + i;
-      if (g < 3 * c) {
-        const int k = g / c, j = g - k * c;
-        const int u = S.seg[j];
-        const int st = S.nst[u], h1 = (S.ncnt[u] + 1) / 2;
-        const int lb = (int)(run - S.npre[k][u]);
-        const bool f = (fm >> i) & 1u;
-        const int dst = f ? st + lb : st + h1 + ((j - st) - lb);
-        S.arr[cur ^ 1][k][dst] = S.arr[cur][k][j];
-        run += f ? 1u : 0u;
+    for (int i = 0; i < kSubPer; ++i) {
+      const int j = j0 + i;
+      if (j < c) {
+        const int u = su[i];
+        const int st = nst[u], h1 = (ncnt[u] + 1) / 2;
+        const uint64_t np = S.npre[u];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int lb = (int)(((run >> (16 * k)) - (np >> (16 * k))) & 0xffffu);
+          const bool f = (fm >> (k * kSubPer + i)) & 1u;
+          const int dst = f ? st + lb : st + h1 + ((j - st) - lb);
+          S.arr[cur ^ 1][k][dst] = S.arr[cur][k][j];
+        }
+        S.seg[j] = (uint16_t)(2 * u + (j - st >= h1 ? 1 : 0));
       }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < c; j += blockDim.x) {
-      const int u = S.seg[j];
-      S.seg[j] = (uint16_t)(2 * u + (j - S.nst[u] >= (S.ncnt[u] + 1) / 2 ? 1 : 0));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) run += (uint64_t)((fm >> (k * kSubPer + i)) & 1u) << (16 * k);
     }
     cur ^= 1;
   }
   __syncthreads();
-  for (int g = threadIdx.x; g < 3 * c; g += blockDim.x) {
-    const int k = g / c, j = g - k * c;
-    A[(int64_t)k * N + st0 + j] = S.gid[S.arr[cur][k][j]];
-  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    for (int j = threadIdx.x; j < c; j += kSubThreads) A[(int64_t)k * N + st0 + j] = S.gid[S.arr[cur][k][j]];
 }
 
 }  // namespace
