@@ -387,26 +387,69 @@ int launch_adj_m2l_fast(fmm_plan_s* P, cudaStream_t s) {
   return FMM_OK;
 }
 
+// Shared-memory bytes ahead of the per-leaf expansion: the staged source rows,
+// or the other groups' compensated sums (2 nc values per owned particle) when
+// those take more room.
+template <typename T>
+__host__ __device__ inline size_t stage_bytes(int rows, int kpt, int nc2, int groups, int NT) {
+  const size_t a = sizeof(typename Vec4<T>::type) * rows * (size_t)groups * NT;
+  const size_t b = sizeof(T) * (size_t)(groups - 1) * kpt * nc2 * NT;
+  return a > b ? a : b;
+}
+
+// The particle kernels run `groups` groups of NT threads per leaf, every
+// group with its own share of the pairs; group 0 adds the compensated sums
+// (sum - comp) of groups 1, 2, ... in that order.  cb overlays the staging
+// rows, which no thread reads any more.
+template <typename T, int KPT, int NC>
+__device__ __forceinline__ void combine_groups(T (&acc)[KPT][NC], T (&cmp)[KPT][NC], T* cb, int groups, int grp,
+                                               int NT, int lt) {
+  if (groups <= 1) return;
+  if (grp > 0)
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        cb[(((grp - 1) * KPT + k) * 2 * NC + c) * NT + lt] = acc[k][c];
+        cb[(((grp - 1) * KPT + k) * 2 * NC + NC + c) * NT + lt] = cmp[k][c];
+      }
+  __syncthreads();
+  if (grp == 0)
+    for (int g2 = 1; g2 < groups; ++g2)
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          kahan_add(acc[k][c], cmp[k][c], cb[(((g2 - 1) * KPT + k) * 2 * NC + c) * NT + lt]);
+          kahan_add(acc[k][c], cmp[k][c], -cb[(((g2 - 1) * KPT + k) * 2 * NC + NC + c) * NT + lt]);
+        }
+  __syncthreads();
+}
+
 // Near field at the targets (J u over the target-major P2P list) plus the far
 // field at the targets (grad of the forward's cumulative local); writes the
 // target-side dL/dx' of every particle (leaf order).
 template <typename T, int KPT>
-__global__ void __launch_bounds__(256) k_adj_target(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
     const typename Vec4<T>::type* __restrict__ pb, const typename Vec4<T>::type* __restrict__ pl,
     const void* __restrict__ pdc_raw, const typename Vec4<T>::type* __restrict__ wle,
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lcum, Cheb ch, ChebD cd, int m,
-    typename Vec4<T>::type* __restrict__ gout) {
+    int groups, int chunks, typename Vec4<T>::type* __restrict__ gout) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 3 : 2;
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);
-  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [6][m]
-  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x;
-  const int64_t st = nstart[t], cnt = ncount[t];
+  const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  T* sl = reinterpret_cast<T*>(smem_raw + stage_bytes<T>(kRow, KPT, 6, groups, NT));  // [6][m]
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int64_t per_pass = (int64_t)KPT * NT;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * per_pass;
+  const int64_t st = nstart[t], cnt = min64(ncount[t], c0 + per_pass);
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gt = geo[t];
   const int b = off[t], e = off[t + 1];
@@ -421,14 +464,13 @@ __global__ void __launch_bounds__(256) k_adj_target(
     const T* Lt = Lcum + (size_t)t * 6 * m;
     for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
   }
-  const int64_t per_pass = (int64_t)KPT * blockDim.x;
-  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+  for (int64_t pass0 = c0; pass0 < cnt; pass0 += per_pass) {
     T ri[KPT][3], rl[KPT][3], we[KPT][3], wb[KPT][3];
     bool valid[KPT];
     T acc[KPT][3], cmp[KPT][3];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      const int64_t j = pass0 + lt + (int64_t)k * NT;
       valid[k] = j < cnt;
       const int64_t jj = st + (valid[k] ? j : 0);
       const V4 u = px[jj], a = wle[jj], c = wlb[jj];
@@ -487,7 +529,8 @@ __global__ void __launch_bounds__(256) k_adj_target(
         }
         __syncthreads();
         const int nj = (int)min64(blockDim.x, scnt - base);
-        for (int jj = 0; jj < nj; ++jj) {
+        const int share = (nj + groups - 1) / groups, j1 = min(nj, (grp + 1) * share);
+        for (int jj = grp * share; jj < j1; ++jj) {
           const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
           V4 ul;
           if constexpr (kSplit) ul = sp[kRow * jj + 2];
@@ -524,18 +567,19 @@ __global__ void __launch_bounds__(256) k_adj_target(
         for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], part[k][d]);
     }
     __syncthreads();
+    const int a3share = (np1 + groups - 1) / groups;
+    const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      if (!valid[k]) continue;
-      if (kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
+      if (valid[k] && kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
         T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
         const T lof = kSplit ? T(1) : T(0);
         basis_deriv<T>((ri[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, cd, lx, dx);
         basis_deriv<T>((ri[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, cd, ly, dy);
         basis_deriv<T>((ri[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, cd, lz, dz);
         T G[3] = {T(0), T(0), T(0)};
-        int mu = 0;
-        for (int a3 = 0; a3 < np1; ++a3) {
+        int mu = a3b * np1 * np1;
+        for (int a3 = a3b; a3 < a3e; ++a3) {
           for (int a2 = 0; a2 < np1; ++a2) {
             T s0 = T(0), sx = T(0);
             for (int a1 = 0; a1 < np1; ++a1, ++mu) {
@@ -552,7 +596,12 @@ __global__ void __launch_bounds__(256) k_adj_target(
 #pragma unroll
         for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], G[d] * invh[d]);
       }
-      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+    }
+    combine_groups<T, KPT, 3>(acc, cmp, reinterpret_cast<T*>(smem_raw), groups, grp, NT, lt);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (grp != 0 || !valid[k]) continue;
+      const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       V4 o;
       o.x = acc[k][0]; o.y = acc[k][1]; o.z = acc[k][2]; o.w = T(0);
       gout[pos] = o;
@@ -564,7 +613,7 @@ __global__ void __launch_bounds__(256) k_adj_target(
 // pushed-down Lambda, plus the target-side part; then the chain rule to
 // physical (x, p, q), written in input order.
 template <typename T, int KPT>
-__global__ void __launch_bounds__(256) k_adj_source(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_source(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
@@ -572,16 +621,20 @@ __global__ void __launch_bounds__(256) k_adj_source(
     const void* __restrict__ sdc_raw, const typename Vec4<T>::type* __restrict__ wle,
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lam, Cheb ch, ChebD cd, int m,
     const typename Vec4<T>::type* __restrict__ gtarget, const int32_t* __restrict__ perm,
-    const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q,
-    double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
+    const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q, int groups,
+    int chunks, double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 4 : 3;
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);
-  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [4][m]
-  const int64_t s = ((int64_t)1 << kappa) + blockIdx.x;
-  const int64_t st = nstart[s], cnt = ncount[s];
+  const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  T* sl = reinterpret_cast<T*>(smem_raw + stage_bytes<T>(kRow, KPT, 14, groups, NT));  // [4][m]
+  const int64_t s = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int64_t per_pass = (int64_t)KPT * NT;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * per_pass;
+  const int64_t st = nstart[s], cnt = min64(ncount[s], c0 + per_pass);
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gs = geo[s];
   const int b = off[s], e = off[s + 1];
@@ -596,14 +649,13 @@ __global__ void __launch_bounds__(256) k_adj_source(
     const T* Ls = Lam + (size_t)s * 4 * m;
     for (int o = threadIdx.x; o < 4 * m; o += blockDim.x) sl[o] = Ls[o];
   }
-  const int64_t per_pass = (int64_t)KPT * blockDim.x;
-  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+  for (int64_t pass0 = c0; pass0 < cnt; pass0 += per_pass) {
     T rj[KPT][3], rl[KPT][3], aj[KPT], bj[KPT][3];
     bool valid[KPT];
     T acc[KPT][7], cmp[KPT][7];  // (dL/da', dL/db~' x3, dL/dx' x3)
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      const int64_t j = pass0 + lt + (int64_t)k * NT;
       valid[k] = j < cnt;
       const int64_t jj = st + (valid[k] ? j : 0);
       const V4 u = px[jj], w = pb[jj];
@@ -664,7 +716,8 @@ __global__ void __launch_bounds__(256) k_adj_source(
         }
         __syncthreads();
         const int ni = (int)min64(blockDim.x, tcnt - base);
-        for (int ii = 0; ii < ni; ++ii) {
+        const int share = (ni + groups - 1) / groups, i1 = min(ni, (grp + 1) * share);
+        for (int ii = grp * share; ii < i1; ++ii) {
           const V4 u = sp[kRow * ii], we = sp[kRow * ii + 1], wb = sp[kRow * ii + 2];
           V4 ul;
           if constexpr (kSplit) ul = sp[kRow * ii + 3];
@@ -706,18 +759,19 @@ __global__ void __launch_bounds__(256) k_adj_source(
     }
     __syncthreads();
     const double gbar = scal[0], mu_u = scal[1], ell = scal[2];
+    const int a3share = (np1 + groups - 1) / groups;
+    const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      if (!valid[k]) continue;
-      if (kappa > 0) {  // far field at the source: through the P2M basis of its leaf
+      if (valid[k] && kappa > 0) {  // far field at the source: through the P2M basis of its leaf
         T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
         const T lof = kSplit ? T(1) : T(0);
         basis_deriv<T>((rj[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, cd, lx, dx);
         basis_deriv<T>((rj[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, cd, ly, dy);
         basis_deriv<T>((rj[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, cd, lz, dz);
         T F[4] = {T(0), T(0), T(0), T(0)}, G[3] = {T(0), T(0), T(0)};
-        int nu = 0;
-        for (int a3 = 0; a3 < np1; ++a3) {
+        int nu = a3b * np1 * np1;
+        for (int a3 = a3b; a3 < a3e; ++a3) {
           for (int a2 = 0; a2 < np1; ++a2) {
             T f[4] = {T(0), T(0), T(0), T(0)};
             T s0 = T(0), sx = T(0);
@@ -744,7 +798,12 @@ __global__ void __launch_bounds__(256) k_adj_source(
 #pragma unroll
         for (int d = 0; d < 3; ++d) kahan_add(acc[k][4 + d], cmp[k][4 + d], G[d] * invh[d]);
       }
-      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+    }
+    combine_groups<T, KPT, 7>(acc, cmp, reinterpret_cast<T*>(smem_raw), groups, grp, NT, lt);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (grp != 0 || !valid[k]) continue;
+      const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       const V4 gt = gtarget[pos];
       // internal (a', b~', x') -> physical (a, b, x)
       const double dA = (double)acc[k][0] / mu_u;
@@ -864,46 +923,29 @@ int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, d
   const Layout& L = P->lay;
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
-  const int kpt = P->leaf > 256 ? 2 : 1;
-  const int nt = (int)std::min<int64_t>(256, div_up(div_up(P->leaf, kpt), 32) * 32);
+  int NT, groups, chunks;
+  particle_shape(P->leaf, 1, &NT, &groups, &chunks);  // as the forward P2P
+  const int nt = groups * NT;
+  const unsigned grid = (unsigned)(P->nleaves * chunks);
   if (target_side) {
-    const size_t smem = sizeof(V4) * (kSplit ? 3 : 2) * nt + sizeof(T) * 6 * P->m;
-    static bool attr1 = false, attr2 = false;
-    if (kpt == 1) {
-      if (!attr1) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr1 = true; }
-      k_adj_target<T, 1><<<(unsigned)P->nleaves, nt, smem, s>>>(
-          ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
-          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part));
-    } else {
-      if (!attr2) { if (int rc = set_smem(k_adj_target<T, 2>)) return rc; attr2 = true; }
-      k_adj_target<T, 2><<<(unsigned)P->nleaves, nt, smem, s>>>(
-          ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
-          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part));
-    }
+    const size_t smem = stage_bytes<T>(kSplit ? 3 : 2, 1, 6, groups, NT) + sizeof(T) * 6 * P->m;
+    static bool attr = false;
+    if (!attr) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr = true; }
+    k_adj_target<T, 1><<<grid, nt, smem, s>>>(
+        ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+        ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
+        P->cheb, P->chebd, P->m, groups, chunks, ws_ptr<V4>(P, L.adj_part));
   } else {
-    const size_t smem = sizeof(V4) * (kSplit ? 4 : 3) * nt + sizeof(T) * 4 * P->m;
-    static bool attr1 = false, attr2 = false;
-    if (kpt == 1) {
-      if (!attr1) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr1 = true; }
-      k_adj_source<T, 1><<<(unsigned)P->nleaves, nt, smem, s>>>(
-          ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
-          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
-          q, dx, dp, dq);
-    } else {
-      if (!attr2) { if (int rc = set_smem(k_adj_source<T, 2>)) return rc; attr2 = true; }
-      k_adj_source<T, 2><<<(unsigned)P->nleaves, nt, smem, s>>>(
-          ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-          ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-          ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
-          P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
-          q, dx, dp, dq);
-    }
+    const size_t smem = stage_bytes<T>(kSplit ? 4 : 3, 1, 14, groups, NT) + sizeof(T) * 4 * P->m;
+    static bool attr = false;
+    if (!attr) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr = true; }
+    k_adj_source<T, 1><<<grid, nt, smem, s>>>(
+        ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+        ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
+        P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
+        q, groups, chunks, dx, dp, dq);
   }
   FMM_LAUNCH_CHECK();
   return FMM_OK;

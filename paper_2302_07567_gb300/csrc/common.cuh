@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -216,6 +217,16 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   T t = sum + y;
   comp = (t - sum) - y;
   sum = t;
+}
+
+// Thread shape of the particle-pair kernels (forward P2P, adjoint target and
+// source sides): blocks of `groups` groups of NT threads over chunks of
+// kpt NT targets of a leaf, `chunks` blocks per leaf.
+inline void particle_shape(int64_t leaf, int kpt, int* NT, int* groups, int* chunks) {
+  const int64_t per_thread = (leaf + kpt - 1) / kpt;
+  *NT = (int)std::min<int64_t>(64, (per_thread + 31) / 32 * 32);
+  *groups = *NT <= 32 ? 4 : 2;
+  *chunks = (int)((leaf + (int64_t)kpt * *NT - 1) / ((int64_t)kpt * *NT));
 }
 
 // Node of a breadth-first tree level containing slot `pos`: binary search in

@@ -1,10 +1,15 @@
 // P2P (Alg. 10) fused with L2P (Alg. 14) and the output transform.
 //
-// One block per target leaf drains the leaf's P2P list (sorted by target, so
-// each particle's fields are written by exactly one thread; Section 10).
-// Every thread owns KPT target particles.  Source leaves are contiguous
-// slot ranges of the leaf-ordered particle arrays, staged through shared
-// memory a block-width at a time.  A pair whose squared stretched, scaled
+// A block takes a chunk of KPT NT targets of one leaf and drains the leaf's
+// P2P list (sorted by target, so each particle's fields are written by
+// exactly one thread; Section 10).  Chunks of a few dozen targets give some
+// thousand blocks even for ~500 leaves, which keeps every SM busy to the
+// end.  The block is `groups` groups of NT threads; in every group a thread
+// owns KPT target particles.  Source leaves are contiguous slot ranges of the
+// leaf-ordered particle arrays, staged through shared memory a block-width
+// at a time; each group takes its own share of every staged batch (and of
+// the far-field sum), and group 0 adds the other groups' compensated sums in
+// group order, so the result does not depend on scheduling.  A pair whose squared stretched, scaled
 // separation is at or below tiny_sep2 (the particle itself, or two particles
 // at the same position, which the leaf-relative coordinates may place a few
 // units of the last place apart) contributes nothing.  Per-source-leaf partial sums are added with Kahan compensation.
@@ -34,22 +39,28 @@ namespace fmm {
 namespace {
 
 template <typename T, int KPT>
-__global__ void __launch_bounds__(256) k_p2p_l2p(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
     const typename Vec4<T>::type* __restrict__ pb, const float4* __restrict__ pl,  // Vec4<T> rows
     const void* __restrict__ pdc_raw, const T* __restrict__ Lcum, Cheb ch, int m,
-    const int32_t* __restrict__ perm, const double* __restrict__ scal, T* __restrict__ Eout,
+    const int32_t* __restrict__ perm, const double* __restrict__ scal, int groups, int chunks, T* __restrict__ Eout,
     T* __restrict__ Bout) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;  // hi + lo separations
   constexpr int kRow = kSplit ? 3 : 2;                      // V4 per staged source particle
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);                                // [blockDim][kRow]
-  T* sl = reinterpret_cast<T*>(smem_raw + sizeof(V4) * kRow * blockDim.x);  // [6][m]
-  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x;
-  const int64_t st = nstart[t], cnt = ncount[t];
+  const size_t stage = max(sizeof(V4) * kRow * blockDim.x,
+                           sizeof(T) * (size_t)(groups - 1) * KPT * 12 * (blockDim.x / groups));
+  T* sl = reinterpret_cast<T*>(smem_raw + stage);  // [6][m]
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  const int64_t per_pass = (int64_t)KPT * NT;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * per_pass;
+  const int64_t st = nstart[t], cnt = min64(ncount[t], c0 + per_pass);
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gt = geo[t];
   const int b = off[t], e = off[t + 1];
@@ -67,14 +78,13 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(
   }
   const double ell2 = scal[2] * scal[2];
   const T g2 = (T)(gbar * gbar);
-  const int64_t per_pass = (int64_t)KPT * blockDim.x;
-  for (int64_t pass0 = 0; pass0 < cnt; pass0 += per_pass) {
+  for (int64_t pass0 = c0; pass0 < cnt; pass0 += per_pass) {
     T ri[KPT][3], rl[KPT][3];
     bool valid[KPT];
     T acc[KPT][6], cmp[KPT][6];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      const int64_t j = pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+      const int64_t j = pass0 + lt + (int64_t)k * NT;
       valid[k] = j < cnt;
       const int64_t jj = st + (valid[k] ? j : 0);
       const V4 u = px[jj];
@@ -135,7 +145,8 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(
         }
         __syncthreads();
         const int nj = (int)min64(blockDim.x, scnt - base);
-        for (int jj = 0; jj < nj; ++jj) {
+        const int share = (nj + groups - 1) / groups, j1 = min(nj, (grp + 1) * share);
+        for (int jj = grp * share; jj < j1; ++jj) {
           const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
           V4 ul;
           if constexpr (kSplit) ul = sp[kRow * jj + 2];
@@ -183,18 +194,19 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(
     }
     __syncthreads();  // sl (loaded above) is visible to every thread from here on
 
+    const int a3share = (np1 + groups - 1) / groups;
+    const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      if (!valid[k]) continue;
-      if (kappa > 0) {  // far field: L2P from the cumulative local field of the leaf
+      if (valid[k] && kappa > 0) {  // far field: L2P from the cumulative local field of the leaf
         T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1];
         const T lof = kSplit ? T(1) : T(0);
         bary_basis<T>((ri[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, lx);
         bary_basis<T>((ri[k][1] + lof * rl[k][1]) * invh[1], deg[1], ch, ly);
         bary_basis<T>((ri[k][2] + lof * rl[k][2]) * invh[2], deg[2], ch, lz);
         T f[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        int mu = 0;
-        for (int a3 = 0; a3 < np1; ++a3) {
+        int mu = a3b * np1 * np1;
+        for (int a3 = a3b; a3 < a3e; ++a3) {
           for (int a2 = 0; a2 < np1; ++a2) {
             const T w = lz[a3] * ly[a2];
             T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -209,7 +221,33 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(
 #pragma unroll
         for (int c = 0; c < 6; ++c) kahan_add(acc[k][c], cmp[k][c], f[c]);
       }
-      const int64_t pos = st + pass0 + threadIdx.x + (int64_t)k * blockDim.x;
+    }
+    if (groups > 1) {  // group 0 adds the other groups' sums, in group order
+      T* cb = reinterpret_cast<T*>(smem_raw);  // [groups - 1][KPT][12][NT], over the staging rows
+      if (grp > 0)
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            cb[(((grp - 1) * KPT + k) * 12 + c) * NT + lt] = acc[k][c];
+            cb[(((grp - 1) * KPT + k) * 12 + 6 + c) * NT + lt] = cmp[k][c];
+          }
+      __syncthreads();
+      if (grp == 0)
+        for (int g2 = 1; g2 < groups; ++g2)
+#pragma unroll
+          for (int k = 0; k < KPT; ++k)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              kahan_add(acc[k][c], cmp[k][c], cb[(((g2 - 1) * KPT + k) * 12 + c) * NT + lt]);
+              kahan_add(acc[k][c], cmp[k][c], -cb[(((g2 - 1) * KPT + k) * 12 + 6 + c) * NT + lt]);
+            }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (grp != 0 || !valid[k]) continue;
+      const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       const int64_t i = perm[pos];
       Eout[3 * i + 0] = (T)(kE * (double)acc[k][0]);
       Eout[3 * i + 1] = (T)(kE * (double)acc[k][1]);
@@ -224,30 +262,33 @@ __global__ void __launch_bounds__(256) k_p2p_l2p(
 template <typename T, int KPT>
 int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   const Layout& L = P->lay;
-  const int nt = (int)std::min<int64_t>(256, div_up(div_up(P->leaf, KPT), 32) * 32);
+  int NT, groups, chunks;
+  particle_shape(P->leaf, KPT, &NT, &groups, &chunks);
+  const int nt = groups * NT;
   const int row = std::is_same<T, float>::value ? 3 : 2;
-  const size_t smem = sizeof(typename Vec4<T>::type) * row * nt + sizeof(T) * 6 * P->m;
+  const size_t stage = std::max(sizeof(typename Vec4<T>::type) * row * nt,
+                                sizeof(T) * (size_t)(groups - 1) * KPT * 12 * NT);
+  const size_t smem = stage + sizeof(T) * 6 * P->m;
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2p_l2p<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_p2p_l2p<T, KPT><<<(unsigned)P->nleaves, nt, smem, s>>>(
+  k_p2p_l2p<T, KPT><<<(unsigned)(P->nleaves * chunks), nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb), ws_ptr<float4>(P, L.pl),
       P->ws + L.p2p_dc, ws_ptr<T>(P, L.local), P->cheb, P->m, ws_ptr<int32_t>(P, L.perm),
-      ws_ptr<double>(P, L.scal), static_cast<T*>(E), static_cast<T*>(B));
+      ws_ptr<double>(P, L.scal), groups, chunks, static_cast<T*>(E), static_cast<T*>(B));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
 
 template <typename T>
 int p2p_t(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
-  // one target per thread up to 256 per leaf (two per thread measured slower:
-  // the extra registers cost more occupancy than the shared loads they save)
-  if (P->leaf <= 256) return launch<T, 1>(P, E, B, s);
-  return launch<T, 2>(P, E, B, s);
+  // one target per thread (two per thread measured slower: the extra
+  // registers cost more occupancy than the shared loads they save)
+  return launch<T, 1>(P, E, B, s);
 }
 
 }  // namespace
