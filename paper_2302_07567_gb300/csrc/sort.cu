@@ -3,10 +3,14 @@
 // Used by the tree build: one presort of the particles along each axis, so
 // that equal coordinates stay in input-index order, which is the tie rule of
 // the median split.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace fmm {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -16,7 +20,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
-// up to this many tiles the scatter kernel forms its digit offsets itself
+// up to this many tiles per batch every pass runs in one cooperative launch
 constexpr int64_t kFusedTiles = 64;
 
 // Exclusive prefix of `v` over the block (blocked arrangement); returns the
@@ -88,45 +92,107 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Block state of the stable scatter of one tile.
+struct ScatterSmem {
+  uint32_t wcnt[kSortWarps][256];  // per warp and digit: keys of the current round
+  uint32_t run[256];               // per digit: keys of the tile placed so far
+  uint32_t gbase[256];             // per digit: first output slot of this tile
+  uint32_t cnt[256];
+  uint32_t wt[33];
+};
+
+// The tile's keys (and values) in registers, thread-strided within each round.
+template <bool kCG>
+__device__ __forceinline__ void load_tile(const uint64_t* keys, const uint32_t* vals, int64_t base, int64_t n,
+                                          uint64_t (&kk)[kSortRounds], uint32_t (&vv)[kSortRounds]) {
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    if (kCG) {
+      kk[r] = i < n ? (uint64_t)__ldcg(reinterpret_cast<const unsigned long long*>(keys) + i) : 0ull;
+      vv[r] = (i < n && vals) ? __ldcg(vals + i) : 0u;
+    } else {
+      kk[r] = i < n ? keys[i] : 0ull;
+      vv[r] = (i < n && vals) ? vals[i] : 0u;
+    }
+  }
+}
+
+// Digit counts of the tile into S.cnt (valid after the call).
+__device__ __forceinline__ void tile_histogram(const uint64_t (&kk)[kSortRounds], int64_t base, int64_t n,
+                                               int shift, ScatterSmem& S) {
+  S.cnt[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned d = valid ? (unsigned)((kk[r] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&S.cnt[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+}
+
+// Stable scatter of the tile by its digit; S.gbase holds the tile's first
+// output slot of every digit.  Rounds go in input order, warps in order
+// inside a round and lanes in order inside a warp.
+__device__ __forceinline__ void tile_scatter(const uint64_t (&kk)[kSortRounds], const uint32_t (&vv)[kSortRounds],
+                                             int64_t base, int64_t n, int shift, bool with_vals, ScatterSmem& S,
+                                             uint64_t* keys_out, uint32_t* vals_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < kSortWarps; ++w) S.wcnt[w][threadIdx.x] = 0;
+  S.run[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned d = valid ? (unsigned)((kk[r] >> shift) & 0xffu) : 0x100u + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned wr = __popc(peers & lanemask_lt());
+    if (valid && wr == 0u) S.wcnt[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pre = S.run[d];
+      for (int w = 0; w < warp; ++w) pre += S.wcnt[w][d];
+      const uint32_t pos = S.gbase[d] + pre + wr;
+      keys_out[pos] = kk[r];
+      if (with_vals) vals_out[pos] = vv[r];
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+      tot += S.wcnt[w][threadIdx.x];
+      S.wcnt[w][threadIdx.x] = 0;
+    }
+    S.run[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
 // Digit histogram of one tile of one batch: hist[batch][digit][tile].
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* __restrict__ keys, int64_t stride,
                                                                int64_t n, int shift, int64_t ntiles,
                                                                uint32_t* __restrict__ hist) {
-  __shared__ uint32_t cnt[256];
+  __shared__ ScatterSmem S;
   keys += blockIdx.y * stride;
   hist += (int64_t)blockIdx.y * 256 * ntiles;
-  cnt[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  uint64_t kk[kSortRounds];  // all loads of the tile in flight at once
-#pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    kk[r] = i < n ? keys[i] : 0ull;
-  }
-#pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    bool valid = i < n;
-    unsigned d = valid ? (unsigned)((kk[r] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+  uint64_t kk[kSortRounds];
+  uint32_t vv[kSortRounds];
+  load_tile<false>(keys, nullptr, base, n, kk, vv);
+  tile_histogram(kk, base, n, shift, S);
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = S.cnt[threadIdx.x];
 }
 
-// Stable scatter of one tile by its digit.  With `fused` the tile's digit
-// offsets are formed here from the raw histogram (few tiles); otherwise
-// `hist` already holds the exclusive scan over (digit, tile).
+// Stable scatter of one tile by its digit; `hist` holds the exclusive scan
+// over (digit, tile).
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t stride, int64_t n, int shift,
-    int64_t ntiles, const uint32_t* __restrict__ hist, bool fused, uint64_t* __restrict__ keys_out,
+    int64_t ntiles, const uint32_t* __restrict__ hist, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t wcnt[kSortWarps][256];
-  __shared__ uint32_t run[256];
-  __shared__ uint32_t gbase[256];
-  __shared__ uint32_t wt[33];
+  __shared__ ScatterSmem S;
   const int64_t boff = blockIdx.y * stride;
   keys += boff;
   keys_out += boff;
@@ -135,63 +201,66 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
     vals_out += boff;
   }
   hist += (int64_t)blockIdx.y * 256 * ntiles;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
-  run[threadIdx.x] = 0;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  uint64_t kk[kSortRounds];  // the tile's keys and values, loaded before any use
+  uint64_t kk[kSortRounds];
   uint32_t vv[kSortRounds];
+  load_tile<false>(keys, vals, base, n, kk, vv);
+  S.gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  tile_scatter(kk, vv, base, n, shift, vals != nullptr, S, keys_out, vals_out);
+}
+
+// Every pass of a sort of at most kFusedTiles tiles per batch in one
+// cooperative launch: per pass, tile histograms hist[batch][tile][digit],
+// a grid-wide barrier, then every tile forms its digit offsets from the
+// histograms (digit totals scanned, plus the counts of the earlier tiles)
+// and scatters; a barrier again before the next digit.
+__global__ void __launch_bounds__(kSortThreads) k_radix_coop(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                                                            uint32_t* vals_alt, int64_t stride, int nbatch,
+                                                            int64_t n, int begin_bit, int end_bit, int64_t ntiles,
+                                                            uint32_t* hist) {
+  __shared__ ScatterSmem S;
+  cg::grid_group grid = cg::this_grid();
+  const bool with_vals = vals != nullptr;
+  uint64_t* kin = keys;
+  uint64_t* kout = keys_alt;
+  uint32_t* vin = vals;
+  uint32_t* vout = vals_alt;
+  const int64_t items = ntiles * nbatch;
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      const int64_t batch = it / ntiles, tile = it - batch * ntiles, base = tile * kSortTile;
+      uint64_t kk[kSortRounds];
+      uint32_t vv[kSortRounds];
+      load_tile<true>(kin + batch * stride, nullptr, base, n, kk, vv);
+      tile_histogram(kk, base, n, shift, S);
+      hist[it * 256 + threadIdx.x] = S.cnt[threadIdx.x];
+    }
+    grid.sync();
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      const int64_t batch = it / ntiles, tile = it - batch * ntiles, base = tile * kSortTile;
+      uint64_t kk[kSortRounds];
+      uint32_t vv[kSortRounds];
+      load_tile<true>(kin + batch * stride, with_vals ? vin + batch * stride : nullptr, base, n, kk, vv);
+      const uint32_t* h = hist + batch * ntiles * 256 + threadIdx.x;
+      uint32_t tot = 0, before = 0;
+      for (int64_t t0 = 0; t0 < ntiles; t0 += 16) {
+        uint32_t c[16];
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    kk[r] = i < n ? keys[i] : 0ull;
-    vv[r] = (i < n && vals) ? vals[i] : 0u;
-  }
-  if (fused) {
-    const uint32_t* h = hist + (int64_t)threadIdx.x * ntiles;
-    uint32_t tot = 0, before = 0;
-    for (int64_t t0 = 0; t0 < ntiles; t0 += 16) {
-      uint32_t c[16];
+        for (int u = 0; u < 16; ++u) c[u] = t0 + u < ntiles ? __ldcg(h + (t0 + u) * 256) : 0u;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) c[u] = t0 + u < ntiles ? h[t0 + u] : 0u;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        tot += c[u];
-        before += t0 + u < (int64_t)blockIdx.x ? c[u] : 0u;
+        for (int u = 0; u < 16; ++u) {
+          tot += c[u];
+          before += t0 + u < tile ? c[u] : 0u;
+        }
       }
+      uint32_t all;
+      S.gbase[threadIdx.x] = block_exclusive_scan(tot, S.wt, all) + before;
+      tile_scatter(kk, vv, base, n, shift, with_vals, S, kout + batch * stride,
+                   with_vals ? vout + batch * stride : nullptr);
     }
-    uint32_t all;
-    gbase[threadIdx.x] = block_exclusive_scan(tot, wt, all) + before;
-  } else {
-    gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    bool valid = i < n;
-    const uint64_t key = kk[r];
-    const uint32_t val = vv[r];
-    unsigned d = valid ? (unsigned)((key >> shift) & 0xffu) : 0x100u + lane;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    unsigned wr = __popc(peers & lanemask_lt());
-    if (valid && wr == 0u) wcnt[warp][d] = (uint32_t)__popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pre = run[d];
-      for (int w = 0; w < warp; ++w) pre += wcnt[w][d];
-      uint32_t pos = gbase[d] + pre + wr;
-      keys_out[pos] = key;
-      if (vals) vals_out[pos] = val;
-    }
-    __syncthreads();
-    uint32_t tot = 0;
-    for (int w = 0; w < kSortWarps; ++w) {
-      tot += wcnt[w][threadIdx.x];
-      wcnt[w][threadIdx.x] = 0;
-    }
-    run[threadIdx.x] += tot;
-    __syncthreads();
+    grid.sync();
+    uint64_t* tk = kin; kin = kout; kout = tk;
+    uint32_t* tv = vin; vin = vout; vout = tv;
   }
 }
 
@@ -229,7 +298,24 @@ int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint3
   if (n <= 1 || nbatch < 1) return FMM_OK;
   const int64_t nt = radix_tiles(n);
   if (nt * nbatch > max_tiles) return FMM_EINVAL;
-  const bool fused = nt <= kFusedTiles;
+  const int passes = (end_bit - begin_bit + 7) / 8;
+  if (nt <= kFusedTiles) {  // one cooperative launch for every pass
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+      int dev = 0;
+      FMM_CUDA_TRY(cudaGetDevice(&dev));
+      FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_coop, kSortThreads, 0));
+      if (per_sm < 1) return FMM_EINVAL;
+    }
+    int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, nt * nbatch);
+    void* args[] = {&keys, &keys_alt, &vals, &vals_alt, &stride, &nbatch, &n, &begin_bit, &end_bit,
+                    (void*)&nt, &hist};
+    FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_radix_coop, dim3(grid), dim3(kSortThreads), args, 0, s));
+    FMM_LAUNCH_CHECK();
+    *in_alt = (passes & 1) != 0;
+    return FMM_OK;
+  }
   uint64_t* k_in = keys;
   uint64_t* k_out = keys_alt;
   uint32_t* v_in = vals;
@@ -239,14 +325,12 @@ int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint3
   for (int b = begin_bit; b < end_bit; b += 8) {
     k_radix_upsweep<<<grid, kSortThreads, 0, s>>>(k_in, stride, n, b, nt, hist);
     FMM_LAUNCH_CHECK();
-    if (!fused) {
-      for (int k = 0; k < nbatch; ++k) {
-        uint32_t* h = hist + (int64_t)k * 256 * nt;
-        int rc = scan_exclusive(h, h, 256 * nt, scan_tmp, s);
-        if (rc != FMM_OK) return rc;
-      }
+    for (int k = 0; k < nbatch; ++k) {
+      uint32_t* h = hist + (int64_t)k * 256 * nt;
+      int rc = scan_exclusive(h, h, 256 * nt, scan_tmp, s);
+      if (rc != FMM_OK) return rc;
     }
-    k_radix_downsweep<<<grid, kSortThreads, 0, s>>>(k_in, v_in, stride, n, b, nt, hist, fused, k_out, v_out);
+    k_radix_downsweep<<<grid, kSortThreads, 0, s>>>(k_in, v_in, stride, n, b, nt, hist, k_out, v_out);
     FMM_LAUNCH_CHECK();
     uint64_t* tk = k_in; k_in = k_out; k_out = tk;
     uint32_t* tv = v_in; v_in = v_out; v_out = tv;

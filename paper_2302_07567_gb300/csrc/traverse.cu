@@ -299,15 +299,19 @@ __global__ void __launch_bounds__(kTravThreads) k_lists_src(ListArgs a) {
   order_lists<kFP32>(grid, a);
 }
 
-// Blocks of a cooperative launch of `kern`: all co-resident, at most `cap`.
+// Blocks of a cooperative launch of `kern`: all co-resident, at most `cap`,
+// about one per `per_block` work items but at least one per SM.  A grid-wide
+// barrier costs more the more blocks arrive at it, and a small tree's
+// frontier fits in few blocks.
 template <typename K>
-int coop_grid(K kern, int64_t cap, int* grid) {
+int coop_grid(K kern, int64_t cap, int64_t items, int64_t per_block, int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTravThreads, 0));
   if (per_sm < 1) return FMM_EINVAL;
-  *grid = (int)std::min<int64_t>((int64_t)per_sm * sms, cap);
+  const int64_t want = std::max<int64_t>(sms, div_up(items, per_block));
+  *grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, cap, want});
   return FMM_OK;
 }
 
@@ -367,7 +371,8 @@ int run_traverse(fmm_plan_s* P, cudaStream_t s) {
   const bool f32 = P->precision == FMM_FP32;
   void* kern = f32 ? (void*)k_traverse<true> : (void*)k_traverse<false>;
   int grid = 0;
-  int rc = f32 ? coop_grid(k_traverse<true>, kTravPartials, &grid) : coop_grid(k_traverse<false>, kTravPartials, &grid);
+  int rc = f32 ? coop_grid(k_traverse<true>, kTravPartials, P->nleaves, 8, &grid)
+               : coop_grid(k_traverse<false>, kTravPartials, P->nleaves, 8, &grid);
   if (rc != FMM_OK) return rc;
   void* args[] = {&a};
   FMM_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTravThreads), args, 0, s));
@@ -382,7 +387,8 @@ int run_list_transpose(fmm_plan_s* P, cudaStream_t s) {
   const bool f32 = P->precision == FMM_FP32;
   void* kern = f32 ? (void*)k_lists_src<true> : (void*)k_lists_src<false>;
   int grid = 0;
-  int rc = f32 ? coop_grid(k_lists_src<true>, kTravPartials, &grid) : coop_grid(k_lists_src<false>, kTravPartials, &grid);
+  int rc = f32 ? coop_grid(k_lists_src<true>, kTravPartials, P->nleaves, 8, &grid)
+               : coop_grid(k_lists_src<false>, kTravPartials, P->nleaves, 8, &grid);
   if (rc != FMM_OK) return rc;
   void* args[] = {&a};
   FMM_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTravThreads), args, 0, s));
