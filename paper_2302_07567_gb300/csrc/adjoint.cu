@@ -151,13 +151,14 @@ __global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __re
 // K(R) x W^B_{S,mu}) with R = xi_{S,mu} - xi_{s,nu}.
 template <typename T, int KPT>
 __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
-                                                 int shift, const NodeGeo* __restrict__ geo,
+                                                 int shift, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
                                                  const void* __restrict__ sdc, Cheb ch, int m,
                                                  const T* __restrict__ W, T* __restrict__ Lam) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ unsigned char smem_raw[];
   V4* sm = reinterpret_cast<V4*>(smem_raw);  // [m][3]
-  const int64_t s = (int64_t)blockIdx.x + 1;
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {  // sources, longest list first
+  const int64_t s = order[w];
   const int np1 = ch.np1;
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int b = off[s], e = off[s + 1];
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
       for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = acc[k][c];
     }
   }
+  }  // work items
 }
 
 // FP32 M2L^T specialised on NP1 = n + 1 (eta <= 1/2), the counterpart of
@@ -251,20 +253,28 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
 //   Lambda^b  += (R_y sum r3 W^B_z - R_z sum r3 W^B_y,
 //                 R_z sum r3 W^B_x - sum r3 W^B_z R_x,
 //                 sum r3 W^B_y R_x - R_y sum r3 W^B_x)
-template <int NP1, int G>
-__global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_adj_m2l_fast(const uint64_t* __restrict__ keys,
-                                                                  const int32_t* __restrict__ off, int shift,
+template <int NP1, int G, int SPLIT>
+__global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_adj_m2l_fast(const uint64_t* __restrict__ keys,
+                                                                  const int32_t* __restrict__ off, int shift, const int32_t* __restrict__ order, int64_t nitems, unsigned int* __restrict__ work,
                                                                   const NodeGeo* __restrict__ geo,
                                                                   const float4* __restrict__ sdc, Cheb ch,
                                                                   const float* __restrict__ W, float* __restrict__ Lam) {
-  constexpr int KPT = (NP1 + G - 1) / G;
+  constexpr int KPT = (NP1 + G * SPLIT - 1) / (G * SPLIT);
   constexpr int NT = NP1 * NP1 * G;
   constexpr int m = NP1 * NP1 * NP1;
   __shared__ float4 swa[m];            // (W^E_x, W^E_y, W^E_z, W^B_x)
   __shared__ float2 swb[m];            // (W^B_y, W^B_z)
   __shared__ float syz[NP1];           // target-cluster point offsets along z
   __shared__ float sacc[KPT][8][NT];   // Kahan sums and compensations
-  const int64_t s = (int64_t)blockIdx.x + 1;
+  __shared__ int64_t s_item;
+  for (;;) {  // items (source, nu3 chunk) fetched in the work order: longest lists first
+  if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(work, 1u);
+  __syncthreads();
+  const int64_t w = s_item;
+  __syncthreads();
+  if (w >= nitems) break;
+  const int64_t s = order[w / SPLIT];
+  const int base3 = (int)(w % SPLIT) * G * KPT;
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int b = off[s], e = off[s + 1];
   const NodeGeo gs = geo[s];
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_adj_m2l_fast(const uint64_
   float zs[KPT];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    const int nu3 = g + k * G;
+    const int nu3 = base3 + g + k * G;
     zs[k] = (float)(gs.h[2] * ch.t[nu3 < NP1 ? nu3 : 0]);
 #pragma unroll
     for (int c = 0; c < 8; ++c) sacc[k][c][tid] = 0.f;
@@ -369,19 +379,25 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_adj_m2l_fast(const uint64_
   }
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    const int nu3 = g + k * G;
+    const int nu3 = base3 + g + k * G;
     if (nu3 >= NP1) continue;
     const int nu = nu1 + NP1 * (nu2 + NP1 * nu3);
 #pragma unroll
     for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = sacc[k][c][tid];
   }
+  }  // work items
 }
 
-template <int NP1, int G>
+template <int NP1, int G, int SPLIT>
 int launch_adj_m2l_fast(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
-  k_adj_m2l_fast<NP1, G><<<(unsigned)P->C, NP1 * NP1 * G, 0, s>>>(
-      ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo),
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_adj_m2l_fast<NP1, G, SPLIT>, NP1 * NP1 * G, 0, P->C * SPLIT, &grid)) return rc;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  FMM_CUDA_TRY(cudaMemsetAsync(&cnt->work[1], 0, sizeof(unsigned int), s));
+  k_adj_m2l_fast<NP1, G, SPLIT><<<grid, NP1 * NP1 * G, 0, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1,
+      ws_ptr<int32_t>(P, L.m2l_sorder), P->C * SPLIT, &cnt->work[1], ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<float4>(P, L.m2l_sdc), P->cheb, ws_ptr<float>(P, L.local), ws_ptr<float>(P, L.mpole));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
@@ -876,8 +892,11 @@ int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
     attr = true;
   }
   const size_t smem = (size_t)3 * P->m * sizeof(typename Vec4<T>::type);
-  k_adj_m2l<T, KPT><<<(unsigned)P->C, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff),
-                                                      P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc,
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_adj_m2l<T, KPT>, nt, smem, P->C, &grid)) return rc;
+  k_adj_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff),
+                                            P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_sorder), P->C,
+                                            ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc,
                                                       P->cheb, P->m, ws_ptr<T>(P, L.local), ws_ptr<T>(P, L.mpole));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
@@ -887,10 +906,10 @@ template <typename T>
 int adj_m2l(fmm_plan_s* P, cudaStream_t s) {
   if (std::is_same<T, float>::value && P->eta <= 0.5) {
     switch (P->np1) {
-      case 3: return launch_adj_m2l_fast<3, 3>(P, s);
-      case 5: return launch_adj_m2l_fast<5, 5>(P, s);
-      case 7: return launch_adj_m2l_fast<7, 4>(P, s);
-      case 9: return launch_adj_m2l_fast<9, 3>(P, s);
+      case 3: return launch_adj_m2l_fast<3, 3, 1>(P, s);
+      case 5: return launch_adj_m2l_fast<5, 5, 1>(P, s);
+      case 7: return launch_adj_m2l_fast<7, 4, 2>(P, s);
+      case 9: return launch_adj_m2l_fast<9, 3, 3>(P, s);
       default: break;
     }
   }

@@ -46,7 +46,8 @@ struct Counters {
   unsigned long long m2l_count;
   unsigned long long frontier_count[3];  // rotating: step k reads [k%3], appends to [(k+1)%3]
   unsigned int err;
-  unsigned int pad[5];
+  unsigned int work[2];  // item counters of the dynamically scheduled M2L and M2L^T launches
+  unsigned int pad[3];
 };
 
 // Chebyshev points of the second kind t_k = cos(k pi / n) and their
@@ -88,6 +89,7 @@ struct Layout {
   size_t wle, wlb;                 // per particle: scaled loss weights (leaf order)
   size_t p2p_sdc, m2l_sdc;         // centre offsets of the source-major lists
   size_t tcnt, tpart;               // list ordering: per-node counts and fills, scan partials
+  size_t thist, m2l_order, m2l_sorder;  // M2L work orders: count buckets, targets, sources
   size_t nblk_sort;   // radix tiles of the three presorts
   size_t nblk_part;   // partition blocks at N
 };
@@ -217,6 +219,20 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   T t = sum + y;
   comp = (t - sum) - y;
   sum = t;
+}
+
+// Blocks of a grid-stride launch of `kern`: as many as are resident at once
+// at `threads` threads and `smem` dynamic shared bytes, at most `items`.
+template <typename K>
+inline int resident_blocks(K kern, int threads, size_t smem, int64_t items, unsigned* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
+    return FMM_ECUDA;
+  if (per_sm < 1) return FMM_EINVAL;
+  *grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, items));
+  return FMM_OK;
 }
 
 // Thread shape of the particle-pair kernels (forward P2P, adjoint target and

@@ -17,13 +17,14 @@ namespace {
 
 template <typename T, int KPT>
 __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
-                                             int shift, const NodeGeo* __restrict__ geo,
+                                             int shift, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
                                              const void* __restrict__ pdc, Cheb ch, int m,
                                              const typename Vec4<T>::type* __restrict__ src, T* __restrict__ Lout) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ unsigned char smem_raw[];
   V4* sm = reinterpret_cast<V4*>(smem_raw);
-  const int64_t t = (int64_t)blockIdx.x + 1;
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {  // targets, longest list first
+  const int64_t t = order[w];
   const int np1 = ch.np1;
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int b = off[t], e = off[t + 1];
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, 
       for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + mu] = acc[k][c];
     }
   }
+  }  // work items
 }
 
 // FP32 M2L specialised on the points per axis NP1 = n + 1 (for eta <= 1/2).
@@ -112,23 +114,34 @@ __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, 
 //   B  += (R_z sum b_y r3 - R_y sum b_z r3,  sum b_z r3 R_x - R_z sum b_x r3,
 //          R_y sum b_x r3 - sum b_y r3 R_x)
 // with seven running sums per target point (13 FP32 operations and one
-// rsqrt per point pair instead of 21).  The same terms are added, in the same
+// rsqrt per point pair instead of 21).  A block takes one of SPLIT chunks of
+// a target's mu3 points at a time, fetching (target, chunk) items from an
+// atomic counter in the work order (longest source lists first), so the
+// SMs finish together even when a few targets have the longest lists.  The same terms are added, in the same
 // per-source groups, as in the generic kernel.  For eta <= 1/2 admissible
 // boxes are disjoint (r_t + r_s < d), so |R|^2 > 0 and a clamp replaces the
 // zero mask.  The running Kahan sums across sources live in shared memory.
-template <int NP1, int G>
-__global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_m2l_fast(const uint64_t* __restrict__ keys,
-                                                              const int32_t* __restrict__ off, int shift,
+template <int NP1, int G, int SPLIT>
+__global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* __restrict__ keys,
+                                                              const int32_t* __restrict__ off, int shift, const int32_t* __restrict__ order, int64_t nitems, unsigned int* __restrict__ work,
                                                               const NodeGeo* __restrict__ geo,
                                                               const float4* __restrict__ pdc, Cheb ch,
                                                               const float* __restrict__ M, float* __restrict__ Lout) {
-  constexpr int KPT = (NP1 + G - 1) / G;
+  constexpr int KPT = (NP1 + G * SPLIT - 1) / (G * SPLIT);
   constexpr int NT = NP1 * NP1 * G;
   constexpr int m = NP1 * NP1 * NP1;
   __shared__ float4 sm[m];              // source effective masses (a, b~x, b~y, b~z)
   __shared__ float syz[NP1];            // source point offsets along z
   __shared__ float sacc[KPT][12][NT];   // Kahan sums and compensations
-  const int64_t t = (int64_t)blockIdx.x + 1;
+  __shared__ int64_t s_item;
+  for (;;) {  // items (target, mu3 chunk) fetched in the work order: longest lists first
+  if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(work, 1u);
+  __syncthreads();
+  const int64_t w = s_item;
+  __syncthreads();
+  if (w >= nitems) break;
+  const int64_t t = order[w / SPLIT];
+  const int base3 = (int)(w % SPLIT) * G * KPT;
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int b = off[t], e = off[t + 1];
   const NodeGeo gt = geo[t];
@@ -139,7 +152,7 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_m2l_fast(const uint64_t* _
   float zt[KPT];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    const int mu3 = g + k * G;
+    const int mu3 = base3 + g + k * G;
     zt[k] = (float)(gt.h[2] * ch.t[mu3 < NP1 ? mu3 : 0]);
 #pragma unroll
     for (int c = 0; c < 12; ++c) sacc[k][c][tid] = 0.f;
@@ -231,19 +244,25 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 2) k_m2l_fast(const uint64_t* _
   }
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    const int mu3 = g + k * G;
+    const int mu3 = base3 + g + k * G;
     if (mu3 >= NP1) continue;
     const int mu = mu1 + NP1 * (mu2 + NP1 * mu3);
 #pragma unroll
     for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + mu] = sacc[k][c][tid];
   }
+  }  // work items
 }
 
-template <int NP1, int G>
+template <int NP1, int G, int SPLIT>
 int launch_fast(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
-  k_m2l_fast<NP1, G><<<(unsigned)P->C, NP1 * NP1 * G, 0, s>>>(
-      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo),
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_m2l_fast<NP1, G, SPLIT>, NP1 * NP1 * G, 0, P->C * SPLIT, &grid)) return rc;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  FMM_CUDA_TRY(cudaMemsetAsync(&cnt->work[0], 0, sizeof(unsigned int), s));
+  k_m2l_fast<NP1, G, SPLIT><<<grid, NP1 * NP1 * G, 0, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1,
+      ws_ptr<int32_t>(P, L.m2l_order), P->C * SPLIT, &cnt->work[0], ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<float4>(P, L.m2l_dc), P->cheb, ws_ptr<float>(P, L.mpole), ws_ptr<float>(P, L.local));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
@@ -279,8 +298,11 @@ int launch(fmm_plan_s* P, int nt, cudaStream_t s) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_m2l<T, KPT><<<(unsigned)P->C, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
-                                                  P->kappa + 1, ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_dc, P->cheb, P->m,
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_m2l<T, KPT>, nt, smem, P->C, &grid)) return rc;
+  k_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
+                                        P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_order), P->C,
+                                        ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_dc, P->cheb, P->m,
                                                   ws_ptr<typename Vec4<T>::type>(P, L.srct), ws_ptr<T>(P, L.local));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
@@ -303,10 +325,10 @@ int m2l_t(fmm_plan_s* P, cudaStream_t s) {
 int run_m2l(fmm_plan_s* P, cudaStream_t s) {
   if (P->precision == FMM_FP32 && P->eta <= 0.5) {
     switch (P->np1) {
-      case 3: return launch_fast<3, 3>(P, s);
-      case 5: return launch_fast<5, 5>(P, s);
-      case 7: return launch_fast<7, 4>(P, s);
-      case 9: return launch_fast<9, 3>(P, s);
+      case 3: return launch_fast<3, 3, 1>(P, s);
+      case 5: return launch_fast<5, 5, 1>(P, s);
+      case 7: return launch_fast<7, 4, 2>(P, s);
+      case 9: return launch_fast<9, 3, 3>(P, s);
       default: break;
     }
   }

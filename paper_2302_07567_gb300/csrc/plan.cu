@@ -93,6 +93,9 @@ void make_layout(fmm_plan_s* P) {
   L.wlb = take(N * V4);
   L.tcnt = take(4 * (C1 + 1) * 4);
   L.tpart = take(2 * (size_t)kTravPartials * 4);
+  L.thist = take(4 * 256 * 4);
+  L.m2l_order = take(C1 * 4);
+  L.m2l_sorder = take(C1 * 4);
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.total = off;

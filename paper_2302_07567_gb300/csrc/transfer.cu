@@ -222,8 +222,10 @@ int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s) {
     FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
     if (per_sm < 1) return FMM_EINVAL;
   }
+  // at most 4 blocks per SM: more make the grid-wide barriers dearer than
+  // the extra blocks help the deepest levels (measured at 2^9 leaves)
   const int64_t most = ((int64_t)1 << (P->kappa - 1)) * nc;
-  const int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, most);
+  const int grid = (int)std::min<int64_t>({(int64_t)std::min(per_sm, 4) * sms, most});
   int first = UP ? P->kappa - 1 : 0, last = UP ? 0 : P->kappa - 1;
   const T* tm = ws_ptr<T>(P, P->lay.tmat);
   void* args[] = {&first, &last, &nc, (void*)&tm, &buf};

@@ -31,6 +31,16 @@ namespace cg = cooperative_groups;
 
 constexpr int kTravThreads = 256;
 constexpr int kSegStage = 128;  // keys of one segment a warp ranks from shared memory
+// Work order of a list's major nodes: counting sort by pair count, longest
+// lists first (counts of kOrderBuckets - 1 and more share the first bucket).
+// Kernels that give a block per major node walk this order, so the long
+// lists start first and the short ones fill in behind them.
+constexpr int kOrderBuckets = kTravThreads;
+static_assert(kOrderBuckets == kTravThreads, "one bucket per thread in the bucket scan");
+
+__device__ __forceinline__ int order_bucket(uint32_t count) {
+  return kOrderBuckets - 1 - (int)min(count, (uint32_t)(kOrderBuckets - 1));
+}
 
 // One list to order: pairs key = (major << shift | minor), optionally swapped
 // from (minor << shift | major), grouped and sorted by key.  Arrays written
@@ -45,6 +55,8 @@ struct ListJob {
   uint64_t* tmp;                    // pairs grouped by major
   uint64_t* out;                    // pairs sorted by key
   void* dc;                         // s o (c_major - c_minor) / ell per pair
+  int32_t* order;                   // [C] nodes 1..C by decreasing pair count, or null
+  uint32_t* hb;                     // [kOrderBuckets] nodes per count bucket, then placed per bucket
 };
 
 struct ListArgs {
@@ -127,11 +139,14 @@ __device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
   const int64_t M = a.C + 2;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-  for (int j = 0; j < 2; ++j)
+  for (int j = 0; j < 2; ++j) {
     for (int64_t i = gtid; i < M; i += gstride) {
       a.job[j].cnt[i] = 0;
       a.job[j].fill[i] = 0;
     }
+    if (a.job[j].order)
+      for (int64_t i = gtid; i < 2 * kOrderBuckets; i += gstride) a.job[j].hb[i] = 0;
+  }
   grid.sync();
   for (int j = 0; j < 2; ++j) {
     const ListJob& J = a.job[j];
@@ -145,7 +160,11 @@ __device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
   const int64_t c0 = (int64_t)blockIdx.x * chunk, c1 = min64(M, c0 + chunk);
   for (int j = 0; j < 2; ++j) {
     uint32_t v = 0;
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) v += __ldcg(a.job[j].cnt + i);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      const uint32_t c = __ldcg(a.job[j].cnt + i);
+      v += c;
+      if (a.job[j].order && i >= 1 && i <= a.C) atomicAdd(&a.job[j].hb[order_bucket(c)], 1u);
+    }
     uint32_t tot;
     block_scan_excl(v, wt, tot);
     if (threadIdx.x == 0) a.partial[j * gridDim.x + blockIdx.x] = tot;
@@ -164,6 +183,19 @@ __device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
       const uint32_t ex = block_scan_excl(c, wt, t);
       if (i < c1) J.off[i] = (int32_t)(base + ex);
       base += t;
+    }
+    if (J.order) {  // place this chunk's nodes in the work order
+      uint32_t tot;
+      const uint32_t bstart = block_scan_excl(__ldcg(J.hb + threadIdx.x), wt, tot);
+      __shared__ uint32_t bofs[kOrderBuckets];
+      bofs[threadIdx.x] = bstart;
+      __syncthreads();
+      for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        if (i < 1 || i > a.C) continue;
+        const int bk = order_bucket(__ldcg(J.cnt + i));
+        J.order[bofs[bk] + atomicAdd(&J.hb[kOrderBuckets + bk], 1u)] = (int32_t)i;
+      }
+      __syncthreads();
     }
   }
   grid.sync();
@@ -336,6 +368,8 @@ ListArgs list_args(fmm_plan_s* P, bool swap) {
     J.cnt = tc + (2 * j) * M;
     J.fill = tc + (2 * j + 1) * M;
     J.tmp = tmp + (p2p ? 0 : P->cap_p2p);
+    J.order = p2p ? nullptr : ws_ptr<int32_t>(P, swap ? L.m2l_sorder : L.m2l_order);
+    J.hb = ws_ptr<uint32_t>(P, L.thist) + (size_t)(swap ? 2 : 0) * kOrderBuckets;
     if (!swap) {  // forward: raw appends (in the source-major buffers) -> target-major lists
       J.in = ws_ptr<uint64_t>(P, p2p ? L.p2p_src : L.m2l_src);
       J.out = ws_ptr<uint64_t>(P, p2p ? L.p2p : L.m2l);
