@@ -42,6 +42,12 @@ METRIC = "particles/s (E,B on all N; fwd and fwd+adjoint) at fixed rel. L2 error
 HOT = {"m2l": (32.0, "m2l_interactions"), "p2p_l2p": (32.0, "p2p_interactions"),
        "adj_m2lt": (32.0, "m2l_interactions"), "adj_target": (46.0, "p2p_interactions"),
        "adj_source": (67.0, "p2p_interactions")}
+# DRAM bytes (read + write) per launch of each hot kernel on the cylinder64k
+# fwd+adj step, from one `ncu --set full` capture per kernel (summary and
+# command in profiles/hot_kernels_cylinder64k.md).  Valid only while the
+# kernel is unchanged since that capture; reported for that workload only.
+TRAFFIC_CYL64K = {"adj_source": 11853568 + 350464, "adj_target": 9832960 + 73472, "p2p_l2p": 7996160 + 3840,
+                  "m2l": 2674944, "adj_m2lt": 3963648}
 SMS = 152          # GB300 streaming multiprocessors
 FP32_LANES = 128   # FP32 FMA lanes per SM
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -261,11 +267,14 @@ def run_ours(args, rank, world, local):
         if ms <= 0.0:
             continue
         flop = per * st0[unit]
+        traffic = (TRAFFIC_CYL64K.get(k) if args.workload == "cylinder64k" and args.precision == "fp32"
+                   and args.passes == "fwd+adj" else None)
         kernels[k] = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
-                      "frac": (flop / (ms / 1e3) / 1e12 / peak) if peak else None}
+                      "frac": (flop / (ms / 1e3) / 1e12 / peak) if peak else None, "traffic": traffic}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak, "unit": "TFLOP/s",
-            "frac": kernels[dom]["frac"], "traffic": None,
+            "frac": kernels[dom]["frac"], "traffic": kernels[dom]["traffic"],
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock)",
             "flop_basis": "algorithmic flop per pair (FMA = 2): M2L and M2L^T 32 per point pair, P2P 32, "
                           "adjoint near field 46 (target side) and 67 (source side) per particle pair",

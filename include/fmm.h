@@ -64,8 +64,12 @@ typedef enum fmm_precision {
 typedef enum fmm_flags {
   FMM_RECOMPUTE = 1u,    /* the adjoint recomputes multipoles and local fields instead
                             of reusing those of the forward call                      */
-  FMM_BOUNDS_CHECK = 2u, /* check every list and tree index on the device; a failure
-                            sets FMM_EBOUNDS instead of reading out of range         */
+  FMM_BOUNDS_CHECK = 2u, /* after the traversal (and the adjoint's source-major lists)
+                            check on the device: node tables, the leaf order is a
+                            permutation, list pairs in range, sorted and matching
+                            their CSR offsets, and sum |S_t||S_s| = N^2 over the
+                            lists; a failure returns FMM_EBOUNDS before any kernel
+                            indexes through the bad value (costs one more wait)     */
   FMM_TIMING = 4u        /* record CUDA events around each stage (fmm_plan_stats)    */
 } fmm_flags;
 

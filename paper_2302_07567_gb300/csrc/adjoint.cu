@@ -985,6 +985,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   if ((rc = record(P, 15, s)) != FMM_OK) return rc;
   if (!P->transposed_valid) {
     if ((rc = run_list_transpose(P, s)) != FMM_OK) return rc;
+    if ((P->flags & FMM_BOUNDS_CHECK) && (rc = run_bounds_check(P, true, s)) != FMM_OK) return rc;
     P->transposed_valid = true;
   }
   if (!P->locals_valid || (P->flags & FMM_RECOMPUTE)) {  // the forward's multipoles and locals again

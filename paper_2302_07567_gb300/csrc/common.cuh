@@ -47,7 +47,8 @@ struct Counters {
   unsigned long long frontier_count[3];  // rotating: step k reads [k%3], appends to [(k+1)%3]
   unsigned int err;
   unsigned int work[2];  // item counters of the dynamically scheduled M2L and M2L^T launches
-  unsigned int pad[3];
+  unsigned int pad[1];
+  unsigned long long cover;  // FMM_BOUNDS_CHECK: sum of |S_t| |S_s| over the list pairs
 };
 
 // Chebyshev points of the second kind t_k = cos(k pi / n) and their
@@ -268,6 +269,9 @@ int run_upward(fmm_plan_s* P, cudaStream_t s);
 // traversal and both target-major lists (sorted, CSR, centre offsets), one launch
 int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
+// FMM_BOUNDS_CHECK: node tables, leaf order and lists (target- or source-major);
+// synchronises the stream, FMM_EBOUNDS on any violation
+int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
 int run_l2l(fmm_plan_s* P, cudaStream_t s);
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);

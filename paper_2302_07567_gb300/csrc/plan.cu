@@ -293,6 +293,7 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   P->gbar = hs[0];
   P->munit = hs[1];
   P->lunit = hs[2];
+  if ((P->flags & FMM_BOUNDS_CHECK) && (rc = run_bounds_check(P, false, s)) != FMM_OK) return rc;
   if ((rc = record(P, 4, s)) != FMM_OK) return rc;
   if ((rc = record(P, 5, s)) != FMM_OK) return rc;
   if ((rc = run_m2l(P, s)) != FMM_OK) return rc;

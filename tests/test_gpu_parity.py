@@ -208,3 +208,24 @@ def test_list_overflow_grows_and_matches():
     assert st["cap_p2p"] >= st["p2p_pairs"] > 8
     _, E2, B2 = run(x, p, q, 4, 64, 0.5, "fp64")
     np.testing.assert_array_equal(E.cpu().numpy(), E2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bounds_check_mode_passes_and_changes_nothing(case, prec):
+    """FMM_BOUNDS_CHECK verifies the tables, the leaf order and both lists
+    (including sum |S_t||S_s| = N^2) and must not change any result."""
+    x, p, q = case["x"], case["p"], case["q"]
+    N = len(x)
+    X, Pm, Q = dev(x, p, q)
+    odt = torch.float32 if prec == "fp32" else torch.float64
+    rng = np.random.default_rng(11)
+    WE, WB = (torch.as_tensor(rng.standard_normal((N, 3)), device=DEV, dtype=odt) for _ in range(2))
+    out = []
+    for flags in (0, fmm.FMM_BOUNDS_CHECK):
+        plan = fmm.Plan(N, case["n"], case["leaf"], case["eta"], precision=prec, flags=flags)
+        E, B = plan.field(X, Pm, Q)
+        E, B = E.clone(), B.clone()
+        grads = [t.clone() for t in plan.adjoint(X, Pm, Q, WE, WB)]
+        out.append((E, B, *grads))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
