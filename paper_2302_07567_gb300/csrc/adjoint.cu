@@ -24,10 +24,11 @@
 // rule finally maps (a', b~', x') to (q, p, x) with a = q gamma, b = q p,
 // gamma = sqrt(1 + |p|^2).
 //
-// Buffer reuse: W is written into the forward's local buffer and Lambda into
-// its multipole buffer, so the target-side kernel (which reads the forward's
-// cumulative locals) runs first.  A second adjoint call for the same forward
-// recomputes the upward pass, M2L and L2L.
+// Buffers: W and Lambda have their own, so the forward's multipoles and
+// cumulative locals survive the adjoint (a second adjoint call reuses them),
+// and the target-side kernel runs on the caller's stream while the source
+// side's far field (L2P^T, L2L^T, M2L^T, M2M^T) runs on the plan's side
+// stream.
 #include <type_traits>
 
 #include "common.cuh"
@@ -398,7 +399,7 @@ int launch_adj_m2l_fast(fmm_plan_s* P, cudaStream_t s) {
   k_adj_m2l_fast<NP1, G, SPLIT><<<grid, NP1 * NP1 * G, 0, s>>>(
       ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1,
       ws_ptr<int32_t>(P, L.m2l_sorder), P->C * SPLIT, &cnt->work[1], ws_ptr<NodeGeo>(P, L.ngeo),
-      ws_ptr<float4>(P, L.m2l_sdc), P->cheb, ws_ptr<float>(P, L.local), ws_ptr<float>(P, L.mpole));
+      ws_ptr<float4>(P, L.m2l_sdc), P->cheb, ws_ptr<float>(P, L.wbuf), ws_ptr<float>(P, L.lbuf));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -863,7 +864,7 @@ int launch_l2pt(fmm_plan_s* P, cudaStream_t s) {
   k_l2pt<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pl), ws_ptr<V4>(P, L.wle),
                                                         ws_ptr<V4>(P, L.wlb), ws_ptr<int64_t>(P, L.nstart),
                                                         ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
-                                                        P->cheb, P->m, ws_ptr<T>(P, L.local));
+                                                        P->cheb, P->m, ws_ptr<T>(P, L.wbuf));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -897,7 +898,7 @@ int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
   k_adj_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff),
                                             P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_sorder), P->C,
                                             ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc,
-                                                      P->cheb, P->m, ws_ptr<T>(P, L.local), ws_ptr<T>(P, L.mpole));
+                                                      P->cheb, P->m, ws_ptr<T>(P, L.wbuf), ws_ptr<T>(P, L.lbuf));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -962,7 +963,7 @@ int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, d
     k_adj_source<T, 1><<<grid, nt, smem, s>>>(
         ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
         ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.mpole),
+        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.lbuf),
         P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
         q, groups, chunks, dx, dp, dq);
   }
@@ -993,30 +994,40 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
     if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
   }
-  if ((rc = record(P, 9, s)) != FMM_OK) return rc;
   const int gs = (int)std::min<int64_t>(8192, div_up(P->N, 256));
   k_adj_prep<T><<<gs, 256, 0, s>>>(static_cast<const T*>(wE), static_cast<const T*>(wB), P->N,
                                     ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), ws_ptr<V4>(P, L.wle),
                                     ws_ptr<V4>(P, L.wlb));
   FMM_LAUNCH_CHECK();
+  if ((rc = record(P, 16, s)) != FMM_OK) return rc;
+  // Two independent branches from here: the far field of the source side
+  // (L2P^T, L2L^T, M2L^T, M2M^T, mostly latency-bound transfers) on the
+  // plan's side stream, the target-side particle kernel (ALU-bound) on the
+  // caller's stream.  They share no buffer that either writes: W and Lambda
+  // have their own, the target side reads the forward's locals.
+  const bool chain = P->kappa > 0;
+  if (chain) {
+    if ((rc = ensure_side(P)) != FMM_OK) return rc;
+    cudaStream_t t = P->side;
+    FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
+    if ((rc = l2pt<T>(P, t)) != FMM_OK) return rc;
+    // beside the particle kernel the transfers keep to one block per SM
+    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, 1)) != FMM_OK) return rc;  // L2L^T: W up
+    if ((rc = record(P, 11, t)) != FMM_OK) return rc;
+    if ((rc = adj_m2l<T>(P, t)) != FMM_OK) return rc;
+    if ((rc = record(P, 12, t)) != FMM_OK) return rc;
+    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, 1)) != FMM_OK) return rc;  // M2M^T
+    if ((rc = record(P, 13, t)) != FMM_OK) return rc;
+    FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
+  }
   if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, true, s)) != FMM_OK) return rc;
-  P->locals_valid = false;  // the local buffer now receives W
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
-  if (P->kappa > 0) {
-    if ((rc = l2pt<T>(P, s)) != FMM_OK) return rc;
-    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.local), s)) != FMM_OK) return rc;  // L2L^T: W up
-  }
-  if ((rc = record(P, 11, s)) != FMM_OK) return rc;
-  if (P->kappa > 0 && (rc = adj_m2l<T>(P, s)) != FMM_OK) return rc;
-  if ((rc = record(P, 12, s)) != FMM_OK) return rc;
-  if (P->kappa > 0) {
-    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.mpole), s)) != FMM_OK) return rc;  // M2M^T: Lambda down
-  }
-  if ((rc = record(P, 13, s)) != FMM_OK) return rc;
+  if (chain) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
   if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, false, s)) != FMM_OK) return rc;
   if ((rc = record(P, 14, s)) != FMM_OK) return rc;
   (void)x;
-  if (P->flags & FMM_TIMING) P->flags |= 0x100u;
+  if (P->flags & FMM_TIMING) P->flags = (P->flags & ~0x300u) | 0x100u | (chain ? 0x200u : 0u);
   return FMM_OK;
 }
 

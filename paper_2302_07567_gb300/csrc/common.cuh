@@ -87,6 +87,7 @@ struct Layout {
   size_t mpole, local, srct, tmat;
   size_t front0, front1, p2p, m2l, p2p_off, m2l_off, p2p_src, m2l_src, p2p_soff, m2l_soff;
   size_t adj_part;                 // per particle: target-side position gradient (leaf order)
+  size_t wbuf, lbuf;               // adjoint expansions: W [C+1][6][m] and Lambda [C+1][4][m]
   size_t wle, wlb;                 // per particle: scaled loss weights (leaf order)
   size_t p2p_sdc, m2l_sdc;         // centre offsets of the source-major lists
   size_t tcnt, tpart;               // list ordering: per-node counts and fills, scan partials
@@ -119,6 +120,8 @@ struct fmm_plan_s {
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[18] = {};
   bool ev_made = false;
+  cudaStream_t side = nullptr;    // second stream for independent branches (higher priority)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   double stage_ms[16] = {};
 };
 
@@ -269,6 +272,8 @@ int run_upward(fmm_plan_s* P, cudaStream_t s);
 // traversal and both target-major lists (sorted, CSR, centre offsets), one launch
 int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
+// the plan's side stream and its fork / join events (created on first use)
+int ensure_side(fmm_plan_s* P);
 // FMM_BOUNDS_CHECK: node tables, leaf order and lists (target- or source-major);
 // synchronises the stream, FMM_EBOUNDS on any violation
 int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);
@@ -289,7 +294,7 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, 
 // levels (see transfer.cu)
 int run_tmats(fmm_plan_s* P, cudaStream_t s);
 template <typename T, int NC, bool UP>
-int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s);
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm = 4);
 int64_t radix_tiles(int64_t n);
 int64_t scan_tmp_words(int64_t n);
 }  // namespace fmm

@@ -96,6 +96,8 @@ void make_layout(fmm_plan_s* P) {
   L.thist = take(4 * 256 * 4);
   L.m2l_order = take(C1 * 4);
   L.m2l_sorder = take(C1 * 4);
+  L.wbuf = take(C1 * 6 * m * R);
+  L.lbuf = take(C1 * 4 * m * R);
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.total = off;
@@ -166,6 +168,16 @@ int record(fmm_plan_s* P, int k, cudaStream_t s) {
 }
 
 }  // namespace
+
+int ensure_side(fmm_plan_s* P) {
+  if (P->side) return FMM_OK;
+  int least = 0, greatest = 0;
+  FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  FMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, greatest));
+  FMM_CUDA_TRY(cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming));
+  FMM_CUDA_TRY(cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming));
+  return FMM_OK;
+}
 }  // namespace fmm
 
 using namespace fmm;
@@ -367,13 +379,20 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[7] = el(7, 8);
     P->stage_ms[13] = el(0, 8);
     if (P->flags & 0x100u) {  // adjoint events recorded
-      P->stage_ms[8] = el(10, 11);   // L2P^T + L2L^T
-      P->stage_ms[9] = el(11, 12);   // M2L^T
-      P->stage_ms[10] = el(12, 13);  // M2M^T
-      P->stage_ms[11] = el(9, 10);   // target-side particle kernel
-      P->stage_ms[12] = el(13, 14);  // source-side particle kernel + chain rule
+      // the target side runs on the caller's stream while L2P^T .. M2M^T run
+      // on the side stream, both from event 16; the source side starts when
+      // both have finished
+      P->stage_ms[11] = el(16, 10);  // target-side particle kernel
+      if (P->flags & 0x200u) {
+        P->stage_ms[8] = el(16, 11);   // L2P^T + L2L^T
+        P->stage_ms[9] = el(11, 12);   // M2L^T
+        P->stage_ms[10] = el(12, 13);  // M2M^T
+        P->stage_ms[12] = std::min(el(10, 14), el(13, 14));  // source side + chain rule
+      } else {
+        P->stage_ms[12] = el(10, 14);
+      }
       P->stage_ms[14] = el(15, 14);  // whole adjoint call
-      P->stage_ms[15] = el(15, 9);   // source-major lists, recompute if needed
+      P->stage_ms[15] = el(15, 16);  // source-major lists, recompute if asked, weights
     }
     for (int k = 0; k < 16; ++k) out->stage_ms[k] = P->stage_ms[k];
   }
@@ -483,6 +502,12 @@ void fmm_plan_destroy(fmm_plan_t P) {
   if (!P) return;
   if (P->ev_made)
     for (auto& e : P->ev) cudaEventDestroy(e);
+  if (P->side) {
+    cudaStreamSynchronize(P->side);
+    cudaStreamDestroy(P->side);
+    cudaEventDestroy(P->fork_ev);
+    cudaEventDestroy(P->join_ev);
+  }
   delete P;
 }
 

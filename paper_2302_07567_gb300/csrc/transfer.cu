@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_transfer_np(int level_first, int level_
 }
 
 template <typename T, int NP1, bool UP>
-int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s) {
+int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm) {
   static int per_sm = 0, sms = 0;
   auto kern = k_transfer_np<T, NP1, UP>;
   if (per_sm == 0) {
@@ -222,10 +222,11 @@ int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s) {
     FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
     if (per_sm < 1) return FMM_EINVAL;
   }
-  // at most 4 blocks per SM: more make the grid-wide barriers dearer than
-  // the extra blocks help the deepest levels (measured at 2^9 leaves)
+  // at most cap_per_sm (4 by default) blocks per SM: more make the grid-wide
+  // barriers dearer than the extra blocks help the deepest levels (measured
+  // at 2^9 leaves); a transfer beside another kernel takes fewer
   const int64_t most = ((int64_t)1 << (P->kappa - 1)) * nc;
-  const int grid = (int)std::min<int64_t>({(int64_t)std::min(per_sm, 4) * sms, most});
+  const int grid = (int)std::min<int64_t>({(int64_t)std::min(per_sm, cap_per_sm) * sms, most});
   int first = UP ? P->kappa - 1 : 0, last = UP ? 0 : P->kappa - 1;
   const T* tm = ws_ptr<T>(P, P->lay.tmat);
   void* args[] = {&first, &last, &nc, (void*)&tm, &buf};
@@ -285,24 +286,25 @@ int run_tmats(fmm_plan_s* P, cudaStream_t s) {
 }
 
 template <typename T, int NC, bool UP>
-int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s) {
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm) {
   if (P->kappa == 0) return FMM_OK;
+  const int c = std::max(1, max_blocks_per_sm);
   switch (P->np1) {
-    case 3: return launch_np<T, 3, UP>(P, NC, buf, s);
-    case 5: return launch_np<T, 5, UP>(P, NC, buf, s);
-    case 7: return launch_np<T, 7, UP>(P, NC, buf, s);
-    case 9: return launch_np<T, 9, UP>(P, NC, buf, s);
+    case 3: return launch_np<T, 3, UP>(P, NC, buf, s, c);
+    case 5: return launch_np<T, 5, UP>(P, NC, buf, s, c);
+    case 7: return launch_np<T, 7, UP>(P, NC, buf, s, c);
+    case 9: return launch_np<T, 9, UP>(P, NC, buf, s, c);
     default: return launch_all<T, NC, UP>(P, buf, s);
   }
 }
 
-template int run_transfer<float, 4, true>(fmm_plan_s*, float*, cudaStream_t);
-template int run_transfer<double, 4, true>(fmm_plan_s*, double*, cudaStream_t);
-template int run_transfer<float, 6, false>(fmm_plan_s*, float*, cudaStream_t);
-template int run_transfer<double, 6, false>(fmm_plan_s*, double*, cudaStream_t);
-template int run_transfer<float, 6, true>(fmm_plan_s*, float*, cudaStream_t);
-template int run_transfer<double, 6, true>(fmm_plan_s*, double*, cudaStream_t);
-template int run_transfer<float, 4, false>(fmm_plan_s*, float*, cudaStream_t);
-template int run_transfer<double, 4, false>(fmm_plan_s*, double*, cudaStream_t);
+template int run_transfer<float, 4, true>(fmm_plan_s*, float*, cudaStream_t, int);
+template int run_transfer<double, 4, true>(fmm_plan_s*, double*, cudaStream_t, int);
+template int run_transfer<float, 6, false>(fmm_plan_s*, float*, cudaStream_t, int);
+template int run_transfer<double, 6, false>(fmm_plan_s*, double*, cudaStream_t, int);
+template int run_transfer<float, 6, true>(fmm_plan_s*, float*, cudaStream_t, int);
+template int run_transfer<double, 6, true>(fmm_plan_s*, double*, cudaStream_t, int);
+template int run_transfer<float, 4, false>(fmm_plan_s*, float*, cudaStream_t, int);
+template int run_transfer<double, 4, false>(fmm_plan_s*, double*, cudaStream_t, int);
 
 }  // namespace fmm
