@@ -48,6 +48,7 @@ HOT = {"m2l": (32.0, "m2l_interactions"), "p2p_l2p": (32.0, "p2p_interactions"),
 # kernel is unchanged since that capture; reported for that workload only.
 TRAFFIC_CYL64K = {"adj_source": 11853568 + 350464, "adj_target": 9832960 + 73472, "p2p_l2p": 7996160 + 3840,
                   "m2l": 2674944, "adj_m2lt": 3963648}
+CONCURRENT = ("adj_target", "adj_m2lt")  # stages that overlap each other (two streams)
 SMS = 152          # GB300 streaming multiprocessors
 FP32_LANES = 128   # FP32 FMA lanes per SM
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -271,7 +272,13 @@ def run_ours(args, rank, world, local):
                    and args.passes == "fwd+adj" else None)
         kernels[k] = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
                       "frac": (flop / (ms / 1e3) / 1e12 / peak) if peak else None, "traffic": traffic}
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    # the adjoint runs its target side and M2L^T on two streams at once: their
+    # stage times are shared-GPU times, so the dominant kernel is chosen among
+    # the stages that have the GPU to themselves
+    for k in CONCURRENT:
+        if k in kernels:
+            kernels[k]["concurrent"] = True
+    dom = max((k for k in kernels if k not in CONCURRENT), key=lambda k: kernels[k]["ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak, "unit": "TFLOP/s",
             "frac": kernels[dom]["frac"], "traffic": kernels[dom]["traffic"],
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
