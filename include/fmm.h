@@ -70,7 +70,12 @@ typedef enum fmm_flags {
                             their CSR offsets, and sum |S_t||S_s| = N^2 over the
                             lists; a failure returns FMM_EBOUNDS before any kernel
                             indexes through the bad value (costs one more wait)     */
-  FMM_TIMING = 4u        /* record CUDA events around each stage (fmm_plan_stats)    */
+  FMM_TIMING = 4u,       /* record CUDA events around each stage (fmm_plan_stats)    */
+  FMM_SIZE_AWARE = 8u    /* not in the paper: in the traversal (Alg. 17) an admissible
+                            pair with |S_t||S_s| < m^2 particle pairs (m = (n+1)^3) is
+                            evaluated directly, as P2P of all leaf pairs under it,
+                            instead of by M2L: fewer operations and no truncation
+                            error for that pair                                     */
 } fmm_flags;
 
 typedef struct fmm_plan_s* fmm_plan_t;

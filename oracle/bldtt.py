@@ -69,8 +69,27 @@ def admissible(lo1, hi1, lo2, hi2, s, eta: float) -> bool:
 
 
 # --------------------------------------------------------------------- Alg. 17
-def dualtraverse(tree: Tree, eta: float):
-    """Alg. 17 from (1, 1): returns (p2p_itl, m2l_itl) as lists of (target, source)."""
+def leaves_under(tree: Tree, i: int) -> list:
+    """The leaves of the subtree of node i (all at depth kappa)."""
+    out, stack = [], [i]
+    while stack:
+        k = stack.pop()
+        if tree.is_leaf(k):
+            out.append(k)
+        else:
+            stack += [2 * k + 1, 2 * k]
+    return sorted(out)
+
+
+def dualtraverse(tree: Tree, eta: float, m2_substitute: int = 0):
+    """Alg. 17 from (1, 1): returns (p2p_itl, m2l_itl) as lists of (target, source).
+
+    With m2_substitute > 0 (the size-aware variant, not in the paper): an
+    admissible pair with |S_t| |S_s| < m2_substitute is evaluated directly
+    instead of by M2L, as the P2P pairs of all leaf pairs under it.  The
+    particle pairs covered are the same, so the lists still partition the
+    interaction matrix.
+    """
     s = (1.0, 1.0, tree.gbar)
     p2p, m2l = [], []
 
@@ -80,7 +99,12 @@ def dualtraverse(tree: Tree, eta: float):
             p2p.append((i, j))
             return
         if admissible(tree.lo[i], tree.hi[i], tree.lo[j], tree.hi[j], s, eta):
-            m2l.append((i, j))
+            if len(tree.members[i]) * len(tree.members[j]) < m2_substitute:
+                for a in leaves_under(tree, i):
+                    for b in leaves_under(tree, j):
+                        p2p.append((a, b))
+            else:
+                m2l.append((i, j))
         elif li:
             for k in (2 * j, 2 * j + 1):
                 rec(i, k)
@@ -118,13 +142,18 @@ class Plan:
         return self.proxy[i]
 
 
-def build_plan(x, p, n: int, N0: int, eta: float) -> Plan:
-    """Tree (Algs. 1-2 with s = (1,1,gbar)) plus interaction lists (Alg. 17)."""
+def build_plan(x, p, n: int, N0: int, eta: float, size_aware: bool = False) -> Plan:
+    """Tree (Algs. 1-2 with s = (1,1,gbar)) plus interaction lists (Alg. 17).
+
+    size_aware: admissible pairs with fewer particle pairs than proxy-point
+    pairs, |S_t| |S_s| < m^2 with m = (n+1)^3, go to P2P instead of M2L.
+    """
     x = np.asarray(x.detach().numpy() if isinstance(x, torch.Tensor) else x, dtype=np.float64)
     p = np.asarray(p.detach().numpy() if isinstance(p, torch.Tensor) else p, dtype=np.float64)
     gb = gamma_bar(p)
     tree = subdivide(x, gb, N0)
-    p2p, m2l = dualtraverse(tree, eta)
+    m = (n + 1) ** 3
+    p2p, m2l = dualtraverse(tree, eta, m * m if size_aware else 0)
     return Plan(tree, n, eta, p2p, m2l)
 
 

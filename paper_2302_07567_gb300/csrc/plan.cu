@@ -213,6 +213,7 @@ int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, doubl
   if (leaf_size < 2 || leaf_size > 4096) return FMM_EINVAL;
   if (!(eta > 0.0) || !std::isfinite(eta)) return FMM_EINVAL;
   if (precision != FMM_FP32 && precision != FMM_FP64) return FMM_EINVAL;
+  if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE)) return FMM_EINVAL;
   fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
   if (!P) return FMM_EINVAL;
   P->N = N;

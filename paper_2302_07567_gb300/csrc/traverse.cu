@@ -17,6 +17,10 @@
 // order a sort by (target << bits | source) gives, whatever the append order.
 // The centre offset of each pair is written as it reaches its final slot.
 //
+// Size-aware variant (FMM_SIZE_AWARE, not in the paper): an admissible pair
+// with |S_t| |S_s| < m^2 particle pairs is cheaper and exact as a direct sum,
+// so every leaf pair under it goes to the P2P list instead of M2L.
+//
 // The admissibility test is Alg. 8 with diam and dist of Algs. 6-7 in FP64
 // with round-to-nearest operations in a fixed order and no contraction:
 // max(r_t, r_s) / d < eta, d = sqrt((v_x^2 + v_y^2) + v_z^2), v = s o (c_t - c_s).
@@ -78,6 +82,8 @@ struct TravArgs {
   uint64_t* m2l;
   int64_t cap_m2l;
   const double* ndiam;
+  const int64_t* ncount;
+  int64_t m2sub;                    // size-aware: admissible pairs below this many particle pairs go to P2P
   double eta;
   int kappa;
   ListArgs lists;
@@ -299,6 +305,22 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
                                             __dmul_rn(v[2], v[2])));
       const double ratio = __ddiv_rn(rt >= ru ? rt : ru, d);
       if (ratio < a.eta) {
+        if (a.m2sub > 0 && a.ncount[t] * a.ncount[u] < a.m2sub) {
+          // fewer particle pairs than proxy-point pairs: every leaf pair under
+          // (t, u) goes to P2P instead (all leaves sit at depth kappa)
+          const int dt = a.kappa - (31 - __clz(t)), du = a.kappa - (31 - __clz(u));
+          const int64_t t0 = (int64_t)t << dt, u0 = (int64_t)u << du;
+          const int64_t nt = (int64_t)1 << dt, nu = (int64_t)1 << du;
+          const unsigned long long at = atomicAdd(&cnt->p2p_count, (unsigned long long)(nt * nu));
+          if ((int64_t)at + nt * nu <= a.cap_p2p) {
+            for (int64_t i = 0; i < nt; ++i)
+              for (int64_t k = 0; k < nu; ++k)
+                a.p2p[at + i * nu + k] = ((uint64_t)(t0 + i) << shift) | (uint64_t)(u0 + k);
+          } else {
+            atomicOr(&cnt->err, kErrOvfP2P);
+          }
+          continue;
+        }
         push(&cnt->m2l_count, a.cap_m2l, a.m2l, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfM2L);
         continue;
       }
@@ -399,6 +421,8 @@ int run_traverse(fmm_plan_s* P, cudaStream_t s) {
   a.m2l = ws_ptr<uint64_t>(P, L.m2l_src);
   a.cap_m2l = P->cap_m2l;
   a.ndiam = ws_ptr<double>(P, L.ndiam);
+  a.ncount = ws_ptr<int64_t>(P, L.ncount);
+  a.m2sub = (P->flags & FMM_SIZE_AWARE) ? (int64_t)P->m * P->m : 0;
   a.eta = P->eta;
   a.kappa = P->kappa;
   a.lists = list_args(P, false);

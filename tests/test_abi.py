@@ -44,6 +44,7 @@ def test_host_side_argument_checks(libpath):
            (100, 4, 64, 0.0, 1), (100, 4, 64, float("nan"), 1), (100, 4, 64, 0.5, 7), (100, 4, 5000, 0.5, 1)]
     for N, n, leaf, eta, prec in bad:
         assert lib.fmm_plan_create(ctypes.byref(h), N, n, leaf, eta, prec, 0) == 1
+    assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 0x100) == 1  # unknown flag bit
     assert lib.fmm_plan_create(ctypes.byref(h), 4096, 4, 64, 0.5, 1, 0) == 0
     lib.fmm_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     nb = ctypes.c_size_t()

@@ -229,3 +229,44 @@ def test_bounds_check_mode_passes_and_changes_nothing(case, prec):
         out.append((E, B, *grads))
     for a, b in zip(*out):
         assert torch.equal(a, b)
+
+
+SIZE_AWARE_CASES = {
+    "gauss4k_n4": lambda: (make_beam("gauss4k"), 4, 64, 0.5),
+    "ragged3001_n3": lambda: (random_beam(3001, seed=1, gamma=20.0, spread=0.05, angle=0.01), 3, 37, 0.5),
+    "cylinder8k_n3": lambda: (make_beam("cylinder64k", N=8192), 3, 32, 0.5),
+}
+
+
+@pytest.mark.parametrize("name", list(SIZE_AWARE_CASES))
+def test_size_aware_variant_matches_oracle(name):
+    """FMM_SIZE_AWARE: admissible pairs below m^2 particle pairs go to P2P.  The
+    lists equal the oracle's size-aware plan, FP64 fields and gradients match
+    its FMM, and the error against the brute force does not grow."""
+    (x, p, q), n, leaf, eta = SIZE_AWARE_CASES[name]()
+    N = len(x)
+    ref = bldtt.build_plan(x, p, n, leaf, eta, size_aware=True)
+    plain = bldtt.build_plan(x, p, n, leaf, eta)
+    assert len(ref.m2l) < len(plain.m2l)
+    X, Pm, Q = dev(x, p, q)
+    plan = fmm.Plan(N, n, leaf, eta, precision="fp64", flags=fmm.FMM_SIZE_AWARE)
+    E, B = plan.field(X, Pm, Q)
+    np.testing.assert_array_equal(plan.export("p2p"), np.array(sorted(ref.p2p), dtype=np.int32))
+    np.testing.assert_array_equal(plan.export("m2l"), np.array(sorted(ref.m2l), dtype=np.int32).reshape(-1, 2))
+    Er, Br = bldtt.fmm_fields(x, p, q, n, leaf, eta, plan=ref)
+    assert metrics.field_error(E.cpu().numpy(), B.cpu().numpy(), Er.numpy(), Br.numpy()) < 1e-12
+    rng = np.random.default_rng(5)
+    wE, wB = rng.standard_normal((N, 3)), rng.standard_normal((N, 3))
+    from oracle import gradient
+    _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, ref)
+    dx, dp, dq = plan.adjoint(X, Pm, Q, *dev(wE, wB))
+    for a, b in ((dx, gx), (dp, gp), (dq, gq)):
+        a, b = a.cpu().numpy(), b.numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-10
+    E32, B32 = fmm.Plan(N, n, leaf, eta, precision="fp32", flags=fmm.FMM_SIZE_AWARE).field(X, Pm, Q)
+    assert metrics.field_error(E32.double().cpu().numpy(), B32.double().cpu().numpy(), Er.numpy(), Br.numpy()) < 1e-5
+    Ed, Bd = physics.direct_fields(x, p, q)
+    Ep, Bp = bldtt.fmm_fields(x, p, q, n, leaf, eta, plan=plain)
+    e_sa = metrics.field_error(E.cpu().numpy(), B.cpu().numpy(), Ed.numpy(), Bd.numpy())
+    e_plain = metrics.field_error(Ep.numpy(), Bp.numpy(), Ed.numpy(), Bd.numpy())
+    assert e_sa <= e_plain, (e_sa, e_plain)

@@ -181,3 +181,46 @@ def test_planted_mistakes_are_caught(monkeypatch, mistake):
         monkeypatch.setattr(bldtt, "m2m", bad)
     with pytest.raises(AssertionError):
         test_polynomial_kernel_is_exact(3)
+
+
+# ------------------------------------------------ size-aware M2L -> P2P variant
+@pytest.mark.parametrize("N,N0,n,eta", [(600, 8, 2, 0.5), (1024, 16, 3, 0.5), (513, 16, 2, 0.7)])
+def test_size_aware_lists_partition_all_pairs(N, N0, n, eta):
+    """Substituted pairs are expanded into leaf pairs: every ordered particle
+    pair is still covered once, M2L keeps only pairs with |S_t||S_s| >= m^2,
+    and every admissible pair that left M2L is below m^2."""
+    x, p, q = random_beam(N, seed=N + 1, gamma=20.0)
+    plain = bldtt.build_plan(x, p, n, N0, eta)
+    sized = bldtt.build_plan(x, p, n, N0, eta, size_aware=True)
+    np.testing.assert_array_equal(_coverage(sized), np.ones((N, N), dtype=np.int64))
+    tr, m2 = sized.tree, ((n + 1) ** 3) ** 2
+    size = lambda i: len(tr.members[i])  # noqa: E731
+    assert all(tr.is_leaf(t) and tr.is_leaf(u) for t, u in sized.p2p)
+    assert all(size(t) * size(u) >= m2 for t, u in sized.m2l)
+    moved = set(plain.m2l) - set(sized.m2l)
+    assert moved and all(size(t) * size(u) < m2 for t, u in moved)
+    assert set(sized.m2l) <= set(plain.m2l)
+    assert len(sized.p2p) == len(plain.p2p) + sum(
+        len(bldtt.leaves_under(tr, t)) * len(bldtt.leaves_under(tr, u)) for t, u in moved)
+
+
+def test_size_aware_with_m2_above_n2_is_brute_force():
+    """m^2 = 125^2 > N^2: every admissible pair is substituted, so the FMM is
+    the direct sum to rounding."""
+    x, p, q = random_beam(100, seed=21, gamma=5.0)
+    plan = bldtt.build_plan(x, p, 4, 8, 0.5, size_aware=True)
+    assert not plan.m2l and plan.p2p
+    E, B = bldtt.fmm_fields(x, p, q, 4, 8, 0.5, plan=plan)
+    Ed, Bd = physics.direct_fields(x, p, q)
+    assert metrics.field_error(E.numpy(), B.numpy(), Ed.numpy(), Bd.numpy()) < 1e-13
+
+
+def test_size_aware_error_is_not_larger():
+    x, p, q = random_beam(1500, seed=22, gamma=15.0)
+    Ed, Bd = physics.direct_fields(x, p, q)
+    errs = []
+    for sa in (False, True):
+        plan = bldtt.build_plan(x, p, 2, 16, 0.5, size_aware=sa)
+        E, B = bldtt.fmm_fields(x, p, q, 2, 16, 0.5, plan=plan)
+        errs.append(metrics.field_error(E.numpy(), B.numpy(), Ed.numpy(), Bd.numpy()))
+    assert errs[1] < errs[0], errs
