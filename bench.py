@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 GPU FMM side measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the paper's uniform-cube experiments (Figs. 2, 3, Section 11) instead of the bench line")
     ap.add_argument("--size-aware", action="store_true",
                     help="admissible pairs with fewer particle pairs than proxy-point pairs go to P2P (not in the paper)")
     ap.add_argument("--profile", action="store_true",
@@ -376,9 +378,69 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The paper's own experiments on its uniform-cube workload (Section 5), on this GPU.
+
+    Fig. 2: forward time against the error of Eq. 5.1 for eta in {0.3, 0.4, 0.5} and
+    n in {2, 4, 6, 8, 10} with N0 = (n+1)^3, N = 1.28e6.  Fig. 3: forward time against N
+    for n = 4, N0 = 125, eta = 0.5.  Section 11 (Fig. 7): N = 2.56e7 with the same
+    parameters.  Times are CUDA-event medians of the whole fmm_field call (inputs in HBM);
+    errors are max over E, B of the relative L2 error on 4096 sampled targets against the
+    FP64 brute force.  One JSON line per point.
+    """
+    import torch
+
+    from paper_2302_07567_gb300 import fmm
+
+    dev = torch.device("cuda", 0)
+
+    def point(N, n, N0, eta, prec, reps=3, err=True, exp=""):
+        x, p, q = make_beam("cube", N=N)
+        X, Pm, Q = (torch.as_tensor(a, device=dev) for a in (x, p, q))
+        plan = fmm.Plan(N, n, N0, eta, precision=prec)
+        for _ in range(2):
+            plan.field(X, Pm, Q)
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            E, B = plan.field(X, Pm, Q)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out = {"sweep": exp, "N": N, "n": n, "N0": N0, "eta": eta, "precision": prec,
+               "ms": statistics.median(times), "particles_per_s": N / (statistics.median(times) / 1e3)}
+        if err:
+            st = plan.stats()
+            tg = torch.as_tensor(sample_targets(N, 4096, tag=9), device=dev)
+            Ed, Bd = fmm.direct_field(X, Pm, Q, gbar=st["gbar"], targets=tg)
+            rel = lambda a, b: float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))  # noqa: E731
+            out["error"] = max(rel(E[tg], Ed), rel(B[tg], Bd))
+            out["m2l_pairs"], out["p2p_pairs"] = st["m2l_pairs"], st["p2p_pairs"]
+        print(json.dumps(out), flush=True)
+        del plan
+        torch.cuda.empty_cache()
+
+    for eta in (0.3, 0.4, 0.5):
+        for n in (2, 4, 6, 8, 10):
+            point(1_280_000, n, (n + 1) ** 3, eta, "fp32", exp="fig2")
+    for eta in (0.5,):
+        for n in (2, 4, 6):
+            point(1_280_000, n, (n + 1) ** 3, eta, "fp64", exp="fig2")
+    for N in (10_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000, 4_000_000, 8_000_000,
+              16_000_000):
+        point(N, 4, 125, 0.5, "fp32", err=False, exp="fig3")
+    point(25_600_000, 4, 125, 0.5, "fp32", exp="sec11")
+    point(25_600_000, 4, 125, 0.5, "fp64", reps=1, err=False, exp="sec11")
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
