@@ -120,7 +120,10 @@ int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q
  * with the tree, its boxes, the interaction lists and gbar held fixed at the
  * values of the last fmm_field call.  wE, wB: device [N,3] of the plan's
  * output type.  x, p, q must be the arrays of the last fmm_field call, still
- * unchanged.  Returns FMM_ESTATE if no successful fmm_field preceded it. */
+ * unchanged.  Returns FMM_ESTATE if no successful fmm_field preceded it.
+ * The source side's far field runs on a second stream the plan owns, beside
+ * the target-side kernel on `stream`; the call joins it into `stream` before
+ * it returns, so work queued later on `stream` is ordered after all of it. */
 int fmm_field_adjoint(fmm_plan_t plan, const double* x, const double* p, const double* q,
                       const void* wE, const void* wB, double* dx, double* dp, double* dq,
                       void* stream);
@@ -134,8 +137,8 @@ typedef struct fmm_stats {
   double m2l_interactions;               /* m2l_pairs * (n+1)^6                       */
   int64_t cap_p2p, cap_m2l, cap_frontier;
   /* stage times of the last calls in ms (FMM_TIMING only, else 0):
-     forward: 0 setup, 1 tree, 2 upward, 3 traversal with the ordering of the
-     lists and the host wait after it, 4 none (0), 5 M2L, 6 L2L,
+     forward: 0 setup, 1 tree, 2 upward pass, 3 traversal with the ordering
+     of the lists, 4 the host read of the list sizes, 5 M2L, 6 L2L,
      7 P2P+L2P, 13 whole forward;  adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T,
      11 target-side particle kernel (near + far), 12 source-side particle kernel
      (near + far + chain rule), 14 whole adjoint, 15 source-major lists and any

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
     const typename Vec4<T>::type* __restrict__ pb, const typename Vec4<T>::type* __restrict__ pl,
     const void* __restrict__ pdc_raw, const typename Vec4<T>::type* __restrict__ wle,
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lcum, Cheb ch, ChebD cd, int m,
-    int groups, int chunks, typename Vec4<T>::type* __restrict__ gout) {
+    int groups, int chunks, int64_t nitems, typename Vec4<T>::type* __restrict__ gout) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 3 : 2;
@@ -462,11 +462,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
   V4* sp = reinterpret_cast<V4*>(smem_raw);
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
   T* sl = reinterpret_cast<T*>(smem_raw + stage_bytes<T>(kRow, KPT, 6, groups, NT));  // [6][m]
-  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x / chunks;
   const int64_t per_pass = (int64_t)KPT * NT;
-  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * per_pass;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
+  __syncthreads();  // the previous item's readers of sl are done
+  const int64_t t = ((int64_t)1 << kappa) + item / chunks;
+  const int64_t c0 = (int64_t)(item % chunks) * per_pass;
   const int64_t st = nstart[t], cnt = min64(ncount[t], c0 + per_pass);
-  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
+  if (c0 >= cnt) continue;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gt = geo[t];
   const int b = off[t], e = off[t + 1];
@@ -624,6 +626,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
       gout[pos] = o;
     }
   }
+  }  // items
 }
 
 // Source side: near field over the source-major P2P list, far field from the
@@ -946,16 +949,25 @@ int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, d
   int NT, groups, chunks;
   particle_shape(P->leaf, 1, &NT, &groups, &chunks);  // as the forward P2P
   const int nt = groups * NT;
-  const unsigned grid = (unsigned)(P->nleaves * chunks);
+  const int64_t items = P->nleaves * chunks;
+  unsigned grid = (unsigned)items;
   if (target_side) {
     const size_t smem = stage_bytes<T>(kSplit ? 3 : 2, 1, 6, groups, NT) + sizeof(T) * 6 * P->m;
     static bool attr = false;
     if (!attr) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr = true; }
+    // beside the source side's far field (side stream) the target side keeps
+    // to half of the SMs' block slots, so the other branch finds room
+    if (P->kappa > 0) {
+      int dev = 0, sms = 0;
+      FMM_CUDA_TRY(cudaGetDevice(&dev));
+      FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
+    }
     k_adj_target<T, 1><<<grid, nt, smem, s>>>(
         ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
         ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
         ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
-        P->cheb, P->chebd, P->m, groups, chunks, ws_ptr<V4>(P, L.adj_part));
+        P->cheb, P->chebd, P->m, groups, chunks, items, ws_ptr<V4>(P, L.adj_part));
   } else {
     const size_t smem = stage_bytes<T>(kSplit ? 4 : 3, 1, 14, groups, NT) + sizeof(T) * 4 * P->m;
     static bool attr = false;
@@ -1012,12 +1024,13 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
     FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
     if ((rc = l2pt<T>(P, t)) != FMM_OK) return rc;
-    // beside the particle kernel the transfers keep to one block per SM
-    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, 1)) != FMM_OK) return rc;  // L2L^T: W up
+    // beside the particle kernel the transfers are launched once per level: a
+    // cooperative launch would wait for the particle kernel to end
+    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, 4, true)) != FMM_OK) return rc;  // L2L^T
     if ((rc = record(P, 11, t)) != FMM_OK) return rc;
     if ((rc = adj_m2l<T>(P, t)) != FMM_OK) return rc;
     if ((rc = record(P, 12, t)) != FMM_OK) return rc;
-    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, 1)) != FMM_OK) return rc;  // M2M^T
+    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, 4, true)) != FMM_OK) return rc;  // M2M^T
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
     FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
   }

@@ -268,7 +268,8 @@ namespace fmm {
 int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
 int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s);
 int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
-int run_upward(fmm_plan_s* P, cudaStream_t s);
+// P2M, M2M (at most xfer_cap blocks per SM in the transfer) and the M2L source table
+int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap = 4, bool per_level = false);
 // traversal and both target-major lists (sorted, CSR, centre offsets), one launch
 int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
@@ -294,7 +295,7 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, 
 // levels (see transfer.cu)
 int run_tmats(fmm_plan_s* P, cudaStream_t s);
 template <typename T, int NC, bool UP>
-int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm = 4);
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm = 4, bool per_level = false);
 int64_t radix_tiles(int64_t n);
 int64_t scan_tmp_words(int64_t n);
 }  // namespace fmm

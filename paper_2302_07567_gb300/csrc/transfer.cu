@@ -11,7 +11,9 @@
 // Each block handles one parent with both children and a group of
 // components at once, so a parent costs three synchronised stages.  One
 // cooperative launch walks all levels (deepest first for UP, root first for
-// DOWN) with a grid-wide barrier between levels.
+// DOWN) with a grid-wide barrier between levels; beside another cooperative
+// kernel (which the driver would run first) the same kernel is launched once
+// per level instead.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(256) k_transfer_np(int level_first, int level_
 }
 
 template <typename T, int NP1, bool UP>
-int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm) {
+int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm, bool per_level) {
   static int per_sm = 0, sms = 0;
   auto kern = k_transfer_np<T, NP1, UP>;
   if (per_sm == 0) {
@@ -226,9 +228,19 @@ int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm) {
   // barriers dearer than the extra blocks help the deepest levels (measured
   // at 2^9 leaves); a transfer beside another kernel takes fewer
   const int64_t most = ((int64_t)1 << (P->kappa - 1)) * nc;
-  const int grid = (int)std::min<int64_t>({(int64_t)std::min(per_sm, cap_per_sm) * sms, most});
-  int first = UP ? P->kappa - 1 : 0, last = UP ? 0 : P->kappa - 1;
+  const int64_t blocks = (int64_t)std::min(per_sm, cap_per_sm) * sms;
   const T* tm = ws_ptr<T>(P, P->lay.tmat);
+  if (per_level) {  // one ordinary launch per level (no grid barrier is reached)
+    for (int i = 0; i < P->kappa; ++i) {
+      const int level = UP ? P->kappa - 1 - i : i;
+      const int grid = (int)std::min<int64_t>(blocks, ((int64_t)1 << level) * nc);
+      kern<<<grid, 256, 0, s>>>(level, level, nc, tm, buf);
+      FMM_LAUNCH_CHECK();
+    }
+    return FMM_OK;
+  }
+  const int grid = (int)std::min<int64_t>(blocks, most);
+  int first = UP ? P->kappa - 1 : 0, last = UP ? 0 : P->kappa - 1;
   void* args[] = {&first, &last, &nc, (void*)&tm, &buf};
   FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(256), args, 0, s));
   FMM_LAUNCH_CHECK();
@@ -286,25 +298,25 @@ int run_tmats(fmm_plan_s* P, cudaStream_t s) {
 }
 
 template <typename T, int NC, bool UP>
-int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm) {
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm, bool per_level) {
   if (P->kappa == 0) return FMM_OK;
   const int c = std::max(1, max_blocks_per_sm);
   switch (P->np1) {
-    case 3: return launch_np<T, 3, UP>(P, NC, buf, s, c);
-    case 5: return launch_np<T, 5, UP>(P, NC, buf, s, c);
-    case 7: return launch_np<T, 7, UP>(P, NC, buf, s, c);
-    case 9: return launch_np<T, 9, UP>(P, NC, buf, s, c);
+    case 3: return launch_np<T, 3, UP>(P, NC, buf, s, c, per_level);
+    case 5: return launch_np<T, 5, UP>(P, NC, buf, s, c, per_level);
+    case 7: return launch_np<T, 7, UP>(P, NC, buf, s, c, per_level);
+    case 9: return launch_np<T, 9, UP>(P, NC, buf, s, c, per_level);
     default: return launch_all<T, NC, UP>(P, buf, s);
   }
 }
 
-template int run_transfer<float, 4, true>(fmm_plan_s*, float*, cudaStream_t, int);
-template int run_transfer<double, 4, true>(fmm_plan_s*, double*, cudaStream_t, int);
-template int run_transfer<float, 6, false>(fmm_plan_s*, float*, cudaStream_t, int);
-template int run_transfer<double, 6, false>(fmm_plan_s*, double*, cudaStream_t, int);
-template int run_transfer<float, 6, true>(fmm_plan_s*, float*, cudaStream_t, int);
-template int run_transfer<double, 6, true>(fmm_plan_s*, double*, cudaStream_t, int);
-template int run_transfer<float, 4, false>(fmm_plan_s*, float*, cudaStream_t, int);
-template int run_transfer<double, 4, false>(fmm_plan_s*, double*, cudaStream_t, int);
+template int run_transfer<float, 4, true>(fmm_plan_s*, float*, cudaStream_t, int, bool);
+template int run_transfer<double, 4, true>(fmm_plan_s*, double*, cudaStream_t, int, bool);
+template int run_transfer<float, 6, false>(fmm_plan_s*, float*, cudaStream_t, int, bool);
+template int run_transfer<double, 6, false>(fmm_plan_s*, double*, cudaStream_t, int, bool);
+template int run_transfer<float, 6, true>(fmm_plan_s*, float*, cudaStream_t, int, bool);
+template int run_transfer<double, 6, true>(fmm_plan_s*, double*, cudaStream_t, int, bool);
+template int run_transfer<float, 4, false>(fmm_plan_s*, float*, cudaStream_t, int, bool);
+template int run_transfer<double, 4, false>(fmm_plan_s*, double*, cudaStream_t, int, bool);
 
 }  // namespace fmm

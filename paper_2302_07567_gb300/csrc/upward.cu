@@ -219,7 +219,7 @@ int launch_p2m(fmm_plan_s* P, cudaStream_t s) {
 }
 
 template <typename T>
-int upward_t(fmm_plan_s* P, cudaStream_t s) {
+int upward_t(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
   const int nv = (int)div_up(P->m, 256);
   int rc;
   switch (nv) {
@@ -235,7 +235,7 @@ int upward_t(fmm_plan_s* P, cudaStream_t s) {
   }
   if (rc != FMM_OK) return rc;
   const Layout& L = P->lay;
-  rc = run_transfer<T, 4, true>(P, ws_ptr<T>(P, L.mpole), s);  // M2M, all levels
+  rc = run_transfer<T, 4, true>(P, ws_ptr<T>(P, L.mpole), s, xfer_cap, per_level);  // M2M, all levels
   if (rc != FMM_OK) return rc;
   const int64_t total = (P->C + 1) * (int64_t)P->m;
   k_srctab<T><<<(unsigned)std::min<int64_t>(div_up(total, 256), 8192), 256, 0, s>>>(
@@ -272,8 +272,9 @@ int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, c
   return FMM_OK;
 }
 
-int run_upward(fmm_plan_s* P, cudaStream_t s) {
-  return P->precision == FMM_FP32 ? upward_t<float>(P, s) : upward_t<double>(P, s);
+int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
+  return P->precision == FMM_FP32 ? upward_t<float>(P, s, xfer_cap, per_level)
+                                  : upward_t<double>(P, s, xfer_cap, per_level);
 }
 
 int run_l2l(fmm_plan_s* P, cudaStream_t s) {
