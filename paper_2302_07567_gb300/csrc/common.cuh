@@ -122,6 +122,8 @@ struct fmm_plan_s {
   bool ev_made = false;
   cudaStream_t side = nullptr;    // second stream for independent branches (higher priority)
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  void* hpin = nullptr;           // pinned host copy of the counters and scalars after the traversal
+  cudaEvent_t trav_ev = nullptr;  // recorded after that copy
   double stage_ms[16] = {};
 };
 

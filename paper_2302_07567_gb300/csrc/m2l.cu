@@ -17,12 +17,13 @@ namespace {
 
 template <typename T, int KPT>
 __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
-                                             int shift, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
+                                             int shift, const unsigned int* __restrict__ err, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
                                              const void* __restrict__ pdc, Cheb ch, int m,
                                              const typename Vec4<T>::type* __restrict__ src, T* __restrict__ Lout) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ unsigned char smem_raw[];
   V4* sm = reinterpret_cast<V4*>(smem_raw);
+  if (*err) return;  // the traversal failed: the lists are incomplete
   for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {  // targets, longest list first
   const int64_t t = order[w];
   const int np1 = ch.np1;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, 
 // zero mask.  The running Kahan sums across sources live in shared memory.
 template <int NP1, int G, int SPLIT>
 __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* __restrict__ keys,
-                                                              const int32_t* __restrict__ off, int shift, const int32_t* __restrict__ order, int64_t nitems, unsigned int* __restrict__ work,
+                                                              const int32_t* __restrict__ off, int shift, const unsigned int* __restrict__ err, const int32_t* __restrict__ order, int64_t nitems, unsigned int* __restrict__ work,
                                                               const NodeGeo* __restrict__ geo,
                                                               const float4* __restrict__ pdc, Cheb ch,
                                                               const float* __restrict__ M, float* __restrict__ Lout) {
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* _
   __shared__ float4 sm[m];              // source effective masses (a, b~x, b~y, b~z)
   __shared__ float syz[NP1];            // source point offsets along z
   __shared__ float sacc[KPT][12][NT];   // Kahan sums and compensations
+  if (*err) return;  // the traversal failed: the lists are incomplete
   __shared__ int64_t s_item;
   for (;;) {  // items (target, mu3 chunk) fetched in the work order: longest lists first
   if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(work, 1u);
@@ -261,7 +263,7 @@ int launch_fast(fmm_plan_s* P, cudaStream_t s) {
   Counters* cnt = ws_ptr<Counters>(P, L.counters);
   FMM_CUDA_TRY(cudaMemsetAsync(&cnt->work[0], 0, sizeof(unsigned int), s));
   k_m2l_fast<NP1, G, SPLIT><<<grid, NP1 * NP1 * G, 0, s>>>(
-      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1,
+      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1, &cnt->err,
       ws_ptr<int32_t>(P, L.m2l_order), P->C * SPLIT, &cnt->work[0], ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<float4>(P, L.m2l_dc), P->cheb, ws_ptr<float>(P, L.mpole), ws_ptr<float>(P, L.local));
   FMM_LAUNCH_CHECK();
@@ -301,7 +303,8 @@ int launch(fmm_plan_s* P, int nt, cudaStream_t s) {
   unsigned grid = 0;
   if (int rc = resident_blocks(k_m2l<T, KPT>, nt, smem, P->C, &grid)) return rc;
   k_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
-                                        P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_order), P->C,
+                                        P->kappa + 1, &ws_ptr<Counters>(P, L.counters)->err,
+                                        ws_ptr<int32_t>(P, L.m2l_order), P->C,
                                         ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_dc, P->cheb, P->m,
                                                   ws_ptr<typename Vec4<T>::type>(P, L.srct), ws_ptr<T>(P, L.local));
   FMM_LAUNCH_CHECK();

@@ -40,7 +40,7 @@ namespace {
 
 template <typename T, int KPT>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
-    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift, const unsigned int* __restrict__ err,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
     const typename Vec4<T>::type* __restrict__ pb, const float4* __restrict__ pl,  // Vec4<T> rows
@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
   constexpr int kRow = kSplit ? 3 : 2;                      // V4 per staged source particle
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);                                // [blockDim][kRow]
+  if (*err) return;  // the traversal failed: the lists are incomplete
   const size_t stage = max(sizeof(V4) * kRow * blockDim.x,
                            sizeof(T) * (size_t)(groups - 1) * KPT * 12 * (blockDim.x / groups));
   T* sl = reinterpret_cast<T*>(smem_raw + stage);  // [6][m]
@@ -275,7 +276,8 @@ int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
     attr_set = true;
   }
   k_p2p_l2p<T, KPT><<<(unsigned)(P->nleaves * chunks), nt, smem, s>>>(
-      ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+      ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1,
+      &ws_ptr<Counters>(P, L.counters)->err, ws_ptr<int64_t>(P, L.nstart),
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb), ws_ptr<float4>(P, L.pl),
       P->ws + L.p2p_dc, ws_ptr<T>(P, L.local), P->cheb, P->m, ws_ptr<int32_t>(P, L.perm),

@@ -293,24 +293,40 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   if ((rc = record(P, 17, s)) != FMM_OK) return rc;
   if ((rc = run_traverse(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 3, s)) != FMM_OK) return rc;
-  Counters hc;
-  double hs[8];
-  FMM_CUDA_TRY(cudaMemcpyAsync(&hc, P->ws + P->lay.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-  FMM_CUDA_TRY(cudaMemcpyAsync(hs, P->ws + P->lay.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
-  FMM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (hc.err & kErrNonFinite) return FMM_ENONFINITE;
-  if ((hc.err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || (int64_t)hc.p2p_count > P->cap_p2p ||
-      (int64_t)hc.m2l_count > P->cap_m2l) {
-    P->p2p_count = (int64_t)hc.p2p_count;
-    P->m2l_count = (int64_t)hc.m2l_count;
-    return FMM_EOVERFLOW;
+  // The list sizes, error flags and scalars go to pinned host memory right
+  // after the traversal, and M2L, L2L and P2P are queued at once: the host
+  // waits only for that copy, the GPU not at all.  On an error the M2L and
+  // P2P kernels return at their first instruction (they read the device error
+  // word), so nothing indexes through an incomplete list and E, B stay
+  // unwritten.  FMM_BOUNDS_CHECK needs the sizes first and waits before.
+  if (!P->hpin) {
+    FMM_CUDA_TRY(cudaHostAlloc(&P->hpin, 256 + 8 * sizeof(double), cudaHostAllocDefault));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&P->trav_ev, cudaEventDisableTiming));
   }
-  P->p2p_count = (int64_t)hc.p2p_count;
-  P->m2l_count = (int64_t)hc.m2l_count;
-  P->gbar = hs[0];
-  P->munit = hs[1];
-  P->lunit = hs[2];
-  if ((P->flags & FMM_BOUNDS_CHECK) && (rc = run_bounds_check(P, false, s)) != FMM_OK) return rc;
+  Counters* hc = static_cast<Counters*>(P->hpin);
+  double* hs = reinterpret_cast<double*>(static_cast<char*>(P->hpin) + 256);
+  static_assert(sizeof(Counters) <= 256, "counters fit the pinned slot");
+  FMM_CUDA_TRY(cudaMemcpyAsync(hc, P->ws + P->lay.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaMemcpyAsync(hs, P->ws + P->lay.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaEventRecord(P->trav_ev, s));
+  auto read_back = [&]() -> int {
+    FMM_CUDA_TRY(cudaEventSynchronize(P->trav_ev));
+    P->p2p_count = (int64_t)hc->p2p_count;
+    P->m2l_count = (int64_t)hc->m2l_count;
+    if (hc->err & kErrNonFinite) return FMM_ENONFINITE;
+    if ((hc->err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || P->p2p_count > P->cap_p2p ||
+        P->m2l_count > P->cap_m2l)
+      return FMM_EOVERFLOW;
+    P->gbar = hs[0];
+    P->munit = hs[1];
+    P->lunit = hs[2];
+    return FMM_OK;
+  };
+  const bool wait_first = (P->flags & FMM_BOUNDS_CHECK) != 0;
+  if (wait_first) {
+    if ((rc = read_back()) != FMM_OK) return rc;
+    if ((rc = run_bounds_check(P, false, s)) != FMM_OK) return rc;
+  }
   if ((rc = record(P, 4, s)) != FMM_OK) return rc;
   if ((rc = record(P, 5, s)) != FMM_OK) return rc;
   if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
@@ -319,6 +335,7 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   if ((rc = record(P, 7, s)) != FMM_OK) return rc;
   if ((rc = run_p2p_l2p(P, E, B, s)) != FMM_OK) return rc;
   if ((rc = record(P, 8, s)) != FMM_OK) return rc;
+  if (!wait_first && (rc = read_back()) != FMM_OK) return rc;
   P->have_forward = true;
   P->transposed_valid = false;
   P->locals_valid = true;
@@ -378,7 +395,7 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[1] = el(1, 2);
     P->stage_ms[2] = el(2, 17);  // upward pass
     P->stage_ms[3] = el(17, 3);  // traversal and lists
-    P->stage_ms[4] = el(3, 5);   // host read of the list sizes
+    P->stage_ms[4] = el(3, 5);   // copy of the list sizes to the host
     P->stage_ms[5] = el(5, 6);
     P->stage_ms[6] = el(6, 7);
     P->stage_ms[7] = el(7, 8);
@@ -507,6 +524,11 @@ void fmm_plan_destroy(fmm_plan_t P) {
   if (!P) return;
   if (P->ev_made)
     for (auto& e : P->ev) cudaEventDestroy(e);
+  if (P->hpin) {
+    cudaEventSynchronize(P->trav_ev);
+    cudaEventDestroy(P->trav_ev);
+    cudaFreeHost(P->hpin);
+  }
   if (P->side) {
     cudaStreamSynchronize(P->side);
     cudaStreamDestroy(P->side);
