@@ -44,7 +44,7 @@ void make_layout(fmm_plan_s* P) {
   L.scal = take(16 * sizeof(double));
   const size_t np0 = (size_t)div_up(P->N, 2048);
   L.psum_part = take(3 * 2 * (np0 + 2) * sizeof(double));
-  L.qmax_part = take(1024 * sizeof(double));
+  L.qmax_part = take((np0 + 2) * sizeof(double));
   L.keys = take(sort_n * 8);
   L.keys_alt = take(alt_n * 8);
   L.vals = take(3 * N * 4);

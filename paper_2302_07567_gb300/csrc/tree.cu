@@ -29,12 +29,13 @@ constexpr int kPartThreads = 256;
 constexpr int kPartItems = 8;
 constexpr int kPartChunk = kPartThreads * kPartItems;
 
-// Adjacent-pair (binary tree) sum of the aligned chunk of 2048 terms
-// in[chunk*2048 ...], stride `stride`, zero beyond n.  Writes out[chunk].
-__global__ void __launch_bounds__(kRedThreads) k_pairwise(const double* __restrict__ in, int64_t n,
-                                                         int64_t stride, double* __restrict__ out) {
-  __shared__ double wsum[kRedThreads / 32];
-  const int64_t base = (int64_t)blockIdx.x * kRedChunk + (int64_t)threadIdx.x * kRedItems;
+// Adjacent-pair (binary tree) sum of the aligned chunk `chunk` of 2048
+// terms in[i * stride], zero beyond n, by the whole block; the result is
+// valid in thread 0.  Eight terms per thread, then the warp butterfly
+// (adjacent lanes first), then the eight warp sums: one fixed binary tree.
+__device__ __forceinline__ double chunk_pairwise(const double* __restrict__ in, int64_t n, int64_t stride,
+                                                 int64_t chunk, double* wsum) {
+  const int64_t base = chunk * kRedChunk + (int64_t)threadIdx.x * kRedItems;
   double e[kRedItems];
 #pragma unroll
   for (int k = 0; k < kRedItems; ++k) e[k] = (base + k < n) ? in[(base + k) * stride] : 0.0;
@@ -44,52 +45,82 @@ __global__ void __launch_bounds__(kRedThreads) k_pairwise(const double* __restri
   for (int o = 1; o < 32; o <<= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = __dadd_rn(__dadd_rn(__dadd_rn(wsum[0], wsum[1]), __dadd_rn(wsum[2], wsum[3])),
-                         __dadd_rn(__dadd_rn(wsum[4], wsum[5]), __dadd_rn(wsum[6], wsum[7])));
-    out[blockIdx.x] = a;
-  }
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    r = __dadd_rn(__dadd_rn(__dadd_rn(wsum[0], wsum[1]), __dadd_rn(wsum[2], wsum[3])),
+                  __dadd_rn(__dadd_rn(wsum[4], wsum[5]), __dadd_rn(wsum[6], wsum[7])));
+  __syncthreads();
+  return r;
 }
 
-// max |q| per chunk, and non-finite inputs flagged.
-__global__ void k_check_inputs(const double* __restrict__ x, const double* __restrict__ p,
-                               const double* __restrict__ q, int64_t N, double* __restrict__ qmax,
-                               Counters* cnt) {
-  __shared__ double wmax[kRedThreads / 32];
-  double m = 0.0;
+// First level of the three momentum sums (grid.y = component k): chunk sums
+// of p[i][k]; the same blocks flag non-finite x, p, q and (k = 0) take the
+// chunk's max |q|.
+__global__ void __launch_bounds__(kRedThreads) k_setup_first(const double* __restrict__ x,
+                                                            const double* __restrict__ p,
+                                                            const double* __restrict__ q, int64_t N,
+                                                            double* __restrict__ part, int64_t comp_step,
+                                                            double* __restrict__ qmax, Counters* cnt) {
+  __shared__ double wsum[kRedThreads / 32];
+  const int k = blockIdx.y;
+  const int64_t base = (int64_t)blockIdx.x * kRedChunk + (int64_t)threadIdx.x * kRedItems;
   bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double a = fabs(q[i]);
-    bad |= !isfinite(q[i]);
-    m = fmax(m, a);
+  double m = 0.0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bad |= !isfinite(x[3 * i + k]) || !isfinite(p[3 * i + k]);
+  for (int j = 0; j < kRedItems; ++j) {
+    const int64_t i = base + j;
+    if (i >= N) break;
+    bad |= !isfinite(x[3 * i + k]) || !isfinite(p[3 * i + k]);
+    if (k == 0) {
+      bad |= !isfinite(q[i]);
+      m = fmax(m, fabs(q[i]));
+    }
   }
   if (bad) atomicOr(&cnt->err, kErrNonFinite);
+  const double r = chunk_pairwise(p + k, N, 3, blockIdx.x, wsum);
+  if (threadIdx.x == 0) part[k * comp_step + blockIdx.x] = r;
+  if (k == 0) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, wmax[w]);
-    qmax[blockIdx.x] = r;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kRedThreads / 32; ++w) t = fmax(t, wsum[w]);
+      qmax[blockIdx.x] = t;
+    }
   }
 }
 
+// A further level of the three sums (more than 2048 partials left).
+__global__ void __launch_bounds__(kRedThreads) k_pairwise(const double* __restrict__ in, int64_t n,
+                                                         int64_t comp_step, double* __restrict__ out) {
+  __shared__ double wsum[kRedThreads / 32];
+  const double r = chunk_pairwise(in + blockIdx.y * comp_step, n, 1, blockIdx.x, wsum);
+  if (threadIdx.x == 0) out[blockIdx.y * comp_step + blockIdx.x] = r;
+}
+
+// Last level (at most 2048 partials per component), max |q| and
 // scal[0] = gbar, scal[1] = mass unit mu (power of two near max|q|).
-__global__ void k_gbar(const double* __restrict__ sx, const double* __restrict__ sy,
-                       const double* __restrict__ sz, int64_t N, const double* __restrict__ qmax,
-                       int nq, double* __restrict__ scal) {
-  double m = 0.0;  // max|q| over the partials, one warp
-  for (int i = threadIdx.x; i < nq; i += 32) m = fmax(m, qmax[i]);
+__global__ void __launch_bounds__(kRedThreads) k_setup_final(const double* __restrict__ part, int64_t n,
+                                                            int64_t comp_step, int64_t N,
+                                                            const double* __restrict__ qmax, int64_t nq,
+                                                            double* __restrict__ scal) {
+  __shared__ double wsum[kRedThreads / 32];
+  double sum[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sum[k] = chunk_pairwise(part + k * comp_step, n, 1, 0, wsum);
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < nq; i += blockDim.x) m = fmax(m, qmax[i]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double dn = (double)N;
-  double px = __ddiv_rn(sx[0], dn), py = __ddiv_rn(sy[0], dn), pz = __ddiv_rn(sz[0], dn);
-  double pp = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 0; w < kRedThreads / 32; ++w) m = fmax(m, wsum[w]);
+  const double dn = (double)N;
+  const double px = __ddiv_rn(sum[0], dn), py = __ddiv_rn(sum[1], dn), pz = __ddiv_rn(sum[2], dn);
+  const double pp = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
   scal[0] = __dsqrt_rn(__dadd_rn(1.0, pp));
   scal[1] = (m > 0.0 && isfinite(m)) ? ldexp(1.0, (int)rint(log2(m))) : 1.0;
 }
@@ -481,35 +512,24 @@ int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   const Layout& L = P->lay;
   const int64_t N = P->N;
   Counters* cnt = ws_ptr<Counters>(P, L.counters);
-  double* scal = ws_ptr<double>(P, L.scal);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(Counters), s));
-  const int nq = (int)std::min<int64_t>(1024, div_up(N, kRedThreads));
-  double* qmax = ws_ptr<double>(P, L.qmax_part);
-  k_check_inputs<<<nq, kRedThreads, 0, s>>>(x, p, q, N, qmax, cnt);
-  FMM_LAUNCH_CHECK();
-  // pairwise momentum sums: three arrays of partials, reduced level by level
-  double* part = ws_ptr<double>(P, L.psum_part);
+  // pairwise momentum sums: per component two ping-pong arrays of partials
   const int64_t np0 = div_up(N, kRedChunk);
-  const double* res[3];
-  for (int k = 0; k < 3; ++k) {
-    double* a = part + (size_t)k * 2 * (np0 + 2);
-    double* b = a + (np0 + 2);
-    int64_t n = N;
-    const double* src = p + k;
-    int64_t stride = 3;
-    double* dst = a;
-    do {
-      int64_t nb = div_up(n, kRedChunk);
-      k_pairwise<<<(unsigned)nb, kRedThreads, 0, s>>>(src, n, stride, dst);
-      FMM_LAUNCH_CHECK();
-      n = nb;
-      src = dst;
-      stride = 1;
-      dst = (dst == a) ? b : a;
-    } while (n > 1);
-    res[k] = src;
+  const int64_t comp_step = 2 * (np0 + 2);
+  double* a = ws_ptr<double>(P, L.psum_part);
+  double* b = a + (np0 + 2);
+  double* qmax = ws_ptr<double>(P, L.qmax_part);
+  k_setup_first<<<dim3((unsigned)np0, 3), kRedThreads, 0, s>>>(x, p, q, N, a, comp_step, qmax, cnt);
+  FMM_LAUNCH_CHECK();
+  int64_t n = np0;
+  while (n > kRedChunk) {
+    const int64_t nb = div_up(n, kRedChunk);
+    k_pairwise<<<dim3((unsigned)nb, 3), kRedThreads, 0, s>>>(a, n, comp_step, b);
+    FMM_LAUNCH_CHECK();
+    std::swap(a, b);
+    n = nb;
   }
-  k_gbar<<<1, 32, 0, s>>>(res[0], res[1], res[2], N, qmax, nq, scal);
+  k_setup_final<<<1, kRedThreads, 0, s>>>(a, n, comp_step, N, qmax, np0, ws_ptr<double>(P, L.scal));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
