@@ -71,6 +71,12 @@ typedef enum fmm_flags {
                             lists; a failure returns FMM_EBOUNDS before any kernel
                             indexes through the bad value (costs one more wait)     */
   FMM_TIMING = 4u,       /* record CUDA events around each stage (fmm_plan_stats)    */
+  FMM_TEST_POLY_KERNEL = 16u, /* test mode, FP64 plans, forward only: the kernel is the
+                            polynomial g(R) = R (R_x^2 + R_y^2 + gbar^2 R_z^2 + 1),
+                            of degree 3 in each variable, so with n >= 3 every
+                            interpolation step is exact (Theorem 1, the lemma of
+                            Appendix A) and the FMM equals the direct sum of this g
+                            to rounding; E = k_e sum a_j g, B = k_e/c0 sum b_j x g */
   FMM_SIZE_AWARE = 8u    /* not in the paper: in the traversal (Alg. 17) an admissible
                             pair with |S_t||S_s| < m^2 particle pairs (m = (n+1)^3) is
                             evaluated directly, as P2P of all leaf pairs under it,

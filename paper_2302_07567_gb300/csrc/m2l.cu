@@ -15,10 +15,10 @@
 namespace fmm {
 namespace {
 
-template <typename T, int KPT>
+template <typename T, int KPT, bool POLY>
 __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
                                              int shift, const unsigned int* __restrict__ err, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
-                                             const void* __restrict__ pdc, Cheb ch, int m,
+                                             const void* __restrict__ pdc, Cheb ch, int m, const double* __restrict__ scal,
                                              const typename Vec4<T>::type* __restrict__ src, T* __restrict__ Lout) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ unsigned char smem_raw[];
@@ -76,8 +76,13 @@ __global__ void __launch_bounds__(256) k_m2l(const uint64_t* __restrict__ keys, 
         for (int k = 0; k < KPT; ++k) {
           const T rx = X[k][0] - ya.x, ry = X[k][1] - ya.y, rz = X[k][2] - ya.z;
           const T d = rx * rx + ry * ry + rz * rz;
-          const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
-          const T r3 = inv * inv * inv;
+          T r3;
+          if constexpr (POLY) {  // the polynomial test kernel R' (1 + l^2 |R'|^2)
+            r3 = T(1) + (T)(scal[2] * scal[2]) * d;
+          } else {
+            const T inv = d > tiny_sep2<T>() ? rsqrt_t<T>(d) : T(0);
+            r3 = inv * inv * inv;
+          }
           const T ar3 = ya.w * r3;
           part[k][0] += ar3 * rx;
           part[k][1] += ar3 * ry;
@@ -291,42 +296,43 @@ void pick_shape(int m, int* nt, int* kpt) {
   *kpt = best_k;
 }
 
-template <typename T, int KPT>
+template <typename T, int KPT, bool POLY>
 int launch(fmm_plan_s* P, int nt, cudaStream_t s) {
   const Layout& L = P->lay;
   const size_t smem = (size_t)2 * P->m * sizeof(typename Vec4<T>::type);
   static bool attr_set = false;
   if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l<T, KPT, POLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   unsigned grid = 0;
-  if (int rc = resident_blocks(k_m2l<T, KPT>, nt, smem, P->C, &grid)) return rc;
-  k_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
+  if (int rc = resident_blocks(k_m2l<T, KPT, POLY>, nt, smem, P->C, &grid)) return rc;
+  k_m2l<T, KPT, POLY><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),
                                         P->kappa + 1, &ws_ptr<Counters>(P, L.counters)->err,
                                         ws_ptr<int32_t>(P, L.m2l_order), P->C,
                                         ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_dc, P->cheb, P->m,
+                                        ws_ptr<double>(P, L.scal),
                                                   ws_ptr<typename Vec4<T>::type>(P, L.srct), ws_ptr<T>(P, L.local));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
 
-template <typename T>
+template <typename T, bool POLY>
 int m2l_t(fmm_plan_s* P, cudaStream_t s) {
   int nt, kpt;
   pick_shape(P->m, &nt, &kpt);
   switch (kpt) {
-    case 1: return launch<T, 1>(P, nt, s);
-    case 2: return launch<T, 2>(P, nt, s);
-    case 3: return launch<T, 3>(P, nt, s);
-    default: return launch<T, 4>(P, nt, s);
+    case 1: return launch<T, 1, POLY>(P, nt, s);
+    case 2: return launch<T, 2, POLY>(P, nt, s);
+    case 3: return launch<T, 3, POLY>(P, nt, s);
+    default: return launch<T, 4, POLY>(P, nt, s);
   }
 }
 
 }  // namespace
 
 int run_m2l(fmm_plan_s* P, cudaStream_t s) {
-  if (P->precision == FMM_FP32 && P->eta <= 0.5) {
+  if (P->precision == FMM_FP32 && P->eta <= 0.5 && !(P->flags & FMM_TEST_POLY_KERNEL)) {
     switch (P->np1) {
       case 3: return launch_fast<3, 3, 1>(P, s);
       case 5: return launch_fast<5, 5, 1>(P, s);
@@ -335,7 +341,8 @@ int run_m2l(fmm_plan_s* P, cudaStream_t s) {
       default: break;
     }
   }
-  return P->precision == FMM_FP32 ? m2l_t<float>(P, s) : m2l_t<double>(P, s);
+  if (P->flags & FMM_TEST_POLY_KERNEL) return m2l_t<double, true>(P, s);  // FP64 plans only
+  return P->precision == FMM_FP32 ? m2l_t<float, false>(P, s) : m2l_t<double, false>(P, s);
 }
 
 }  // namespace fmm

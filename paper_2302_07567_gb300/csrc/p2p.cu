@@ -38,7 +38,7 @@
 namespace fmm {
 namespace {
 
-template <typename T, int KPT>
+template <typename T, int KPT, bool POLY>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift, const unsigned int* __restrict__ err,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
               d = rx * rx + ry * ry + g2 * (rz * rz);
               inv = d > T(0) ? rsqrt_t<T>(d) : T(0);
             }
-            const T r3 = inv * inv * inv;
+            T r3;
+            if constexpr (POLY) r3 = T(1) + d;  // the polynomial test kernel R (1 + D), FP64 only
+            else r3 = inv * inv * inv;
             const T ar3 = u.w * r3;
             part[k][0] += ar3 * rx;
             part[k][1] += ar3 * ry;
@@ -184,7 +186,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
         for (int c = 0; c < 6; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
     }
     if constexpr (!kSplit) {  // physical near field -> stretched, scaled convention of the far field
-      const T fe[6] = {(T)ell2, (T)ell2, (T)(ell2 * gbar), (T)ell2, (T)ell2, (T)(ell2 / gbar)};
+      // normal kernel: l^2 S R / D^{3/2};  polynomial test kernel: S R (1 + D) / l
+      const double c = POLY ? scal[3] : ell2;
+      const T fe[6] = {(T)c, (T)c, (T)(c * gbar), (T)c, (T)c, (T)(c / gbar)};
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
   }
 }
 
-template <typename T, int KPT>
+template <typename T, int KPT, bool POLY>
 int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   const Layout& L = P->lay;
   int NT, groups, chunks;
@@ -272,10 +276,10 @@ int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   const size_t smem = stage + sizeof(T) * 6 * P->m;
   static bool attr_set = false;
   if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2p_l2p<T, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2p_l2p<T, KPT, POLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  k_p2p_l2p<T, KPT><<<(unsigned)(P->nleaves * chunks), nt, smem, s>>>(
+  k_p2p_l2p<T, KPT, POLY><<<(unsigned)(P->nleaves * chunks), nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1,
       &ws_ptr<Counters>(P, L.counters)->err, ws_ptr<int64_t>(P, L.nstart),
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
@@ -290,7 +294,9 @@ template <typename T>
 int p2p_t(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   // one target per thread (two per thread measured slower: the extra
   // registers cost more occupancy than the shared loads they save)
-  return launch<T, 1>(P, E, B, s);
+  if constexpr (sizeof(T) == 8)
+    if (P->flags & FMM_TEST_POLY_KERNEL) return launch<T, 1, true>(P, E, B, s);
+  return launch<T, 1, false>(P, E, B, s);
 }
 
 }  // namespace

@@ -213,7 +213,9 @@ int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, doubl
   if (leaf_size < 2 || leaf_size > 4096) return FMM_EINVAL;
   if (!(eta > 0.0) || !std::isfinite(eta)) return FMM_EINVAL;
   if (precision != FMM_FP32 && precision != FMM_FP64) return FMM_EINVAL;
-  if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE)) return FMM_EINVAL;
+  if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE | FMM_TEST_POLY_KERNEL))
+    return FMM_EINVAL;
+  if ((flags & FMM_TEST_POLY_KERNEL) && precision != FMM_FP64) return FMM_EINVAL;
   fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
   if (!P) return FMM_EINVAL;
   P->N = N;
@@ -347,6 +349,7 @@ int fmm_field_adjoint(fmm_plan_t P, const double* x, const double* p, const doub
   if (!P || !x || !p || !q || !wE || !wB || !dx || !dp || !dq) return FMM_EINVAL;
   if (!P->ws) return FMM_ENOWORKSPACE;
   if (!P->have_forward) return FMM_ESTATE;
+  if (P->flags & FMM_TEST_POLY_KERNEL) return FMM_EINVAL;  // the adjoint is of the physical kernel only
   return run_adjoint(P, x, p, q, wE, wB, dx, dp, dq, static_cast<cudaStream_t>(stream));
 }
 

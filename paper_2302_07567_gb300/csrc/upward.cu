@@ -13,7 +13,7 @@ namespace {
 // scal[2] = ell, scal[3] = 1/ell (powers of two near the root box's stretched
 // half-diagonal), scal[4] = (1/(4 pi eps0)) mu / ell^2, scal[5] = scal[4] / c0.
 __global__ void k_units(const double* __restrict__ nlo, const double* __restrict__ nhi,
-                        double* __restrict__ scal) {
+                        double* __restrict__ scal, bool poly) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double s[3] = {1.0, 1.0, scal[0]};
   double r2 = 0.0;
@@ -28,7 +28,9 @@ __global__ void k_units(const double* __restrict__ nlo, const double* __restrict
   scal[2] = ell;
   scal[3] = inv;
   const double ke = 1.0 / (4.0 * 3.14159265358979323846 * kEps0);
-  scal[4] = ke * scal[1] * inv * inv;
+  // internal kernel R'/|R'|^3 = l^2 S R / D^{3/2}, or for the polynomial test
+  // kernel R' (1 + l^2 |R'|^2) = S R (1 + D) / l, with S = diag(1, 1, gbar)
+  scal[4] = poly ? ke * scal[1] * ell : ke * scal[1] * inv * inv;
   scal[5] = scal[4] / kC0;
 }
 
@@ -250,7 +252,8 @@ int upward_t(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
 int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s) {
   const Layout& L = P->lay;
   double* scal = ws_ptr<double>(P, L.scal);
-  k_units<<<1, 32, 0, s>>>(ws_ptr<double>(P, L.nlo), ws_ptr<double>(P, L.nhi), scal);
+  k_units<<<1, 32, 0, s>>>(ws_ptr<double>(P, L.nlo), ws_ptr<double>(P, L.nhi), scal,
+                           (P->flags & FMM_TEST_POLY_KERNEL) != 0);
   FMM_LAUNCH_CHECK();
   k_node_geo<<<(unsigned)div_up(P->C, 128), 128, 0, s>>>(ws_ptr<double>(P, L.nlo), ws_ptr<double>(P, L.nhi),
                                                           P->C, scal, ws_ptr<double>(P, L.ncen),

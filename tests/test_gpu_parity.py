@@ -270,3 +270,30 @@ def test_size_aware_variant_matches_oracle(name):
     e_sa = metrics.field_error(E.cpu().numpy(), B.cpu().numpy(), Ed.numpy(), Bd.numpy())
     e_plain = metrics.field_error(Ep.numpy(), Bp.numpy(), Ed.numpy(), Bd.numpy())
     assert e_sa <= e_plain, (e_sa, e_plain)
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_polynomial_test_kernel_is_exact(n):
+    """FMM_TEST_POLY_KERNEL: g(R) = R (1 + R_x^2 + R_y^2 + gbar^2 R_z^2) has degree 3
+    in each variable, so for n >= 3 every interpolation step is exact (Theorem 1,
+    the lemma of Appendix A) and the FMM equals the direct sum of this g to
+    rounding, for any eta."""
+    x, p, q = random_beam(600, seed=7, gamma=4.0)
+    x = x * 1e3  # O(1) coordinates: both terms of 1 + D matter
+    plan = fmm.Plan(600, n, 16, 0.9, precision="fp64", flags=fmm.FMM_TEST_POLY_KERNEL)
+    E, B = plan.field(*dev(x, p, q))
+    st = plan.stats()
+    assert st["m2l_pairs"] > 20
+    gb = st["gbar"]
+    R = x[:, None, :] - x[None, :, :]
+    D = R[..., 0] ** 2 + R[..., 1] ** 2 + gb * gb * R[..., 2] ** 2
+    g = R * (1.0 + D)[..., None]
+    a = q * np.sqrt(1.0 + (p * p).sum(1))
+    b = q[:, None] * p
+    Ed = physics.KE * np.einsum("j,ijk->ik", a, g)
+    Bd = physics.KE / physics.C0 * np.cross(np.broadcast_to(b[None, :, :], g.shape), g).sum(1)
+    assert metrics.field_error(E.cpu().numpy(), B.cpu().numpy(), Ed, Bd) < 1e-10
+    with pytest.raises(fmm.FMMError):
+        fmm.Plan(600, n, 16, 0.9, precision="fp32", flags=fmm.FMM_TEST_POLY_KERNEL)
+    with pytest.raises(fmm.FMMError):
+        plan.adjoint(*dev(x, p, q), *dev(np.ones((600, 3)), np.ones((600, 3))))
