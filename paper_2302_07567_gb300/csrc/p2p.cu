@@ -49,7 +49,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     T* __restrict__ Bout) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;  // hi + lo separations
-  constexpr int kRow = kSplit ? 3 : 2;                      // V4 per staged source particle
+  constexpr int kRow = kSplit ? 4 : 2;                      // V4 per staged source particle
+  // FP32: sources are staged in pairs, 7 float4 (28 floats) per pair, each of
+  // 14 components as (source 2q, source 2q+1): -x_hi, -y_hi, -z_hi, a, b~x,
+  // b~y, b~z, -b~x, -b~y, -b~z, -x_lo, -y_lo, -z_lo, 0.  A thread evaluates
+  // both sources of a pair at once with paired FP32 arithmetic (__fadd2_rn,
+  // __fmul2_rn, __ffma2_rn: two lanes per instruction).
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);                                // [blockDim][kRow]
   if (*err) return;  // the traversal failed: the lists are incomplete
@@ -127,15 +132,29 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
         for (int c = 0; c < 6; ++c) part[k][c] = T(0);
+      float2 pp2[6];  // paired partial sums (FP32 path): even and odd sources of the leaf
+#pragma unroll
+      for (int c = 0; c < 6; ++c) pp2[c] = make_float2(0.f, 0.f);
       for (int64_t base = 0; base < scnt; base += blockDim.x) {
         __syncthreads();
         const int64_t j = base + threadIdx.x;
+        if constexpr (kSplit) {
+          float c[14];
+          if (j < scnt) {
+            const float4 u = px[sst + j], w = pb[sst + j], l = pl[sst + j];
+            c[0] = -u.x; c[1] = -u.y; c[2] = -u.z; c[3] = u.w;
+            c[4] = w.x; c[5] = w.y; c[6] = w.z; c[7] = -w.x; c[8] = -w.y; c[9] = -w.z;
+            c[10] = -l.x; c[11] = -l.y; c[12] = -l.z; c[13] = 0.f;
+          } else {  // partner of an odd last source: no mass, no field
+#pragma unroll
+            for (int q = 0; q < 14; ++q) c[q] = 0.f;
+          }
+          float* f = reinterpret_cast<float*>(sp) + (threadIdx.x >> 1) * 28 + (threadIdx.x & 1);
+#pragma unroll
+          for (int q = 0; q < 14; ++q) f[2 * q] = c[q];
+        }
         if (j < scnt) {
-          if constexpr (kSplit) {
-            sp[kRow * threadIdx.x] = px[sst + j];
-            sp[kRow * threadIdx.x + 1] = pb[sst + j];
-            reinterpret_cast<float4*>(sp)[kRow * threadIdx.x + 2] = pl[sst + j];
-          } else {  // absolute physical position with a', and b' = (b~x gbar, b~y gbar, b~z)
+          if constexpr (!kSplit) {  // absolute physical position with a', and b' = (b~x gbar, b~y gbar, b~z)
             const V4 a = reinterpret_cast<const V4*>(pl)[sst + j], u = px[sst + j], w = pb[sst + j];
             V4 r0, r1;
             r0.x = a.x; r0.y = a.y; r0.z = a.z; r0.w = u.w;
@@ -146,6 +165,37 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
         }
         __syncthreads();
         const int nj = (int)min64(blockDim.x, scnt - base);
+        if constexpr (kSplit && KPT == 1) {  // source pairs, paired arithmetic
+          const int npq = (nj + 1) >> 1;
+          const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
+          const float2 X0 = make_float2(X[0][0], X[0][0]), X1 = make_float2(X[0][1], X[0][1]),
+                       X2 = make_float2(X[0][2], X[0][2]);
+          const float2 L0 = make_float2(XL[0][0], XL[0][0]), L1 = make_float2(XL[0][1], XL[0][1]),
+                       L2 = make_float2(XL[0][2], XL[0][2]);
+          for (int q = grp * share2; q < q1; ++q) {
+            const float4* s4 = reinterpret_cast<const float4*>(sp) + 7 * q;
+            const float4 A = s4[0], Bq = s4[1], Cq = s4[2], Dq = s4[3], Eq = s4[4], Fq = s4[5], Gq = s4[6];
+            const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(A.x, A.y)), __fadd2_rn(L0, make_float2(Fq.x, Fq.y)));
+            const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(A.z, A.w)), __fadd2_rn(L1, make_float2(Fq.z, Fq.w)));
+            const float2 rz = __fadd2_rn(__fadd2_rn(X2, make_float2(Bq.x, Bq.y)), __fadd2_rn(L2, make_float2(Gq.x, Gq.y)));
+            const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+            float2 inv;
+            inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+            inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+            const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+            const float2 ar3 = __fmul2_rn(make_float2(Bq.z, Bq.w), r3);
+            pp2[0] = __ffma2_rn(ar3, rx, pp2[0]);
+            pp2[1] = __ffma2_rn(ar3, ry, pp2[1]);
+            pp2[2] = __ffma2_rn(ar3, rz, pp2[2]);
+            const float2 cx = __ffma2_rn(make_float2(Eq.z, Eq.w), ry, __fmul2_rn(make_float2(Cq.z, Cq.w), rz));
+            const float2 cy = __ffma2_rn(make_float2(Dq.z, Dq.w), rz, __fmul2_rn(make_float2(Dq.x, Dq.y), rx));
+            const float2 cz = __ffma2_rn(make_float2(Eq.x, Eq.y), rx, __fmul2_rn(make_float2(Cq.x, Cq.y), ry));
+            pp2[3] = __ffma2_rn(r3, cx, pp2[3]);
+            pp2[4] = __ffma2_rn(r3, cy, pp2[4]);
+            pp2[5] = __ffma2_rn(r3, cz, pp2[5]);
+          }
+          continue;
+        }
         const int share = (nj + groups - 1) / groups, j1 = min(nj, (grp + 1) * share);
         for (int jj = grp * share; jj < j1; ++jj) {
           const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
@@ -179,6 +229,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
             part[k][5] += r3 * (w.x * ry - w.y * rx);
           }
         }
+      }
+      if constexpr (kSplit && KPT == 1) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) part[0][c] = pp2[c].x + pp2[c].y;
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
@@ -270,7 +324,7 @@ int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   int NT, groups, chunks;
   particle_shape(P->leaf, KPT, &NT, &groups, &chunks);
   const int nt = groups * NT;
-  const int row = std::is_same<T, float>::value ? 3 : 2;
+  const int row = std::is_same<T, float>::value ? 4 : 2;
   const size_t stage = std::max(sizeof(typename Vec4<T>::type) * row * nt,
                                 sizeof(T) * (size_t)(groups - 1) * KPT * 12 * NT);
   const size_t smem = stage + sizeof(T) * 6 * P->m;
