@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
 // pushed-down Lambda, plus the target-side part; then the chain rule to
 // physical (x, p, q), written in input order.
 template <typename T, int KPT>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_source(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
@@ -725,10 +725,30 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_source(
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
         for (int c = 0; c < 7; ++c) part[k][c] = T(0);
+      float2 pp2[7];  // paired partial sums (FP32 path): even and odd targets of the leaf
+#pragma unroll
+      for (int c = 0; c < 7; ++c) pp2[c] = make_float2(0.f, 0.f);
       for (int64_t base = 0; base < tcnt; base += blockDim.x) {
         __syncthreads();
         const int64_t i = base + threadIdx.x;
-        if (i < tcnt) {
+        if constexpr (kSplit && KPT == 1) {
+          // targets staged in pairs, 8 float4 (32 floats) per pair, each of 16
+          // components as (target 2q, target 2q+1): x_hi, y_hi, z_hi, x_lo,
+          // y_lo, z_lo, wE^ (3), wB^ (3), -wB^ (3), 0
+          float c[16];
+          if (i < tcnt) {
+            const float4 u = px[tst + i], l = pl[tst + i], e = wle[tst + i], w = wlb[tst + i];
+            c[0] = u.x; c[1] = u.y; c[2] = u.z; c[3] = l.x; c[4] = l.y; c[5] = l.z;
+            c[6] = e.x; c[7] = e.y; c[8] = e.z; c[9] = w.x; c[10] = w.y; c[11] = w.z;
+            c[12] = -w.x; c[13] = -w.y; c[14] = -w.z; c[15] = 0.f;
+          } else {  // partner of an odd last target: no weights, no contribution
+#pragma unroll
+            for (int q = 0; q < 16; ++q) c[q] = 0.f;
+          }
+          float* f = reinterpret_cast<float*>(sp) + (threadIdx.x >> 1) * 32 + (threadIdx.x & 1);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) f[2 * q] = c[q];
+        } else if (i < tcnt) {
           sp[kRow * threadIdx.x] = px[tst + i];
           sp[kRow * threadIdx.x + 1] = wle[tst + i];
           sp[kRow * threadIdx.x + 2] = wlb[tst + i];
@@ -736,6 +756,54 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_source(
         }
         __syncthreads();
         const int ni = (int)min64(blockDim.x, tcnt - base);
+        if constexpr (kSplit && KPT == 1) {  // target pairs, paired arithmetic
+          const int npq = (ni + 1) >> 1;
+          const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
+          const float2 nX0 = make_float2(-X[0][0], -X[0][0]), nX1 = make_float2(-X[0][1], -X[0][1]),
+                       nX2 = make_float2(-X[0][2], -X[0][2]);
+          const float2 nL0 = make_float2(-XL[0][0], -XL[0][0]), nL1 = make_float2(-XL[0][1], -XL[0][1]),
+                       nL2 = make_float2(-XL[0][2], -XL[0][2]);
+          const float2 a2 = make_float2(aj[0], aj[0]);
+          const float2 b0 = make_float2(bj[0][0], bj[0][0]), b1 = make_float2(bj[0][1], bj[0][1]),
+                       b2 = make_float2(bj[0][2], bj[0][2]);
+          const float2 m3 = make_float2(-3.f, -3.f);
+          for (int qq = grp * share2; qq < q1; ++qq) {
+            const float4* s4 = reinterpret_cast<const float4*>(sp) + 8 * qq;
+            const float4 P0 = s4[0], P1 = s4[1], P2 = s4[2], P3 = s4[3], P4 = s4[4], P5 = s4[5], P6 = s4[6];
+            // R = x_i - x_j = (x_hi - X) + (x_lo - X_lo)
+            const float2 rx = __fadd2_rn(__fadd2_rn(make_float2(P0.x, P0.y), nX0), __fadd2_rn(make_float2(P1.z, P1.w), nL0));
+            const float2 ry = __fadd2_rn(__fadd2_rn(make_float2(P0.z, P0.w), nX1), __fadd2_rn(make_float2(P2.x, P2.y), nL1));
+            const float2 rz = __fadd2_rn(__fadd2_rn(make_float2(P1.x, P1.y), nX2), __fadd2_rn(make_float2(P2.z, P2.w), nL2));
+            const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+            float2 inv;
+            inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+            inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 r3 = __fmul2_rn(inv2, inv);
+            const float2 r5 = __fmul2_rn(r3, inv2);
+            const float2 kx = __fmul2_rn(r3, rx), ky = __fmul2_rn(r3, ry), kz = __fmul2_rn(r3, rz);
+            const float2 ex = make_float2(P3.x, P3.y), ey = make_float2(P3.z, P3.w), ez = make_float2(P4.x, P4.y);
+            const float2 wx = make_float2(P4.z, P4.w), wy = make_float2(P5.x, P5.y), wz = make_float2(P5.z, P5.w);
+            const float2 nwx = make_float2(P6.x, P6.y), nwy = make_float2(P6.z, P6.w);
+            const float4 P7 = s4[7];
+            const float2 nwz = make_float2(P7.x, P7.y);
+            // dL/da' += wE^ . K,  dL/db~' += K x wB^
+            pp2[0] = __ffma2_rn(ez, kz, __ffma2_rn(ey, ky, __ffma2_rn(ex, kx, pp2[0])));
+            pp2[1] = __ffma2_rn(kz, nwy, __ffma2_rn(ky, wz, pp2[1]));
+            pp2[2] = __ffma2_rn(kx, nwz, __ffma2_rn(kz, wx, pp2[2]));
+            pp2[3] = __ffma2_rn(ky, nwx, __ffma2_rn(kx, wy, pp2[3]));
+            // u = a'_j wE^ + wB^ x b~'_j;  sum of J u = r^-3 u - 3 r^-5 R (R . u), negated at the end
+            const float2 ux = __ffma2_rn(a2, ex, __ffma2_rn(nwz, b1, __fmul2_rn(wy, b2)));
+            const float2 uy = __ffma2_rn(a2, ey, __ffma2_rn(nwx, b2, __fmul2_rn(wz, b0)));
+            const float2 uz = __ffma2_rn(a2, ez, __ffma2_rn(nwy, b0, __fmul2_rn(wx, b1)));
+            const float2 ru = __ffma2_rn(rz, uz, __ffma2_rn(ry, uy, __fmul2_rn(rx, ux)));
+            const float2 nc3 = __fmul2_rn(__fmul2_rn(r5, m3), ru);
+            pp2[4] = __ffma2_rn(nc3, rx, __ffma2_rn(r3, ux, pp2[4]));
+            pp2[5] = __ffma2_rn(nc3, ry, __ffma2_rn(r3, uy, pp2[5]));
+            pp2[6] = __ffma2_rn(nc3, rz, __ffma2_rn(r3, uz, pp2[6]));
+          }
+          continue;
+        }
         const int share = (ni + groups - 1) / groups, i1 = min(ni, (grp + 1) * share);
         for (int ii = grp * share; ii < i1; ++ii) {
           const V4 u = sp[kRow * ii], we = sp[kRow * ii + 1], wb = sp[kRow * ii + 2];
@@ -771,6 +839,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_source(
             part[k][6] -= r3 * uz - c3 * rz;
           }
         }
+      }
+      if constexpr (kSplit && KPT == 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[0][c] = pp2[c].x + pp2[c].y;
+#pragma unroll
+        for (int c = 4; c < 7; ++c) part[0][c] = -(pp2[c].x + pp2[c].y);
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)

@@ -7,7 +7,8 @@
 //   - node tables: every node non-empty and inside [0, N); the two children
 //     of an inner node split its slot range (Alg. 2, Appendix B: first child
 //     ceil(|S|/2));
-//   - the leaf order is a permutation of 0 .. N-1;
+//   - the leaf order is a permutation of 0 .. N-1, and the M2L work order
+//     (target-major, or source-major in the adjoint) one of the nodes 1 .. C;
 //   - every list pair names nodes 1 .. C, P2P pairs name leaves (Algs. 11,
 //     17: only leaf-leaf pairs go to P2P), the keys are strictly increasing
 //     (sorted by (major, minor), no duplicate pair) and agree with the CSR
@@ -48,6 +49,16 @@ __global__ void k_check_perm_count(const int32_t* __restrict__ perm, int64_t N, 
 __global__ void k_check_perm_once(const uint32_t* __restrict__ seen, int64_t N, Counters* cnt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     if (seen[i] != 1u) bad(cnt);
+}
+
+// A work order: nodes 1 .. C, each exactly once, in C slots.
+__global__ void k_check_order_count(const int32_t* __restrict__ order, int64_t C, uint32_t* __restrict__ seen,
+                                    Counters* cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < C; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = order[k];
+    if (v < 1 || (int64_t)v > C) bad(cnt);
+    else atomicAdd(&seen[v - 1], 1u);
+  }
 }
 
 // One list: keys (major << shift | minor), CSR offsets by major [C + 2].
@@ -94,6 +105,15 @@ int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s) {
     k_check_perm_count<<<grid_for(P->N), 256, 0, s>>>(ws_ptr<int32_t>(P, L.perm), P->N, seen, cnt);
     FMM_LAUNCH_CHECK();
     k_check_perm_once<<<grid_for(P->N), 256, 0, s>>>(seen, P->N, cnt);
+    FMM_LAUNCH_CHECK();
+  }
+  {  // the M2L work order of this list direction is a permutation of the nodes
+    uint32_t* seen = ws_ptr<uint32_t>(P, L.rank);
+    FMM_CUDA_TRY(cudaMemsetAsync(seen, 0, sizeof(uint32_t) * P->C, s));
+    k_check_order_count<<<grid_for(P->C), 256, 0, s>>>(ws_ptr<int32_t>(P, source_major ? L.m2l_sorder : L.m2l_order),
+                                                        P->C, seen, cnt);
+    FMM_LAUNCH_CHECK();
+    k_check_perm_once<<<grid_for(P->C), 256, 0, s>>>(seen, P->C, cnt);
     FMM_LAUNCH_CHECK();
   }
   const size_t kp = source_major ? L.p2p_src : L.p2p, km = source_major ? L.m2l_src : L.m2l;

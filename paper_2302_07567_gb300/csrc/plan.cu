@@ -85,9 +85,9 @@ void make_layout(fmm_plan_s* P) {
   L.p2p_dc = take((size_t)P->cap_p2p * 32);
   L.m2l_dc = take((size_t)P->cap_m2l * 32);
   L.m2l_soff = take((C1 + 1) * 4);
-  // adjoint: the node weights W and adjoint moments Lambda reuse the local and
-  // multipole buffers; per particle it needs the scaled weights and the
-  // target-side position gradient, per source-major list pair a centre offset
+  // adjoint: per particle the scaled weights and the target-side position
+  // gradient, per source-major list pair a centre offset; the node weights W
+  // and adjoint moments Lambda have buffers of their own (wbuf, lbuf below)
   L.adj_part = take(N * V4);
   L.wle = take(N * V4);
   L.wlb = take(N * V4);
