@@ -457,7 +457,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
     int groups, int chunks, int64_t nitems, typename Vec4<T>::type* __restrict__ gout) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
-  constexpr int kRow = kSplit ? 3 : 2;
+  // FP32: sources staged in pairs, 7 float4 (28 floats) per pair, each of 14
+  // components as (source 2q, source 2q+1): -x_hi, -y_hi, -z_hi, a, b~x,
+  // b~y, b~z, -b~x, -b~y, -b~z, -x_lo, -y_lo, -z_lo, 0; a thread evaluates
+  // both sources of a pair at once with paired FP32 arithmetic
+  constexpr int kRow = kSplit ? 4 : 2;
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
@@ -538,16 +542,74 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
         for (int d = 0; d < 3; ++d) part[k][d] = T(0);
+      float2 pp2[3];  // paired partial sums (FP32 path): even and odd sources of the leaf
+#pragma unroll
+      for (int d = 0; d < 3; ++d) pp2[d] = make_float2(0.f, 0.f);
       for (int64_t base = 0; base < scnt; base += blockDim.x) {
         __syncthreads();
         const int64_t j = base + threadIdx.x;
-        if (j < scnt) {
+        if constexpr (kSplit && KPT == 1) {
+          float c[14];
+          if (j < scnt) {
+            const float4 u = px[sst + j], w = pb[sst + j], l = pl[sst + j];
+            c[0] = -u.x; c[1] = -u.y; c[2] = -u.z; c[3] = u.w;
+            c[4] = w.x; c[5] = w.y; c[6] = w.z; c[7] = -w.x; c[8] = -w.y; c[9] = -w.z;
+            c[10] = -l.x; c[11] = -l.y; c[12] = -l.z; c[13] = 0.f;
+          } else {  // partner of an odd last source: no mass, no contribution
+#pragma unroll
+            for (int q = 0; q < 14; ++q) c[q] = 0.f;
+          }
+          float* f = reinterpret_cast<float*>(sp) + (threadIdx.x >> 1) * 28 + (threadIdx.x & 1);
+#pragma unroll
+          for (int q = 0; q < 14; ++q) f[2 * q] = c[q];
+        } else if (j < scnt) {
           sp[kRow * threadIdx.x] = px[sst + j];
           sp[kRow * threadIdx.x + 1] = pb[sst + j];
           if constexpr (kSplit) sp[kRow * threadIdx.x + 2] = pl[sst + j];
         }
         __syncthreads();
         const int nj = (int)min64(blockDim.x, scnt - base);
+        if constexpr (kSplit && KPT == 1) {  // source pairs, paired arithmetic
+          const int npq = (nj + 1) >> 1;
+          const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
+          const float2 X0 = make_float2(X[0][0], X[0][0]), X1 = make_float2(X[0][1], X[0][1]),
+                       X2 = make_float2(X[0][2], X[0][2]);
+          const float2 L0 = make_float2(XL[0][0], XL[0][0]), L1 = make_float2(XL[0][1], XL[0][1]),
+                       L2 = make_float2(XL[0][2], XL[0][2]);
+          const float2 E0 = make_float2(we[0][0], we[0][0]), E1 = make_float2(we[0][1], we[0][1]),
+                       E2 = make_float2(we[0][2], we[0][2]);
+          const float2 B0 = make_float2(wb[0][0], wb[0][0]), B1 = make_float2(wb[0][1], wb[0][1]),
+                       B2 = make_float2(wb[0][2], wb[0][2]);
+          const float2 m3 = make_float2(-3.f, -3.f);
+          for (int qq = grp * share2; qq < q1; ++qq) {
+            const float4* s4 = reinterpret_cast<const float4*>(sp) + 7 * qq;
+            const float4 A = s4[0], Bq = s4[1], Cq = s4[2], Dq = s4[3], Eq = s4[4], Fq = s4[5], Gq = s4[6];
+            // R = x_i - x_j = (X_hi - x_hi) + (X_lo - x_lo)
+            const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(A.x, A.y)), __fadd2_rn(L0, make_float2(Fq.x, Fq.y)));
+            const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(A.z, A.w)), __fadd2_rn(L1, make_float2(Fq.z, Fq.w)));
+            const float2 rz = __fadd2_rn(__fadd2_rn(X2, make_float2(Bq.x, Bq.y)), __fadd2_rn(L2, make_float2(Gq.x, Gq.y)));
+            const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+            float2 inv;
+            inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+            inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 r3 = __fmul2_rn(inv2, inv);
+            const float2 r5 = __fmul2_rn(r3, inv2);
+            const float2 aa = make_float2(Bq.z, Bq.w);
+            const float2 bx = make_float2(Cq.x, Cq.y), by = make_float2(Cq.z, Cq.w), bz = make_float2(Dq.x, Dq.y);
+            const float2 nbx = make_float2(Dq.z, Dq.w), nby = make_float2(Eq.x, Eq.y), nbz = make_float2(Eq.z, Eq.w);
+            // u = a'_j wE^_i + wB^_i x b~'_j
+            const float2 ux = __ffma2_rn(aa, E0, __ffma2_rn(B1, bz, __fmul2_rn(B2, nby)));
+            const float2 uy = __ffma2_rn(aa, E1, __ffma2_rn(B2, bx, __fmul2_rn(B0, nbz)));
+            const float2 uz = __ffma2_rn(aa, E2, __ffma2_rn(B0, by, __fmul2_rn(B1, nbx)));
+            const float2 ru = __ffma2_rn(rz, uz, __ffma2_rn(ry, uy, __fmul2_rn(rx, ux)));
+            const float2 nc3 = __fmul2_rn(__fmul2_rn(r5, m3), ru);
+            pp2[0] = __ffma2_rn(nc3, rx, __ffma2_rn(r3, ux, pp2[0]));
+            pp2[1] = __ffma2_rn(nc3, ry, __ffma2_rn(r3, uy, pp2[1]));
+            pp2[2] = __ffma2_rn(nc3, rz, __ffma2_rn(r3, uz, pp2[2]));
+          }
+          continue;
+        }
         const int share = (nj + groups - 1) / groups, j1 = min(nj, (grp + 1) * share);
         for (int jj = grp * share; jj < j1; ++jj) {
           const V4 u = sp[kRow * jj], w = sp[kRow * jj + 1];
@@ -579,6 +641,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
             part[k][2] += r3 * uz - c3 * rz;
           }
         }
+      }
+      if constexpr (kSplit && KPT == 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) part[0][d] = pp2[d].x + pp2[d].y;
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
@@ -1026,7 +1092,7 @@ int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, d
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
   if (target_side) {
-    const size_t smem = stage_bytes<T>(kSplit ? 3 : 2, 1, 6, groups, NT) + sizeof(T) * 6 * P->m;
+    const size_t smem = stage_bytes<T>(kSplit ? 4 : 2, 1, 6, groups, NT) + sizeof(T) * 6 * P->m;
     static bool attr = false;
     if (!attr) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr = true; }
     // beside the source side's far field (side stream) the target side keeps
