@@ -11,13 +11,22 @@ The paper has no adjoint.  Two references are kept:
   with gbar held fixed, obtained the same way; the FMM gradient approaches
   it as the interpolation error vanishes.
 Both are checked against central finite differences in the test-suite.
+
+With ``gbar_term=True`` gbar is no longer a constant: it is the function
+gbar(p) = sqrt(1 + pbar.pbar), pbar = (1/N) sum_j p_j, of Section 3 (below
+Eq. 3.2), and dL/dp gains dL/dgbar * pbar / (N gbar) for every particle.
+The tree, its boxes and the lists stay fixed (they depend on gbar only
+through discrete decisions), so gbar enters the FMM only through the kernel
+g of Eq. 3.2 in P2P and M2L: the interpolation points are fixed points of
+the physical boxes.  The value used is the plan's gbar; only its derivative
+is live.
 """
 from __future__ import annotations
 
 import torch
 
 from . import bldtt
-from .physics import as_t, direct_fields, gamma_bar
+from .physics import as_t, direct_fields, gamma_bar, kernel_g
 
 
 def _grad(fn, x, p, q, wE, wB):
@@ -30,16 +39,44 @@ def _grad(fn, x, p, q, wE, wB):
     return float(L.detach()), gx.detach(), gp.detach(), gq.detach()
 
 
-def fmm_gradient(x, p, q, wE, wB, plan: bldtt.Plan):
-    """(L, dL/dx, dL/dp, dL/dq) of the FMM with ``plan`` fixed."""
-    return _grad(lambda a, b, c: bldtt.fmm_fields(a, b, c, plan.n, plan.tree.N0, plan.eta, plan=plan),
-                 x, p, q, wE, wB)
+def live_gbar(p: torch.Tensor, value: float) -> torch.Tensor:
+    """gbar(p) = sqrt(1 + pbar.pbar), pbar = (1/N) sum_j p_j (Section 3), for
+    autograd: the returned scalar equals ``value`` exactly and carries the
+    derivative d gbar / d p_i = pbar / (N gbar)."""
+    pbar = p.mean(dim=0)
+    g = torch.sqrt(1.0 + (pbar * pbar).sum())
+    return value + (g - g.detach())
 
 
-def direct_gradient(x, p, q, wE, wB, gbar: float | None = None):
-    """(L, dL/dx, dL/dp, dL/dq) of the direct sum with gbar fixed."""
+def fmm_gradient(x, p, q, wE, wB, plan: bldtt.Plan, gbar_term: bool = False):
+    """(L, dL/dx, dL/dp, dL/dq) of the FMM with ``plan`` fixed; with
+    ``gbar_term`` gbar follows p (the plan's tree, boxes and lists stay)."""
+    def fn(a, b, c):
+        if not gbar_term:
+            return bldtt.fmm_fields(a, b, c, plan.n, plan.tree.N0, plan.eta, plan=plan)
+        g = live_gbar(b, plan.tree.gbar)
+        return bldtt.fmm_fields(a, b, c, plan.n, plan.tree.N0, plan.eta, plan=plan,
+                                kernel=lambda R, _fixed: kernel_g(R, g))
+    return _grad(fn, x, p, q, wE, wB)
+
+
+def fmm_dloss_dgbar(x, p, q, wE, wB, plan: bldtt.Plan) -> float:
+    """dL/dgbar of the FMM with the plan and x, p, q fixed: gbar as a leaf."""
+    g = torch.tensor(float(plan.tree.gbar), dtype=torch.float64, requires_grad=True)
+    E, B = bldtt.fmm_fields(x, p, q, plan.n, plan.tree.N0, plan.eta, plan=plan,
+                            kernel=lambda R, _fixed: kernel_g(R, g))
+    L = (E * as_t(wE)).sum() + (B * as_t(wB)).sum()
+    (d,) = torch.autograd.grad(L, (g,))
+    return float(d)
+
+
+def direct_gradient(x, p, q, wE, wB, gbar: float | None = None, gbar_term: bool = False):
+    """(L, dL/dx, dL/dp, dL/dq) of the direct sum with gbar fixed, or with
+    ``gbar_term`` gbar following p (value ``gbar``, default gbar(p))."""
     if gbar is None:
         gbar = gamma_bar(as_t(p).numpy())
+    if gbar_term:
+        return _grad(lambda a, b, c: direct_fields(a, b, c, gbar=live_gbar(b, gbar)), x, p, q, wE, wB)
     return _grad(lambda a, b, c: direct_fields(a, b, c, gbar=gbar), x, p, q, wE, wB)
 
 

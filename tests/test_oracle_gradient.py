@@ -75,3 +75,62 @@ def test_sampled_direct_gradient_matches_full_autograd():
     np.testing.assert_allclose(sx.numpy(), gx.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gx.abs().max()))
     np.testing.assert_allclose(sp.numpy(), gp.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gp.abs().max()))
     np.testing.assert_allclose(sq.numpy(), gq.numpy()[idx], rtol=1e-10, atol=1e-12 * float(gq.abs().max()))
+
+
+@pytest.mark.parametrize("which", ["fmm", "direct"])
+def test_gbar_term_matches_central_differences(which):
+    """gbar as the function of p of Section 3 (below Eq. 3.2): dL/dp against
+    central differences of the loss whose gbar is recomputed from the
+    perturbed momenta (tree, boxes and lists of the FMM plan held fixed)."""
+    N = 96 if which == "fmm" else 24
+    x, p, q = random_beam(N, seed=21, gamma=4.0, spread=0.1, angle=0.2)
+    wE, wB = make_weights(N)
+    plan = bldtt.build_plan(x, p, 4, 8, 0.6)
+    assert len(plan.m2l) > 0
+    if which == "fmm":
+        _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan, gbar_term=True)
+        _, fx, fp, fq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+
+        def loss(pp):
+            g = physics.gamma_bar(pp)
+            E, B = bldtt.fmm_fields(x, pp, q, 4, 8, 0.6, plan=plan, kernel=lambda R, _f: physics.kernel_g(R, g))
+            return gradient.loss_value(E, B, wE, wB)
+    else:
+        _, gx, gp, gq = gradient.direct_gradient(x, p, q, wE, wB, gbar_term=True)
+        _, fx, fp, fq = gradient.direct_gradient(x, p, q, wE, wB)
+
+        def loss(pp):
+            E, B = physics.direct_fields(x, pp, q)  # gbar from pp
+            return gradient.loss_value(E, B, wE, wB)
+
+    rng = np.random.default_rng(1)
+    worst_live, worst_frozen = 0.0, 0.0
+    for _ in range(8):
+        j, k = int(rng.integers(N)), int(rng.integers(3))
+        h = 1e-5 * max(abs(p[j, k]), 1e-2)
+        fd = _fd(loss, p, (j, k), h)
+        tol = 2e-5 * abs(fd) + 2e-8 * float(gp.abs().max())
+        worst_live = max(worst_live, abs(fd - float(gp[j, k])) / tol)
+        worst_frozen = max(worst_frozen, abs(fd - float(fp[j, k])) / tol)
+    assert worst_live <= 1.0, worst_live
+    assert worst_frozen > 10.0, worst_frozen  # the gbar term is not negligible here
+
+
+def test_gbar_term_adds_one_common_vector_to_dp():
+    """dL/dp with gbar live minus dL/dp with gbar fixed is, for every particle,
+    dL/dgbar * pbar / (N gbar) (chain rule through gbar = sqrt(1 + pbar.pbar));
+    dL/dx and dL/dq do not change.  dL/dgbar is taken here by differentiating
+    the FMM with respect to gbar alone."""
+    N = 128
+    x, p, q = random_beam(N, seed=22, gamma=6.0, spread=0.05, angle=0.1)
+    wE, wB = make_weights(N)
+    plan = bldtt.build_plan(x, p, 3, 16, 0.5)
+    _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan, gbar_term=True)
+    _, fx, fp, fq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+    assert torch.equal(gx, fx) and torch.equal(gq, fq)
+    dLdg = gradient.fmm_dloss_dgbar(x, p, q, wE, wB, plan)
+    pbar = physics.mean_momentum(p)
+    want = dLdg * pbar / (N * plan.tree.gbar)
+    diff = (gp - fp).numpy()
+    np.testing.assert_allclose(diff, np.broadcast_to(want, diff.shape), rtol=1e-9, atol=1e-12 * abs(want).max())
+    assert abs(want).max() > 1e-6 * float(fp.abs().max())
