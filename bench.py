@@ -70,6 +70,8 @@ def parse():
                     help="the paper's uniform-cube experiments (Figs. 2, 3, Section 11) instead of the bench line")
     ap.add_argument("--size-aware", action="store_true",
                     help="admissible pairs with fewer particle pairs than proxy-point pairs go to P2P (not in the paper)")
+    ap.add_argument("--gbar-term", action="store_true",
+                    help="adjoint with gbar as a function of p (FMM_GBAR_TERM): dL/dp includes dL/dgbar dgbar/dp")
     ap.add_argument("--profile", action="store_true",
                     help="run only the warm-up and the timed steps, print nothing (for profiler captures)")
     return ap.parse_args()
@@ -164,7 +166,8 @@ def run_ours(args, rank, world, local):
     WE, WB = torch.as_tensor(wE, device=dev, dtype=out_dt), torch.as_tensor(wB, device=dev, dtype=out_dt)
     adj = args.passes == "fwd+adj"
     sa_flag = fmm.FMM_SIZE_AWARE if args.size_aware else 0
-    plan = fmm.Plan(N, w.n, w.leaf, w.eta, precision=args.precision, flags=fmm.FMM_TIMING | sa_flag)
+    gb_flag = fmm.FMM_GBAR_TERM if args.gbar_term else 0
+    plan = fmm.Plan(N, w.n, w.leaf, w.eta, precision=args.precision, flags=fmm.FMM_TIMING | sa_flag | gb_flag)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -274,7 +277,7 @@ def run_ours(args, rank, world, local):
             continue
         flop = per * st0[unit]
         traffic = (TRAFFIC_CYL64K.get(k) if args.workload == "cylinder64k" and args.precision == "fp32" and not args.size_aware
-                   and args.passes == "fwd+adj" else None)
+                   and not args.gbar_term and args.passes == "fwd+adj" else None)
         kernels[k] = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
                       "frac": (flop / (ms / 1e3) / 1e12 / peak) if peak else None, "traffic": traffic}
     # the adjoint runs its target side and M2L^T on two streams at once: their
@@ -301,6 +304,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "N": N, "degree": w.n, "leaf": w.leaf, "eta": w.eta,
                        "passes": args.passes, "precision": args.precision, "replicas": world,
                        "lists": "size-aware (M2L -> P2P below m^2 pairs)" if args.size_aware else "paper (Alg. 17)",
+                       "adjoint_gbar": "gbar(p) live" if args.gbar_term else "gbar held fixed",
                        "l2": "flushed before every timed step (512 MiB write)", "note": w.note},
             "rel_l2_error_vs_fp64_direct": err, "error_targets": 4096,
             "stage_ms": {k: round(v, 4) for k, v in st0["stage_ms"].items() if v},

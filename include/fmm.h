@@ -77,11 +77,21 @@ typedef enum fmm_flags {
                             interpolation step is exact (Theorem 1, the lemma of
                             Appendix A) and the FMM equals the direct sum of this g
                             to rounding; E = k_e sum a_j g, B = k_e/c0 sum b_j x g */
-  FMM_SIZE_AWARE = 8u    /* not in the paper: in the traversal (Alg. 17) an admissible
+  FMM_SIZE_AWARE = 8u,   /* not in the paper: in the traversal (Alg. 17) an admissible
                             pair with |S_t||S_s| < m^2 particle pairs (m = (n+1)^3) is
                             evaluated directly, as P2P of all leaf pairs under it,
                             instead of by M2L: fewer operations and no truncation
                             error for that pair                                     */
+  FMM_GBAR_TERM = 32u    /* adjoint only (not in the paper): gbar is the function
+                            sqrt(1 + pbar.pbar), pbar = (1/N) sum_j p_j, of Section 3
+                            instead of a constant, so dL/dp gains
+                            dL/dgbar * pbar / (N gbar) for every particle.  The tree,
+                            its boxes and the lists stay fixed (gbar moves them only
+                            through discrete decisions); gbar enters the FMM through
+                            the kernel g of Eq. 3.2 alone, and dL/dgbar is the sum,
+                            over the same P2P and M2L pairs, of the loss contracted
+                            with dg/dgbar = -3 gbar R_z^2 R / (R_x^2 + R_y^2 +
+                            gbar^2 R_z^2)^(5/2).  M2L^T then runs its generic kernel. */
 } fmm_flags;
 
 typedef struct fmm_plan_s* fmm_plan_t;
@@ -124,7 +134,7 @@ int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q
  * loss L = sum_i wE_i . E_i + wB_i . B_i it returns dL/dx [N,3], dL/dp [N,3]
  * and dL/dq [N] (device float64), the exact derivative of the FMM operator
  * with the tree, its boxes, the interaction lists and gbar held fixed at the
- * values of the last fmm_field call.  wE, wB: device [N,3] of the plan's
+ * values of the last fmm_field call (with FMM_GBAR_TERM, gbar follows p).  wE, wB: device [N,3] of the plan's
  * output type.  x, p, q must be the arrays of the last fmm_field call, still
  * unchanged.  Returns FMM_ESTATE if no successful fmm_field preceded it.
  * The source side's far field runs on a second stream the plan owns, beside

@@ -150,14 +150,22 @@ __global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __re
 // M2L^T: for source cluster s, Lambda[s][nu] = sum over target clusters S of
 // the source-major M2L list and their points mu of (W^E_{S,mu} . K(R),
 // K(R) x W^B_{S,mu}) with R = xi_{S,mu} - xi_{s,nu}.
-template <typename T, int KPT>
+// With GB it also forms the far-field part of gbar dL/dgbar for the cluster,
+// sum over nu and the pairs of -3 R_z^2 r^-5 (R . u), u = a_nu W^E + W^B x b_nu:
+// Gamma[nu] = sum R_z^2 r^-5 (R . W^E, R x W^B) is contracted with the
+// cluster's multipoles (a, b~)_nu and summed over nu in a fixed order into
+// gfar[s].
+template <typename T, int KPT, bool GB>
 __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
                                                  int shift, const int32_t* __restrict__ order, int64_t nitems, const NodeGeo* __restrict__ geo,
                                                  const void* __restrict__ sdc, Cheb ch, int m,
-                                                 const T* __restrict__ W, T* __restrict__ Lam) {
+                                                 const T* __restrict__ W, T* __restrict__ Lam,
+                                                 const T* __restrict__ Mp, double* __restrict__ gfar) {
   using V4 = typename Vec4<T>::type;
+  constexpr int NC = GB ? 8 : 4;  // Lambda (4) and Gamma (4)
   extern __shared__ unsigned char smem_raw[];
   V4* sm = reinterpret_cast<V4*>(smem_raw);  // [m][3]
+  __shared__ double gred[32];
   for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {  // sources, longest list first
   const int64_t s = order[w];
   const int np1 = ch.np1;
@@ -165,10 +173,11 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
   const int b = off[s], e = off[s + 1];
   const NodeGeo gs = geo[s];
   const int per_pass = KPT * blockDim.x;
+  double gsum = 0.0;  // this thread's points: far-field gbar term of the cluster
   for (int pass0 = 0; pass0 < m; pass0 += per_pass) {
     T xh[KPT][3];
     bool valid[KPT];
-    T acc[KPT][4], cmp[KPT][4];
+    T acc[KPT][NC], cmp[KPT][NC];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       const int nu = pass0 + threadIdx.x + k * blockDim.x;
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
       xh[k][1] = (T)(gs.h[1] * ch.t[(nn / np1) % np1]);
       xh[k][2] = (T)(gs.h[2] * ch.t[nn / (np1 * np1)]);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[k][c] = cmp[k][c] = T(0);
+      for (int c = 0; c < NC; ++c) acc[k][c] = cmp[k][c] = T(0);
     }
     for (int it = b; it < e; ++it) {
       const int64_t S = (int64_t)(keys[it] & mask);
@@ -206,14 +215,14 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
         sm[3 * o + 2] = r2;
       }
       __syncthreads();
-      T Z[KPT][3], part[KPT][4];
+      T Z[KPT][3], part[KPT][NC];
 #pragma unroll
       for (int k = 0; k < KPT; ++k) {
         Z[k][0] = xh[k][0] + dc0;
         Z[k][1] = xh[k][1] + dc1;
         Z[k][2] = xh[k][2] + dc2;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) part[k][c] = T(0);
+        for (int c = 0; c < NC; ++c) part[k][c] = T(0);
       }
       for (int mu = 0; mu < m; ++mu) {
         const V4 r0 = sm[3 * mu], r1 = sm[3 * mu + 1], r2 = sm[3 * mu + 2];
@@ -228,12 +237,19 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
           part[k][1] += r3 * (ry * r2.x - rz * r1.w);
           part[k][2] += r3 * (rz * r1.z - rx * r2.x);
           part[k][3] += r3 * (rx * r1.w - ry * r1.z);
+          if constexpr (GB) {
+            const T z2r5 = rz * rz * (r3 * inv * inv);
+            part[k][4] += z2r5 * (rx * r0.w + ry * r1.x + rz * r1.y);
+            part[k][5] += z2r5 * (ry * r2.x - rz * r1.w);
+            part[k][6] += z2r5 * (rz * r1.z - rx * r2.x);
+            part[k][7] += z2r5 * (rx * r1.w - ry * r1.z);
+          }
         }
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
+        for (int c = 0; c < NC; ++c) kahan_add(acc[k][c], cmp[k][c], part[k][c]);
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
@@ -241,6 +257,24 @@ __global__ void __launch_bounds__(256) k_adj_m2l(const uint64_t* __restrict__ ke
       if (!valid[k]) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = acc[k][c];
+      if constexpr (GB) {
+        double f = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f += (double)Mp[((size_t)s * 4 + c) * m + nu] * (double)acc[k][4 + c];
+        gsum += -3.0 * f;
+      }
+    }
+  }
+  if constexpr (GB) {  // fixed-order block sum: lanes by butterfly, warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+    __syncthreads();  // gred of the previous cluster is read
+    if ((threadIdx.x & 31) == 0) gred[threadIdx.x >> 5] = gsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += gred[w2];
+      gfar[s] = t;
     }
   }
   }  // work items
@@ -445,8 +479,11 @@ __device__ __forceinline__ void combine_groups(T (&acc)[KPT][NC], T (&cmp)[KPT][
 
 // Near field at the targets (J u over the target-major P2P list) plus the far
 // field at the targets (grad of the forward's cumulative local); writes the
-// target-side dL/dx' of every particle (leaf order).
-template <typename T, int KPT>
+// target-side dL/dx' of every particle (leaf order).  With GB it also sums,
+// per target, the near-field part of gbar dL/dgbar: in internal units
+// dg/dgbar = -(3/gbar) R_z^2 R / |R|^5, so the pair term is
+// -3 R_z^2 r^-5 (R . u), stored in the .w component of the output.
+template <typename T, int KPT, bool GB>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
@@ -465,7 +502,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
   extern __shared__ unsigned char smem_raw[];
   V4* sp = reinterpret_cast<V4*>(smem_raw);
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
-  T* sl = reinterpret_cast<T*>(smem_raw + stage_bytes<T>(kRow, KPT, 6, groups, NT));  // [6][m]
+  constexpr int NC = GB ? 4 : 3;  // dL/dx' (3) and the gbar term
+  T* sl = reinterpret_cast<T*>(smem_raw + stage_bytes<T>(kRow, KPT, 2 * NC, groups, NT));  // [6][m]
   const int64_t per_pass = (int64_t)KPT * NT;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
   __syncthreads();  // the previous item's readers of sl are done
@@ -490,7 +528,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
   for (int64_t pass0 = c0; pass0 < cnt; pass0 += per_pass) {
     T ri[KPT][3], rl[KPT][3], we[KPT][3], wb[KPT][3];
     bool valid[KPT];
-    T acc[KPT][3], cmp[KPT][3];
+    T acc[KPT][NC], cmp[KPT][NC];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       const int64_t j = pass0 + lt + (int64_t)k * NT;
@@ -507,12 +545,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
       we[k][0] = a.x; we[k][1] = a.y; we[k][2] = a.z;
       wb[k][0] = c.x; wb[k][1] = c.y; wb[k][2] = c.z;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) acc[k][d] = cmp[k][d] = T(0);
+      for (int d = 0; d < NC; ++d) acc[k][d] = cmp[k][d] = T(0);
     }
     for (int it = b; it < e; ++it) {
       const int64_t s = (int64_t)(keys[it] & mask);
       const int64_t sst = nstart[s], scnt = ncount[s];
-      T X[KPT][3], XL[KPT][3], part[KPT][3];
+      T X[KPT][3], XL[KPT][3], part[KPT][NC];
       if constexpr (kSplit) {
         const float4* pdc = static_cast<const float4*>(pdc_raw);
         const float4 dh = pdc[2 * it], dl = pdc[2 * it + 1];
@@ -541,10 +579,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) part[k][d] = T(0);
-      float2 pp2[3];  // paired partial sums (FP32 path): even and odd sources of the leaf
+        for (int d = 0; d < NC; ++d) part[k][d] = T(0);
+      float2 pp2[NC];  // paired partial sums (FP32 path): even and odd sources of the leaf
 #pragma unroll
-      for (int d = 0; d < 3; ++d) pp2[d] = make_float2(0.f, 0.f);
+      for (int d = 0; d < NC; ++d) pp2[d] = make_float2(0.f, 0.f);
       for (int64_t base = 0; base < scnt; base += blockDim.x) {
         __syncthreads();
         const int64_t j = base + threadIdx.x;
@@ -607,6 +645,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
             pp2[0] = __ffma2_rn(nc3, rx, __ffma2_rn(r3, ux, pp2[0]));
             pp2[1] = __ffma2_rn(nc3, ry, __ffma2_rn(r3, uy, pp2[1]));
             pp2[2] = __ffma2_rn(nc3, rz, __ffma2_rn(r3, uz, pp2[2]));
+            if constexpr (GB) pp2[NC - 1] = __ffma2_rn(__fmul2_rn(rz, rz), nc3, pp2[NC - 1]);
           }
           continue;
         }
@@ -639,17 +678,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
             part[k][0] += r3 * ux - c3 * rx;
             part[k][1] += r3 * uy - c3 * ry;
             part[k][2] += r3 * uz - c3 * rz;
+            if constexpr (GB) part[k][NC - 1] -= rz * rz * c3;
           }
         }
       }
       if constexpr (kSplit && KPT == 1) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) part[0][d] = pp2[d].x + pp2[d].y;
+        for (int d = 0; d < NC; ++d) part[0][d] = pp2[d].x + pp2[d].y;
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], part[k][d]);
+        for (int d = 0; d < NC; ++d) kahan_add(acc[k][d], cmp[k][d], part[k][d]);
     }
     __syncthreads();
     const int a3share = (np1 + groups - 1) / groups;
@@ -682,13 +722,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
         for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], G[d] * invh[d]);
       }
     }
-    combine_groups<T, KPT, 3>(acc, cmp, reinterpret_cast<T*>(smem_raw), groups, grp, NT, lt);
+    combine_groups<T, KPT, NC>(acc, cmp, reinterpret_cast<T*>(smem_raw), groups, grp, NT, lt);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       if (grp != 0 || !valid[k]) continue;
       const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       V4 o;
-      o.x = acc[k][0]; o.y = acc[k][1]; o.z = acc[k][2]; o.w = T(0);
+      o.x = acc[k][0]; o.y = acc[k][1]; o.z = acc[k][2]; o.w = GB ? acc[k][NC - 1] : T(0);
       gout[pos] = o;
     }
   }
@@ -708,7 +748,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lam, Cheb ch, ChebD cd, int m,
     const typename Vec4<T>::type* __restrict__ gtarget, const int32_t* __restrict__ perm,
     const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q, int groups,
-    int chunks, double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
+    int chunks, int gbar_term, double* __restrict__ dx_out, double* __restrict__ dp_out,
+    double* __restrict__ dq_out) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 4 : 3;
@@ -977,14 +1018,60 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
       // a = q gamma, b = q p:  dL/dq = gamma dL/da + p . dL/db,
       //                        dL/dp = q (p/gamma) dL/da + q dL/db
       dq_out[i] = gam * dA + (p0 * dB[0] + p1 * dB[1] + p2 * dB[2]);
-      dp_out[3 * i + 0] = qi * (p0 / gam) * dA + qi * dB[0];
-      dp_out[3 * i + 1] = qi * (p1 / gam) * dA + qi * dB[1];
-      dp_out[3 * i + 2] = qi * (p2 / gam) * dA + qi * dB[2];
+      // with gbar(p) live: + dL/dgbar * d gbar/d p_i = scal[10] * pbar
+      const double cg = gbar_term ? scal[10] : 0.0;
+      dp_out[3 * i + 0] = qi * (p0 / gam) * dA + qi * dB[0] + cg * scal[6];
+      dp_out[3 * i + 1] = qi * (p1 / gam) * dA + qi * dB[1] + cg * scal[7];
+      dp_out[3 * i + 2] = qi * (p2 / gam) * dA + qi * dB[2] + cg * scal[8];
       dx_out[3 * i + 0] = dX[0];
       dx_out[3 * i + 1] = dX[1];
       dx_out[3 * i + 2] = dX[2];
     }
   }
+}
+
+// dL/dgbar from the per-target near-field terms (.w of the target-side
+// output, leaf order) and the per-cluster far-field terms gfar[1 .. nfar],
+// in two fixed-order passes: block b sums its strided share into
+// gpart[b], then one block sums gpart[0 .. nb) and sets
+//   scal[9]  = dL/dgbar = (sum of the terms) / gbar,
+//   scal[10] = dL/dgbar / (N gbar),
+// the factor of pbar in d gbar / d p_i for gbar = sqrt(1 + pbar.pbar),
+// pbar = (1/N) sum_j p_j (Section 3).
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gbar_part(const typename Vec4<T>::type* __restrict__ tpart, int64_t N,
+                                                   const double* __restrict__ gfar, int64_t nfar,
+                                                   double* __restrict__ gpart) {
+  __shared__ double red[8];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) v += (double)tpart[i].w;
+  for (int64_t c = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nfar; c += stride) v += gfar[c];
+  const double t = block_sum_fixed(v, red);
+  if (threadIdx.x == 0) gpart[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) k_gbar_final(const double* __restrict__ gpart, int nb, int64_t N,
+                                                    double* __restrict__ scal) {
+  __shared__ double red[8];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += gpart[b];
+  const double t = block_sum_fixed(v, red);
+  if (threadIdx.x != 0) return;
+  const double gbar = scal[0], d = t / gbar;
+  scal[9] = d;
+  scal[10] = d / ((double)N * gbar);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1027,36 +1114,27 @@ int l2pt(fmm_plan_s* P, cudaStream_t s) {
   }
 }
 
-template <typename T, int KPT>
+template <typename T, int KPT, bool GB>
 int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
   const Layout& L = P->lay;
   static bool attr = false;
   if (!attr) {
-    if (int rc = set_smem(k_adj_m2l<T, KPT>)) return rc;
+    if (int rc = set_smem(k_adj_m2l<T, KPT, GB>)) return rc;
     attr = true;
   }
   const size_t smem = (size_t)3 * P->m * sizeof(typename Vec4<T>::type);
   unsigned grid = 0;
-  if (int rc = resident_blocks(k_adj_m2l<T, KPT>, nt, smem, P->C, &grid)) return rc;
-  k_adj_m2l<T, KPT><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff),
-                                            P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_sorder), P->C,
-                                            ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc,
-                                                      P->cheb, P->m, ws_ptr<T>(P, L.wbuf), ws_ptr<T>(P, L.lbuf));
+  if (int rc = resident_blocks(k_adj_m2l<T, KPT, GB>, nt, smem, P->C, &grid)) return rc;
+  k_adj_m2l<T, KPT, GB><<<grid, nt, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1, ws_ptr<int32_t>(P, L.m2l_sorder),
+      P->C, ws_ptr<NodeGeo>(P, L.ngeo), P->ws + L.m2l_sdc, P->cheb, P->m, ws_ptr<T>(P, L.wbuf), ws_ptr<T>(P, L.lbuf),
+      ws_ptr<T>(P, L.mpole), ws_ptr<double>(P, L.gfar));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
 
-template <typename T>
-int adj_m2l(fmm_plan_s* P, cudaStream_t s) {
-  if (std::is_same<T, float>::value && P->eta <= 0.5) {
-    switch (P->np1) {
-      case 3: return launch_adj_m2l_fast<3, 3, 1>(P, s);
-      case 5: return launch_adj_m2l_fast<5, 5, 1>(P, s);
-      case 7: return launch_adj_m2l_fast<7, 4, 2>(P, s);
-      case 9: return launch_adj_m2l_fast<9, 3, 3>(P, s);
-      default: break;
-    }
-  }
+template <typename T, bool GB>
+int adj_m2l_generic(fmm_plan_s* P, cudaStream_t s) {
   // the same thread shape rule as the forward M2L
   int best_nt = 256, best_k = 4;
   int64_t best_waste = -1, best_passes = 0;
@@ -1073,16 +1151,32 @@ int adj_m2l(fmm_plan_s* P, cudaStream_t s) {
     }
   }
   switch (best_k) {
-    case 1: return launch_adj_m2l<T, 1>(P, best_nt, s);
-    case 2: return launch_adj_m2l<T, 2>(P, best_nt, s);
-    case 3: return launch_adj_m2l<T, 3>(P, best_nt, s);
-    default: return launch_adj_m2l<T, 4>(P, best_nt, s);
+    case 1: return launch_adj_m2l<T, 1, GB>(P, best_nt, s);
+    case 2: return launch_adj_m2l<T, 2, GB>(P, best_nt, s);
+    case 3: return launch_adj_m2l<T, 3, GB>(P, best_nt, s);
+    default: return launch_adj_m2l<T, 4, GB>(P, best_nt, s);
   }
 }
 
+// With the gbar term the generic kernel runs (it also forms the far-field
+// part of dL/dgbar); otherwise FP32 at eta <= 1/2 takes the specialised one.
 template <typename T>
-int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq,
-                  bool target_side, cudaStream_t s) {
+int adj_m2l(fmm_plan_s* P, bool gbar_term, cudaStream_t s) {
+  if (gbar_term) return adj_m2l_generic<T, true>(P, s);
+  if (std::is_same<T, float>::value && P->eta <= 0.5) {
+    switch (P->np1) {
+      case 3: return launch_adj_m2l_fast<3, 3, 1>(P, s);
+      case 5: return launch_adj_m2l_fast<5, 5, 1>(P, s);
+      case 7: return launch_adj_m2l_fast<7, 4, 2>(P, s);
+      case 9: return launch_adj_m2l_fast<9, 3, 3>(P, s);
+      default: break;
+    }
+  }
+  return adj_m2l_generic<T, false>(P, s);
+}
+
+template <typename T, bool GB>
+int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
@@ -1091,34 +1185,60 @@ int adj_particles(fmm_plan_s* P, const double* p, const double* q, double* dx, d
   const int nt = groups * NT;
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
-  if (target_side) {
-    const size_t smem = stage_bytes<T>(kSplit ? 4 : 2, 1, 6, groups, NT) + sizeof(T) * 6 * P->m;
-    static bool attr = false;
-    if (!attr) { if (int rc = set_smem(k_adj_target<T, 1>)) return rc; attr = true; }
-    // beside the source side's far field (side stream) the target side keeps
-    // to half of the SMs' block slots, so the other branch finds room
-    if (P->kappa > 0) {
-      int dev = 0, sms = 0;
-      FMM_CUDA_TRY(cudaGetDevice(&dev));
-      FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
-    }
-    k_adj_target<T, 1><<<grid, nt, smem, s>>>(
-        ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-        ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
-        P->cheb, P->chebd, P->m, groups, chunks, items, ws_ptr<V4>(P, L.adj_part));
-  } else {
-    const size_t smem = stage_bytes<T>(kSplit ? 4 : 3, 1, 14, groups, NT) + sizeof(T) * 4 * P->m;
-    static bool attr = false;
-    if (!attr) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr = true; }
-    k_adj_source<T, 1><<<grid, nt, smem, s>>>(
-        ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
-        ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
-        ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.lbuf),
-        P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
-        q, groups, chunks, dx, dp, dq);
+  const size_t smem = stage_bytes<T>(kSplit ? 4 : 2, 1, GB ? 8 : 6, groups, NT) + sizeof(T) * 6 * P->m;
+  static bool attr = false;
+  if (!attr) { if (int rc = set_smem(k_adj_target<T, 1, GB>)) return rc; attr = true; }
+  // beside the source side's far field (side stream) the target side keeps
+  // to half of the SMs' block slots, so the other branch finds room
+  if (P->kappa > 0) {
+    int dev = 0, sms = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
   }
+  k_adj_target<T, 1, GB><<<grid, nt, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+      ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+      ws_ptr<V4>(P, L.pl), P->ws + L.p2p_dc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.local),
+      P->cheb, P->chebd, P->m, groups, chunks, items, ws_ptr<V4>(P, L.adj_part));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+template <typename T>
+int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq, bool gbar_term,
+               cudaStream_t s) {
+  const Layout& L = P->lay;
+  using V4 = typename Vec4<T>::type;
+  constexpr bool kSplit = std::is_same<T, float>::value;
+  int NT, groups, chunks;
+  particle_shape(P->leaf, 1, &NT, &groups, &chunks);  // as the forward P2P
+  const int nt = groups * NT;
+  const unsigned grid = (unsigned)(P->nleaves * chunks);
+  const size_t smem = stage_bytes<T>(kSplit ? 4 : 3, 1, 14, groups, NT) + sizeof(T) * 4 * P->m;
+  static bool attr = false;
+  if (!attr) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr = true; }
+  k_adj_source<T, 1><<<grid, nt, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
+      ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
+      ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.lbuf),
+      P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
+      q, groups, chunks, gbar_term ? 1 : 0, dx, dp, dq);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+// dL/dgbar into scal[9], scal[10] (after the target side and M2L^T).
+template <typename T>
+int gbar_sum(fmm_plan_s* P, bool far, cudaStream_t s) {
+  const Layout& L = P->lay;
+  using V4 = typename Vec4<T>::type;
+  const int64_t nfar = far ? P->C : 0;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kGbarBlocks, div_up(std::max(P->N, nfar), 256 * 8)));
+  k_gbar_part<T><<<nb, 256, 0, s>>>(ws_ptr<V4>(P, L.adj_part), P->N, ws_ptr<double>(P, L.gfar), nfar,
+                                    ws_ptr<double>(P, L.gpart));
+  FMM_LAUNCH_CHECK();
+  k_gbar_final<<<1, 256, 0, s>>>(ws_ptr<double>(P, L.gpart), nb, P->N, ws_ptr<double>(P, L.scal));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -1158,6 +1278,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   // caller's stream.  They share no buffer that either writes: W and Lambda
   // have their own, the target side reads the forward's locals.
   const bool chain = P->kappa > 0;
+  const bool gb = (P->flags & FMM_GBAR_TERM) != 0;
   if (chain) {
     if ((rc = ensure_side(P)) != FMM_OK) return rc;
     cudaStream_t t = P->side;
@@ -1168,16 +1289,18 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     // cooperative launch would wait for the particle kernel to end
     if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, 4, true)) != FMM_OK) return rc;  // L2L^T
     if ((rc = record(P, 11, t)) != FMM_OK) return rc;
-    if ((rc = adj_m2l<T>(P, t)) != FMM_OK) return rc;
+    if ((rc = adj_m2l<T>(P, gb, t)) != FMM_OK) return rc;
     if ((rc = record(P, 12, t)) != FMM_OK) return rc;
     if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, 4, true)) != FMM_OK) return rc;  // M2M^T
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
     FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
   }
-  if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, true, s)) != FMM_OK) return rc;
+  rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
+  if (rc != FMM_OK) return rc;
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
   if (chain) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
-  if ((rc = adj_particles<T>(P, p, q, dx, dp, dq, false, s)) != FMM_OK) return rc;
+  if (gb && (rc = gbar_sum<T>(P, chain, s)) != FMM_OK) return rc;
+  if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, s)) != FMM_OK) return rc;
   if ((rc = record(P, 14, s)) != FMM_OK) return rc;
   (void)x;
   if (P->flags & FMM_TIMING) P->flags = (P->flags & ~0x300u) | 0x100u | (chain ? 0x200u : 0u);

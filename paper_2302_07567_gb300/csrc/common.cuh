@@ -40,6 +40,7 @@ enum : unsigned {
 // Device-resident counters of one call (first bytes of the workspace).
 // Blocks a cooperative traversal launch may use (scan partials reserved per list).
 constexpr int64_t kTravPartials = 4096;
+constexpr int kGbarBlocks = 512;  // most blocks of the dL/dgbar partial sums
 
 struct Counters {
   unsigned long long p2p_count;
@@ -92,6 +93,7 @@ struct Layout {
   size_t p2p_sdc, m2l_sdc;         // centre offsets of the source-major lists
   size_t tcnt, tpart;               // list ordering: per-node counts and fills, scan partials
   size_t thist, m2l_order, m2l_sorder;  // M2L work orders: count buckets, targets, sources
+  size_t gfar, gpart;  // adjoint with the gbar term: per-cluster far-field sums, block partials
   size_t nblk_sort;   // radix tiles of the three presorts
   size_t nblk_part;   // partition blocks at N
 };

@@ -100,6 +100,8 @@ void make_layout(fmm_plan_s* P) {
   L.lbuf = take(C1 * 4 * m * R);
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
+  L.gfar = take(C1 * 8);
+  L.gpart = take((size_t)kGbarBlocks * 8);
   L.total = off;
   P->lay = L;
 }
@@ -213,7 +215,8 @@ int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, doubl
   if (leaf_size < 2 || leaf_size > 4096) return FMM_EINVAL;
   if (!(eta > 0.0) || !std::isfinite(eta)) return FMM_EINVAL;
   if (precision != FMM_FP32 && precision != FMM_FP64) return FMM_EINVAL;
-  if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE | FMM_TEST_POLY_KERNEL))
+  if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE | FMM_TEST_POLY_KERNEL |
+                          FMM_GBAR_TERM))
     return FMM_EINVAL;
   if ((flags & FMM_TEST_POLY_KERNEL) && precision != FMM_FP64) return FMM_EINVAL;
   fmm_plan_s* P = new (std::nothrow) fmm_plan_s();

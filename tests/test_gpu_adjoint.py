@@ -124,3 +124,34 @@ def test_autograd_function_backward_is_the_adjoint():
     assert torch.allclose(Xr.grad, dx, rtol=0, atol=0)
     assert torch.allclose(Pr.grad, dp, rtol=0, atol=0)
     assert torch.allclose(Qr.grad, dq, rtol=0, atol=0)
+
+
+GBAR_CASES = {
+    "gauss2k": CASES["gauss2k"],
+    "ragged1501": CASES["ragged1501"],
+    "cylinder4k": CASES["cylinder4k"],
+    "single40": lambda: (random_beam(40, seed=4, gamma=5.0, spread=0.1, angle=0.2), 3, 64, 0.5),  # one leaf
+}
+
+
+@pytest.mark.parametrize("name", list(GBAR_CASES))
+def test_gbar_term_matches_oracle(name):
+    """FMM_GBAR_TERM: gbar follows p (Section 3, gbar = sqrt(1 + pbar.pbar)).
+    The full gradient against the oracle's with the same plan and gbar live;
+    the gbar term alone (live minus fixed) against the oracle's difference."""
+    (x, p, q), n, leaf, eta = GBAR_CASES[name]()
+    N = x.shape[0]
+    wE, wB = make_weights(N)
+    plan = bldtt.build_plan(x, p, n, leaf, eta)
+    _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, plan, gbar_term=True)
+    _, fx, fp, fq = gradient.fmm_gradient(x, p, q, wE, wB, plan)
+    want = (gp - fp).numpy()
+    assert np.linalg.norm(want) > 1e-8 * np.linalg.norm(gp.numpy())
+    c = dict(x=x, p=p, q=q, n=n, leaf=leaf, eta=eta, wE=wE, wB=wB)
+    for prec, tol, ttol in (("fp64", 1e-10, 1e-8), ("fp32", 2e-5, 1e-3)):
+        _, dx, dp, dq = gpu_grad(c, prec, flags=fmm.FMM_GBAR_TERM)
+        assert rel(dx, gx.numpy()) < tol, (prec, rel(dx, gx.numpy()))
+        assert rel(dp, gp.numpy()) < tol, (prec, rel(dp, gp.numpy()))
+        assert rel(dq, gq.numpy()) < tol, (prec, rel(dq, gq.numpy()))
+        _, dx0, dp0, dq0 = gpu_grad(c, prec)
+        assert rel(dp - dp0, want) < ttol, (prec, rel(dp - dp0, want))
