@@ -46,7 +46,7 @@ HOT = {"m2l": (32.0, "m2l_interactions"), "p2p_l2p": (32.0, "p2p_interactions"),
 # fwd+adj step, from one `ncu --set full` capture per kernel (summary and
 # command in profiles/hot_kernels_cylinder64k.md).  Valid only while the
 # kernel is unchanged since that capture; reported for that workload only.
-TRAFFIC_CYL64K = {"adj_source": 11883776 + 719616, "p2p_l2p": 7997696 + 3072,
+TRAFFIC_CYL64K = {"adj_source": 11883776 + 719616, "adj_target": 9832448 + 3584, "p2p_l2p": 7997696 + 3072,
                   "m2l": 2673920, "adj_m2lt": 3963392}
 CONCURRENT = ("adj_target", "adj_m2lt")  # stages that overlap each other (two streams)
 SMS = 152          # GB300 streaming multiprocessors
