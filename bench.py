@@ -38,17 +38,21 @@ if ROOT not in sys.path:
 from paper_2302_07567_gb300.workloads import WORKLOADS, make_beam, make_weights, sample_targets  # noqa: E402
 
 METRIC = "particles/s (E,B on all N; fwd and fwd+adjoint) at fixed rel. L2 error vs FP64"
-# hot kernels: stage name -> (algorithmic flop per unit, stats key counting the units)
+# hot kernels: stage name -> (algorithmic flop per unit, stats key counting the units).
+# The FP32 adjoint without the gbar term evaluates both roles of every
+# near-field pair in one kernel (stage adj_near, 84 flop per pair; its
+# adj_source stage is then the far field and the chain rule only); otherwise
+# adj_near is the target side (46) and adj_source the source side (67).
 HOT = {"m2l": (32.0, "m2l_interactions"), "p2p_l2p": (32.0, "p2p_interactions"),
-       "adj_m2lt": (32.0, "m2l_interactions"), "adj_target": (46.0, "p2p_interactions"),
-       "adj_source": (67.0, "p2p_interactions")}
+       "adj_m2lt": (32.0, "m2l_interactions")}
+HOT_FUSED = {"adj_near": (84.0, "p2p_interactions")}
+HOT_SPLIT = {"adj_near": (46.0, "p2p_interactions"), "adj_source": (67.0, "p2p_interactions")}
 # DRAM bytes (read + write) per launch of each hot kernel on the cylinder64k
 # fwd+adj step, from one `ncu --set full` capture per kernel (summary and
 # command in profiles/hot_kernels_cylinder64k.md).  Valid only while the
 # kernel is unchanged since that capture; reported for that workload only.
-TRAFFIC_CYL64K = {"adj_source": 11883776 + 719616, "adj_target": 9832448 + 3584, "p2p_l2p": 7997696 + 3072,
-                  "m2l": 2673920, "adj_m2lt": 3963392}
-CONCURRENT = ("adj_target", "adj_m2lt")  # stages that overlap each other (two streams)
+TRAFFIC_CYL64K = {"p2p_l2p": 7997696 + 3072, "m2l": 2673920, "adj_m2lt": 3963392}
+CONCURRENT = ("adj_near", "adj_m2lt")  # stages that overlap each other (two streams)
 SMS = 152          # GB300 streaming multiprocessors
 FP32_LANES = 128   # FP32 FMA lanes per SM
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -181,7 +185,8 @@ def run_ours(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     st0 = plan.stats()
-    stage_hist = {k: [] for k in HOT}
+    hot = dict(HOT, **(HOT_FUSED if args.precision == "fp32" and not args.gbar_term else HOT_SPLIT))
+    stage_hist = {k: [] for k in hot}
     step_ms = []
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -196,7 +201,7 @@ def run_ours(args, rank, world, local):
             step()
             ev1[k].record(stream)
             st = plan.stats()  # stage events of this step (same stream)
-            for k in HOT:
+            for k in hot:
                 stage_hist[k].append(st["stage_ms"][k])
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -271,7 +276,7 @@ def run_ours(args, rank, world, local):
     mhz = clocks["sm_mhz"] or 2070.0
     peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12 if args.precision == "fp32" else None
     kernels = {}
-    for k, (per, unit) in HOT.items():
+    for k, (per, unit) in hot.items():
         ms = statistics.median(stage_hist[k]) if stage_hist[k] else 0.0
         if ms <= 0.0:
             continue
@@ -292,7 +297,8 @@ def run_ours(args, rank, world, local):
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock)",
             "flop_basis": "algorithmic flop per pair (FMA = 2): M2L and M2L^T 32 per point pair, P2P 32, "
-                          "adjoint near field 46 (target side) and 67 (source side) per particle pair",
+                          "adjoint near field 84 per particle pair for both roles in one kernel (FP32), "
+                          "else 46 (target side) and 67 (source side)",
             "kernels": kernels}
 
     if rank == 0:

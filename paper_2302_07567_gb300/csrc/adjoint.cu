@@ -735,9 +735,221 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
   }  // items
 }
 
+// FP32 near field of both roles in one pass (the default FP32 adjoint).  A
+// thread owns particle i of leaf L.  For every P2P partner leaf P of L it
+// takes both roles of each pair (i, j), R = x_i - x_j:
+//   i as target:  dL/dx'_i += J(R) u_ij,         u_ij = a'_j w^E_i + w^B_i x b~'_j
+//   i as source:  dL/dx'_i -= J(R) u_ji,         u_ji = a'_i w^E_j + w^B_j x b~'_i
+//                 dL/da'_i -= w^E_j . K(R),  dL/db~'_i -= K(R) x w^B_j,  K = r^-3 R
+// with J(R) v = r^-3 v - 3 r^-5 R (R . v) even in R, so the two J terms are
+// one J(R)(u_ij - u_ji).  The partners come from merging L's target-major
+// list (P is a source of L) with its source-major list (P is a target of L),
+// both sorted by partner: a partner in only one list gets only that role,
+// by staging its masses (no target role) or its weights (no source role) as
+// zero.  Partners are staged in pairs as in k_adj_target and evaluated with
+// paired FP32 arithmetic; per partner leaf the two lanes are added and
+// Kahan-summed.  The target-side far field (grad of the forward's cumulative
+// local) is added as in k_adj_target.  Output per particle (leaf order):
+// g1 = (dL/dx' (3), dL/da'), g2 = (dL/db~' (3), 0); the source-side far field
+// and the chain rule follow in k_adj_source.
+__global__ void __launch_bounds__(128, 5) k_adj_near(
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, const uint64_t* __restrict__ skeys,
+    const int32_t* __restrict__ soff, int shift, const int64_t* __restrict__ nstart,
+    const int64_t* __restrict__ ncount, int kappa, const NodeGeo* __restrict__ geo, const float4* __restrict__ px,
+    const float4* __restrict__ pb, const float4* __restrict__ pl, const float4* __restrict__ pdc,
+    const float4* __restrict__ sdc, const float4* __restrict__ wle, const float4* __restrict__ wlb,
+    const float* __restrict__ Lcum, Cheb ch, ChebD cd, int m, int groups, int chunks, int64_t nitems,
+    float4* __restrict__ g1, float4* __restrict__ g2) {
+  // staged partner pairs: 12 float4 (48 floats), 24 components as (partner
+  // 2q, partner 2q+1): -x_hi (3), -x_lo (3), a, b~ (3), -b~ (3), w^E (3),
+  // w^B (3), -w^B (3), 0, 0
+  constexpr int kRow = 6;  // float4 per staged partner
+  constexpr int NC = 7;    // dL/dx' (3), dL/da', dL/db~' (3)
+  extern __shared__ unsigned char smem_raw[];
+  const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  float* sl = reinterpret_cast<float*>(smem_raw + stage_bytes<float>(kRow, 1, 2 * NC, groups, NT));  // [6][m]
+  const uint64_t mask = ((uint64_t)1 << shift) - 1;
+  const int np1 = ch.np1;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
+  __syncthreads();  // the previous item's readers of the stage and sl are done
+  const int64_t L = ((int64_t)1 << kappa) + item / chunks;
+  const int64_t c0 = (int64_t)(item % chunks) * NT;
+  const int64_t st = nstart[L], cnt = min64(ncount[L], c0 + NT);
+  if (c0 >= cnt) continue;  // the leaf is smaller than this chunk
+  const NodeGeo gt = geo[L];
+  float invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(gt.h[d] > 0.0);
+    invh[d] = deg[d] ? 0.f : (float)(1.0 / gt.h[d]);
+  }
+  if (kappa > 0) {
+    const float* Lt = Lcum + (size_t)L * 6 * m;
+    for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
+  }
+  const int64_t j0 = c0 + lt;
+  const bool valid = j0 < cnt;
+  const int64_t jj = st + (valid ? j0 : 0);
+  const float4 u0 = px[jj], b0 = pb[jj], l0 = pl[jj], e0 = wle[jj], w0 = wlb[jj];
+  float acc[NC], cmp[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
+  const float2 WE0 = make_float2(e0.x, e0.x), WE1 = make_float2(e0.y, e0.y), WE2 = make_float2(e0.z, e0.z);
+  const float2 WB0 = make_float2(w0.x, w0.x), WB1 = make_float2(w0.y, w0.y), WB2 = make_float2(w0.z, w0.z);
+  const float2 NA = make_float2(-u0.w, -u0.w);
+  const float2 B0 = make_float2(b0.x, b0.x), B1 = make_float2(b0.y, b0.y), B2 = make_float2(b0.z, b0.z);
+  const float2 m3 = make_float2(-3.f, -3.f);
+  int it1 = off[L], it2 = soff[L];
+  const int e1 = off[L + 1], e2 = soff[L + 1];
+  while (it1 < e1 || it2 < e2) {  // merge by partner leaf (block-uniform)
+    const int64_t P1 = it1 < e1 ? (int64_t)(keys[it1] & mask) : INT64_MAX;
+    const int64_t P2 = it2 < e2 ? (int64_t)(skeys[it2] & mask) : INT64_MAX;
+    const int64_t P = P1 < P2 ? P1 : P2;
+    const bool tgt = P1 == P, src = P2 == P;  // i as target of P's particles / as their source
+    // c_L - c_P (scaled), the same in both lists for major L
+    const float4 dh = tgt ? pdc[2 * it1] : sdc[2 * it2], dl = tgt ? pdc[2 * it1 + 1] : sdc[2 * it2 + 1];
+    if (tgt) ++it1;
+    if (src) ++it2;
+    float X[3], XL[3];  // x_i in P's frame, hi + lo
+    {
+      const float ri[3] = {u0.x, u0.y, u0.z}, rl[3] = {l0.x, l0.y, l0.z};
+      const float dch[3] = {dh.x, dh.y, dh.z}, dcl[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float hs, he;
+        two_sum(ri[d], dch[d], hs, he);
+        const float lo = he + (rl[d] + dcl[d]);
+        X[d] = hs + lo;
+        XL[d] = lo - (X[d] - hs);
+      }
+    }
+    const float2 X0 = make_float2(X[0], X[0]), X1 = make_float2(X[1], X[1]), X2 = make_float2(X[2], X[2]);
+    const float2 L0 = make_float2(XL[0], XL[0]), L1 = make_float2(XL[1], XL[1]), L2 = make_float2(XL[2], XL[2]);
+    const int64_t sst = nstart[P], scnt = ncount[P];
+    float2 pp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pp[c] = make_float2(0.f, 0.f);
+    for (int64_t base = 0; base < scnt; base += blockDim.x) {
+      __syncthreads();
+      const int64_t j = base + threadIdx.x;
+      {
+        float c[24];
+        if (j < scnt) {
+          const float4 u = px[sst + j], w = pb[sst + j], l = pl[sst + j];
+          const float4 e = src ? wle[sst + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 v = src ? wlb[sst + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float a = tgt ? u.w : 0.f, bx = tgt ? w.x : 0.f, by = tgt ? w.y : 0.f, bz = tgt ? w.z : 0.f;
+          c[0] = -u.x; c[1] = -u.y; c[2] = -u.z; c[3] = -l.x; c[4] = -l.y; c[5] = -l.z;
+          c[6] = a; c[7] = bx; c[8] = by; c[9] = bz; c[10] = -bx; c[11] = -by; c[12] = -bz;
+          c[13] = e.x; c[14] = e.y; c[15] = e.z; c[16] = v.x; c[17] = v.y; c[18] = v.z;
+          c[19] = -v.x; c[20] = -v.y; c[21] = -v.z; c[22] = 0.f; c[23] = 0.f;
+        } else {  // partner of an odd last particle: no mass, no weight, no contribution
+#pragma unroll
+          for (int q = 0; q < 24; ++q) c[q] = 0.f;
+        }
+        float* f = reinterpret_cast<float*>(smem_raw) + (threadIdx.x >> 1) * 48 + (threadIdx.x & 1);
+#pragma unroll
+        for (int q = 0; q < 24; ++q) f[2 * q] = c[q];
+      }
+      __syncthreads();
+      const int nj = (int)min64(blockDim.x, scnt - base);
+      const int npq = (nj + 1) >> 1;
+      const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
+      for (int qq = grp * share2; qq < q1; ++qq) {
+        const float4* s4 = reinterpret_cast<const float4*>(smem_raw) + 12 * qq;
+        const float4 S0 = s4[0], S1 = s4[1], S2 = s4[2], S3 = s4[3], S4 = s4[4], S5 = s4[5];
+        const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(S0.x, S0.y)), __fadd2_rn(L0, make_float2(S1.z, S1.w)));
+        const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(S0.z, S0.w)), __fadd2_rn(L1, make_float2(S2.x, S2.y)));
+        const float2 rz = __fadd2_rn(__fadd2_rn(X2, make_float2(S1.x, S1.y)), __fadd2_rn(L2, make_float2(S2.z, S2.w)));
+        const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+        float2 inv;
+        inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+        inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+        const float2 inv2 = __fmul2_rn(inv, inv);
+        const float2 r3 = __fmul2_rn(inv2, inv);
+        const float2 r5 = __fmul2_rn(r3, inv2);
+        const float2 aj = make_float2(S3.x, S3.y);
+        const float2 bx = make_float2(S3.z, S3.w), by = make_float2(S4.x, S4.y), bz = make_float2(S4.z, S4.w);
+        const float2 nbx = make_float2(S5.x, S5.y), nby = make_float2(S5.z, S5.w);
+        const float4 S6 = s4[6], S7 = s4[7], S8 = s4[8], S9 = s4[9], S10 = s4[10];
+        const float2 nbz = make_float2(S6.x, S6.y);
+        const float2 ex = make_float2(S6.z, S6.w), ey = make_float2(S7.x, S7.y), ez = make_float2(S7.z, S7.w);
+        const float2 wx = make_float2(S8.x, S8.y), wy = make_float2(S8.z, S8.w), wz = make_float2(S9.x, S9.y);
+        const float2 nwx = make_float2(S9.z, S9.w), nwy = make_float2(S10.x, S10.y), nwz = make_float2(S10.z, S10.w);
+        // v = u_ij - u_ji = a_j w^E_i + w^B_i x b_j - a_i w^E_j + b_i x w^B_j
+        const float2 vx = __ffma2_rn(aj, WE0, __ffma2_rn(WB1, bz, __ffma2_rn(WB2, nby,
+                          __ffma2_rn(NA, ex, __ffma2_rn(B1, wz, __fmul2_rn(B2, nwy))))));
+        const float2 vy = __ffma2_rn(aj, WE1, __ffma2_rn(WB2, bx, __ffma2_rn(WB0, nbz,
+                          __ffma2_rn(NA, ey, __ffma2_rn(B2, wx, __fmul2_rn(B0, nwz))))));
+        const float2 vz = __ffma2_rn(aj, WE2, __ffma2_rn(WB0, by, __ffma2_rn(WB1, nbx,
+                          __ffma2_rn(NA, ez, __ffma2_rn(B0, wy, __fmul2_rn(B1, nwx))))));
+        const float2 rv = __ffma2_rn(rz, vz, __ffma2_rn(ry, vy, __fmul2_rn(rx, vx)));
+        const float2 nc3 = __fmul2_rn(__fmul2_rn(r5, m3), rv);
+        pp[0] = __ffma2_rn(nc3, rx, __ffma2_rn(r3, vx, pp[0]));
+        pp[1] = __ffma2_rn(nc3, ry, __ffma2_rn(r3, vy, pp[1]));
+        pp[2] = __ffma2_rn(nc3, rz, __ffma2_rn(r3, vz, pp[2]));
+        // source role, summed with the sign flipped at the end: K . w^E_j, K x w^B_j
+        const float2 re = __ffma2_rn(rz, ez, __ffma2_rn(ry, ey, __fmul2_rn(rx, ex)));
+        pp[3] = __ffma2_rn(r3, re, pp[3]);
+        pp[4] = __ffma2_rn(r3, __ffma2_rn(ry, wz, __fmul2_rn(rz, nwy)), pp[4]);
+        pp[5] = __ffma2_rn(r3, __ffma2_rn(rz, wx, __fmul2_rn(rx, nwz)), pp[5]);
+        pp[6] = __ffma2_rn(r3, __ffma2_rn(rx, wy, __fmul2_rn(ry, nwx)), pp[6]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) kahan_add(acc[c], cmp[c], pp[c].x + pp[c].y);
+#pragma unroll
+    for (int c = 3; c < NC; ++c) kahan_add(acc[c], cmp[c], -(pp[c].x + pp[c].y));
+  }
+  __syncthreads();
+  const int a3share = (np1 + groups - 1) / groups;
+  const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
+  if (valid && kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
+    float lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
+    basis_deriv<float>((u0.x + l0.x) * invh[0], deg[0], ch, cd, lx, dx);
+    basis_deriv<float>((u0.y + l0.y) * invh[1], deg[1], ch, cd, ly, dy);
+    basis_deriv<float>((u0.z + l0.z) * invh[2], deg[2], ch, cd, lz, dz);
+    float G[3] = {0.f, 0.f, 0.f};
+    int mu = a3b * np1 * np1;
+    for (int a3 = a3b; a3 < a3e; ++a3) {
+      for (int a2 = 0; a2 < np1; ++a2) {
+        float s0 = 0.f, sx = 0.f;
+        for (int a1 = 0; a1 < np1; ++a1, ++mu) {
+          const float phi = e0.x * sl[mu] + e0.y * sl[m + mu] + e0.z * sl[2 * m + mu] +
+                            w0.x * sl[3 * m + mu] + w0.y * sl[4 * m + mu] + w0.z * sl[5 * m + mu];
+          s0 += lx[a1] * phi;
+          sx += dx[a1] * phi;
+        }
+        G[0] += ly[a2] * lz[a3] * sx;
+        G[1] += dy[a2] * lz[a3] * s0;
+        G[2] += ly[a2] * dz[a3] * s0;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) kahan_add(acc[d], cmp[d], G[d] * invh[d]);
+  }
+  {
+    float a2[1][NC], c2[1][NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      a2[0][c] = acc[c];
+      c2[0][c] = cmp[c];
+    }
+    combine_groups<float, 1, NC>(a2, c2, reinterpret_cast<float*>(smem_raw), groups, grp, NT, lt);
+    if (grp == 0 && valid) {
+      const int64_t pos = st + j0;
+      g1[pos] = make_float4(a2[0][0], a2[0][1], a2[0][2], a2[0][3]);
+      g2[pos] = make_float4(a2[0][4], a2[0][5], a2[0][6], 0.f);
+    }
+  }
+  }  // items
+}
+
 // Source side: near field over the source-major P2P list, far field from the
 // pushed-down Lambda, plus the target-side part; then the chain rule to
-// physical (x, p, q), written in input order.
+// physical (x, p, q), written in input order.  With `fused` the near field of
+// both roles is already in gtarget = (dL/dx', dL/da') and g2 = (dL/db~', 0)
+// (k_adj_near) and the list walk is skipped.
 template <typename T, int KPT>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
@@ -748,8 +960,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lam, Cheb ch, ChebD cd, int m,
     const typename Vec4<T>::type* __restrict__ gtarget, const int32_t* __restrict__ perm,
     const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q, int groups,
-    int chunks, int gbar_term, double* __restrict__ dx_out, double* __restrict__ dp_out,
-    double* __restrict__ dq_out) {
+    int chunks, int gbar_term, int fused, const typename Vec4<T>::type* __restrict__ g2,
+    double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 4 : 3;
@@ -764,7 +976,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
   if (c0 >= cnt) return;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gs = geo[s];
-  const int b = off[s], e = off[s + 1];
+  const int b = fused ? 0 : off[s], e = fused ? 0 : off[s + 1];
   const int np1 = ch.np1;
   T invh[3];
   bool deg[3];
@@ -1006,10 +1218,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
       if (grp != 0 || !valid[k]) continue;
       const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       const V4 gt = gtarget[pos];
+      V4 gs;  // the fused near field's dL/db~' (zero otherwise)
+      gs.x = gs.y = gs.z = gs.w = T(0);
+      if (fused) gs = g2[pos];
+      const double ga = fused ? (double)gt.w : 0.0;
       // internal (a', b~', x') -> physical (a, b, x)
-      const double dA = (double)acc[k][0] / mu_u;
-      const double dB[3] = {(double)acc[k][1] / (gbar * mu_u), (double)acc[k][2] / (gbar * mu_u),
-                            (double)acc[k][3] / mu_u};
+      const double dA = ((double)acc[k][0] + ga) / mu_u;
+      const double dB[3] = {((double)acc[k][1] + (double)gs.x) / (gbar * mu_u),
+                            ((double)acc[k][2] + (double)gs.y) / (gbar * mu_u), ((double)acc[k][3] + (double)gs.z) / mu_u};
       const double dX[3] = {((double)acc[k][4] + (double)gt.x) / ell, ((double)acc[k][5] + (double)gt.y) / ell,
                             gbar * ((double)acc[k][6] + (double)gt.z) / ell};
       const int64_t i = perm[pos];
@@ -1207,7 +1423,7 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
 
 template <typename T>
 int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq, bool gbar_term,
-               cudaStream_t s) {
+               bool fused, cudaStream_t s) {
   const Layout& L = P->lay;
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
@@ -1223,7 +1439,37 @@ int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, doub
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
       ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.lbuf),
       P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
-      q, groups, chunks, gbar_term ? 1 : 0, dx, dp, dq);
+      q, groups, chunks, gbar_term ? 1 : 0, fused ? 1 : 0, ws_ptr<V4>(P, L.adj_part2), dx, dp, dq);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+// FP32 near field of both roles (k_adj_near), on the caller's stream beside
+// the source side's far field; like the target side it keeps to part of the
+// SMs' block slots.
+int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  int NT, groups, chunks;
+  particle_shape(P->leaf, 1, &NT, &groups, &chunks);  // as the forward P2P
+  const int nt = groups * NT;
+  const int64_t items = P->nleaves * chunks;
+  unsigned grid = (unsigned)items;
+  const size_t smem = stage_bytes<float>(6, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;
+  static bool attr = false;
+  if (!attr) { if (int rc = set_smem(k_adj_near)) return rc; attr = true; }
+  if (P->kappa > 0) {
+    int dev = 0, sms = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);
+  }
+  k_adj_near<<<grid, nt, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), ws_ptr<uint64_t>(P, L.p2p_src),
+      ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount),
+      P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb),
+      ws_ptr<float4>(P, L.pl), ws_ptr<float4>(P, L.p2p_dc), ws_ptr<float4>(P, L.p2p_sdc), ws_ptr<float4>(P, L.wle),
+      ws_ptr<float4>(P, L.wlb), ws_ptr<float>(P, L.local), P->cheb, P->chebd, P->m, groups, chunks, items,
+      ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -1295,12 +1541,15 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
     FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
   }
-  rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
+  // FP32 without the gbar term: both near-field roles in one kernel
+  const bool fused = std::is_same<T, float>::value && !gb;
+  if (fused) rc = launch_adj_near(P, s);
+  else rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
   if (rc != FMM_OK) return rc;
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
   if (chain) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
   if (gb && (rc = gbar_sum<T>(P, chain, s)) != FMM_OK) return rc;
-  if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, s)) != FMM_OK) return rc;
+  if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, fused, s)) != FMM_OK) return rc;
   if ((rc = record(P, 14, s)) != FMM_OK) return rc;
   (void)x;
   if (P->flags & FMM_TIMING) P->flags = (P->flags & ~0x300u) | 0x100u | (chain ? 0x200u : 0u);

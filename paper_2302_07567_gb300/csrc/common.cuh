@@ -94,6 +94,7 @@ struct Layout {
   size_t tcnt, tpart;               // list ordering: per-node counts and fills, scan partials
   size_t thist, m2l_order, m2l_sorder;  // M2L work orders: count buckets, targets, sources
   size_t gfar, gpart;  // adjoint with the gbar term: per-cluster far-field sums, block partials
+  size_t adj_part2;    // FP32 adjoint: dL/db~' of the fused near field, per particle
   size_t nblk_sort;   // radix tiles of the three presorts
   size_t nblk_part;   // partition blocks at N
 };

@@ -101,6 +101,7 @@ void make_layout(fmm_plan_s* P) {
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.gfar = take(C1 * 8);
+  L.adj_part2 = take(N * V4);
   L.gpart = take((size_t)kGbarBlocks * 8);
   L.total = off;
   P->lay = L;
@@ -410,7 +411,7 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
       // the target side runs on the caller's stream while L2P^T .. M2M^T run
       // on the side stream, both from event 16; the source side starts when
       // both have finished
-      P->stage_ms[11] = el(16, 10);  // target-side particle kernel
+      P->stage_ms[11] = el(16, 10);  // near-field particle kernel (both roles in FP32, else the target side)
       if (P->flags & 0x200u) {
         P->stage_ms[8] = el(16, 11);   // L2P^T + L2L^T
         P->stage_ms[9] = el(11, 12);   // M2L^T

@@ -27,7 +27,7 @@ FMM_FP64, FMM_FP32 = 0, 1
 FMM_RECOMPUTE, FMM_BOUNDS_CHECK, FMM_TIMING, FMM_SIZE_AWARE, FMM_TEST_POLY_KERNEL, FMM_GBAR_TERM = 1, 2, 4, 8, 16, 32
 EXPORT = dict(gbar=0, perm=1, nodes=2, bbox=3, axis=4, p2p=5, m2l=6, multipole=7, local=8)
 STAGES = ["setup", "tree", "upward", "traversal", "host_wait", "m2l", "l2l", "p2p_l2p",
-          "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_target", "adj_source", "total", "adj_total", "adj_lists"]
+          "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_near", "adj_source", "total", "adj_total", "adj_lists"]
 
 _lib = None
 

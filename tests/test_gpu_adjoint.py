@@ -28,7 +28,18 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def lattice512():
+    """8 x 8 x 8 lattice: equal cluster radii make the traversal's P2P list
+    one-directional for some leaf pairs (32 of 448 here), which exercises
+    the FP32 fused near field's single-role partners."""
+    g = np.arange(8)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float64) * 1e-3
+    _, p, q = random_beam(x.shape[0], seed=6, gamma=4.0, spread=0.05, angle=0.05)
+    return x, p, q
+
+
 CASES = {
+    "lattice512": lambda: (lattice512(), 3, 8, 0.5),
     "gauss2k": lambda: (make_beam("gauss4k", N=2048), 4, 64, 0.5),
     "ragged1501": lambda: (random_beam(1501, seed=3, gamma=15.0, spread=0.05, angle=0.02), 3, 37, 0.5),
     "cylinder4k": lambda: (make_beam("cylinder64k", N=4096), 6, 128, 0.5),
@@ -57,6 +68,12 @@ def gpu_grad(c, prec, flags=0):
     dx, dp, dq = plan.adjoint(X, Pm, Q, WE, WB)
     torch.cuda.synchronize()
     return plan, dx.cpu().numpy(), dp.cpu().numpy(), dq.cpu().numpy()
+
+
+def test_lattice_case_has_one_directional_p2p_pairs():
+    (x, p, q), n, leaf, eta = CASES["lattice512"]()
+    pairs = set(map(tuple, bldtt.build_plan(x, p, n, leaf, eta).p2p))
+    assert sum((b, a) not in pairs for a, b in pairs) > 0
 
 
 def test_adjoint_fp64_matches_oracle_gradient(case):
