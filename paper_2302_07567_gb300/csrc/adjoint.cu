@@ -1290,6 +1290,142 @@ __global__ void __launch_bounds__(256) k_gbar_final(const double* __restrict__ g
   scal[10] = d / ((double)N * gbar);
 }
 
+// FP32 adjoint after k_adj_near: the source-side far field and the chain
+// rule, one thread per particle of a leaf chunk of 128.  Lambda of the leaf is
+// staged with its four components side by side (one 16-byte shared load per
+// point); then per particle j
+//   dL/da'_j += sum_nu l_nu(x_j) Lambda^a_nu,  dL/db~'_j += sum_nu l_nu(x_j) Lambda^b_nu,
+//   dL/dx'_j += sum_nu grad l_nu(x_j) psi_nu,  psi_nu = Lambda_nu . (a'_j, b~'_j),
+// added to the near field of k_adj_near, and the result is taken to physical
+// (x, p, q) as in k_adj_source.
+constexpr int kFinalThreads = 128;
+
+// basis_deriv with the points per axis fixed at compile time (the same
+// barycentric formula and derivative matrix), so the arrays stay in registers
+template <int NP1>
+__device__ __forceinline__ void basis_deriv_n(float t, bool deg, const Cheb& ch, const ChebD& cd, float (&l)[NP1],
+                                              float (&dl)[NP1]) {
+  int hit = deg ? 0 : -1;
+  if (!deg) {
+#pragma unroll
+    for (int k = 0; k < NP1; ++k)
+      if (hit < 0 && fabsf(t - (float)ch.t[k]) <= 1e-30f) hit = k;
+  }
+  if (hit >= 0) {
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) l[k] = (k == hit) ? 1.f : 0.f;
+  } else {
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) {
+      l[k] = (float)ch.w[k] / (t - (float)ch.t[k]);
+      sum += l[k];
+    }
+    const float inv = 1.f / sum;
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) l[k] *= inv;
+  }
+#pragma unroll
+  for (int k = 0; k < NP1; ++k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int mm = 0; mm < NP1; ++mm) acc += l[mm] * (float)cd.D[mm * NP1 + k];
+    dl[k] = deg ? 0.f : acc;
+  }
+}
+
+template <int NP1>  // 0: points per axis from ch at run time
+__global__ void __launch_bounds__(kFinalThreads) k_adj_final(
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
+    const NodeGeo* __restrict__ geo, const float4* __restrict__ px, const float4* __restrict__ pb,
+    const float4* __restrict__ pl, const float* __restrict__ Lam, Cheb ch, ChebD cd, int m, int chunks,
+    const float4* __restrict__ g1, const float4* __restrict__ g2, const int32_t* __restrict__ perm,
+    const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q,
+    double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
+  extern __shared__ float4 slam[];  // [m]
+  const int64_t s = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * kFinalThreads;
+  const int64_t st = nstart[s], cnt = ncount[s];
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
+  const bool far = kappa > 0;
+  if (far) {
+    const float* Ls = Lam + (size_t)s * 4 * m;
+    for (int o = threadIdx.x; o < m; o += blockDim.x) slam[o] = make_float4(Ls[o], Ls[m + o], Ls[2 * m + o], Ls[3 * m + o]);
+  }
+  __syncthreads();
+  const int64_t j = c0 + threadIdx.x;
+  if (j >= cnt) return;
+  const int64_t pos = st + j;
+  const float4 u = px[pos], b = pb[pos], l = pl[pos];
+  float F[4] = {0.f, 0.f, 0.f, 0.f}, G[3] = {0.f, 0.f, 0.f};
+  const NodeGeo gs = geo[s];
+  float invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(gs.h[d] > 0.0);
+    invh[d] = deg[d] ? 0.f : (float)(1.0 / gs.h[d]);
+  }
+  if (far) {
+    constexpr int K = NP1 > 0 ? NP1 : kMaxNp1;
+    const int np1 = NP1 > 0 ? NP1 : ch.np1;
+    float lx[K], ly[K], lz[K], dx[K], dy[K], dz[K];
+    if constexpr (NP1 > 0) {
+      basis_deriv_n<K>((u.x + l.x) * invh[0], deg[0], ch, cd, lx, dx);
+      basis_deriv_n<K>((u.y + l.y) * invh[1], deg[1], ch, cd, ly, dy);
+      basis_deriv_n<K>((u.z + l.z) * invh[2], deg[2], ch, cd, lz, dz);
+    } else {
+      basis_deriv<float>((u.x + l.x) * invh[0], deg[0], ch, cd, lx, dx);
+      basis_deriv<float>((u.y + l.y) * invh[1], deg[1], ch, cd, ly, dy);
+      basis_deriv<float>((u.z + l.z) * invh[2], deg[2], ch, cd, lz, dz);
+    }
+    int nu = 0;
+    for (int a3 = 0; a3 < np1; ++a3) {
+      for (int a2 = 0; a2 < np1; ++a2) {
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, s0 = 0.f, sx = 0.f;
+#pragma unroll
+        for (int a1 = 0; a1 < (NP1 > 0 ? NP1 : np1); ++a1, ++nu) {
+          const float4 L = slam[nu];
+          const float psi = L.x * u.w + L.y * b.x + L.z * b.y + L.w * b.z;
+          f0 += lx[a1] * L.x;
+          f1 += lx[a1] * L.y;
+          f2 += lx[a1] * L.z;
+          f3 += lx[a1] * L.w;
+          s0 += lx[a1] * psi;
+          sx += dx[a1] * psi;
+        }
+        const float wyz = ly[a2] * lz[a3];
+        F[0] += wyz * f0;
+        F[1] += wyz * f1;
+        F[2] += wyz * f2;
+        F[3] += wyz * f3;
+        G[0] += wyz * sx;
+        G[1] += dy[a2] * lz[a3] * s0;
+        G[2] += ly[a2] * dz[a3] * s0;
+      }
+    }
+  }
+  const float4 h1 = g1[pos], h2 = g2[pos];
+  const double gbar = scal[0], mu_u = scal[1], ell = scal[2];
+  // internal (a', b~', x') -> physical (a, b, x)
+  const double dA = ((double)h1.w + (double)F[0]) / mu_u;
+  const double dB[3] = {((double)h2.x + (double)F[1]) / (gbar * mu_u), ((double)h2.y + (double)F[2]) / (gbar * mu_u),
+                        ((double)h2.z + (double)F[3]) / mu_u};
+  const double dX[3] = {((double)h1.x + (double)(G[0] * invh[0])) / ell, ((double)h1.y + (double)(G[1] * invh[1])) / ell,
+                        gbar * ((double)h1.z + (double)(G[2] * invh[2])) / ell};
+  const int64_t i = perm[pos];
+  const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2], qi = q[i];
+  const double gam = sqrt(1.0 + ((p0 * p0 + p1 * p1) + p2 * p2));
+  // a = q gamma, b = q p:  dL/dq = gamma dL/da + p . dL/db,
+  //                        dL/dp = q (p/gamma) dL/da + q dL/db
+  dq_out[i] = gam * dA + (p0 * dB[0] + p1 * dB[1] + p2 * dB[2]);
+  dp_out[3 * i + 0] = qi * (p0 / gam) * dA + qi * dB[0];
+  dp_out[3 * i + 1] = qi * (p1 / gam) * dA + qi * dB[1];
+  dp_out[3 * i + 2] = qi * (p2 / gam) * dA + qi * dB[2];
+  dx_out[3 * i + 0] = dX[0];
+  dx_out[3 * i + 1] = dX[1];
+  dx_out[3 * i + 2] = dX[2];
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename K>
 int set_smem(K kernel) {
@@ -1421,9 +1557,35 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   return FMM_OK;
 }
 
+// FP32 after k_adj_near: source-side far field and chain rule.
+int launch_adj_final(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq,
+                     cudaStream_t s) {
+  const Layout& L = P->lay;
+  const int64_t most = *std::max_element(P->node_count.begin() + P->nleaves, P->node_count.end());
+  const int chunks = (int)div_up(most, kFinalThreads);
+  const size_t smem = sizeof(float4) * P->m;
+  auto kern = k_adj_final<0>;
+  switch (P->np1) {
+    case 3: kern = k_adj_final<3>; break;
+    case 5: kern = k_adj_final<5>; break;
+    case 7: kern = k_adj_final<7>; break;
+    case 9: kern = k_adj_final<9>; break;
+    default: break;
+  }
+  FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)(P->nleaves * chunks), kFinalThreads, smem, s>>>(
+      ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb), ws_ptr<float4>(P, L.pl), ws_ptr<float>(P, L.lbuf), P->cheb,
+      P->chebd, P->m, chunks, ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2),
+      ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p, q, dx, dp, dq);
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
 template <typename T>
 int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq, bool gbar_term,
                bool fused, cudaStream_t s) {
+  if (fused) return launch_adj_final(P, p, q, dx, dp, dq, s);
   const Layout& L = P->lay;
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;

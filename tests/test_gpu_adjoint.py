@@ -44,6 +44,7 @@ CASES = {
     "ragged1501": lambda: (random_beam(1501, seed=3, gamma=15.0, spread=0.05, angle=0.02), 3, 37, 0.5),
     "cylinder4k": lambda: (make_beam("cylinder64k", N=4096), 6, 128, 0.5),
     "corehalo8k": lambda: (make_beam("corehalo16m", N=8192), 8, 256, 0.5),
+    "gauss3k_n5": lambda: (make_beam("gauss4k", N=3000), 5, 64, 0.5),  # a degree without specialised kernels
 }
 
 
