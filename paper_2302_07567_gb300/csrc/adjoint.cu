@@ -81,8 +81,12 @@ __global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __re
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   constexpr bool kSplit = std::is_same<T, float>::value;
+  using V4 = typename Vec4<T>::type;
   const int np1 = ch.np1;
-  const int stride = 3 * np1 + 6;
+  // per particle: the three 1-D bases, then (w^E, w^B) at a 4-aligned offset
+  // as two 4-vectors (two vector loads in the inner loop)
+  const int boff = (3 * np1 + 3) & ~3;
+  const int stride = boff + 8;
   const int64_t leaf = ((int64_t)1 << kappa) + blockIdx.x;
   const int64_t st = nstart[leaf], cnt = ncount[leaf];
   const NodeGeo g = geo[leaf];
@@ -114,8 +118,11 @@ __global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __re
         rel[0] += l.x; rel[1] += l.y; rel[2] += l.z;
       }
       for (int k = 0; k < 3; ++k) bary_basis<T>(rel[k] * invh[k], deg[k], ch, row + k * np1);
-      row[3 * np1 + 0] = e.x; row[3 * np1 + 1] = e.y; row[3 * np1 + 2] = e.z;
-      row[3 * np1 + 3] = b.x; row[3 * np1 + 4] = b.y; row[3 * np1 + 5] = b.z;
+      V4 w0, w1;
+      w0.x = e.x; w0.y = e.y; w0.z = e.z; w0.w = b.x;
+      w1.x = b.y; w1.y = b.z; w1.z = T(0); w1.w = T(0);
+      *reinterpret_cast<V4*>(row + boff) = w0;
+      *reinterpret_cast<V4*>(row + boff + 4) = w1;
     }
     __syncthreads();
     const int nj = (int)min64(blockDim.x, cnt - base);
@@ -129,8 +136,13 @@ __global__ void __launch_bounds__(256) k_l2pt(const typename Vec4<T>::type* __re
         for (int jj = j0; jj < j1; ++jj) {
           const T* r = sm + (size_t)jj * stride;
           const T wgt = r[nu1[v]] * r[np1 + nu2[v]] * r[2 * np1 + nu3[v]];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) part[c] += wgt * r[3 * np1 + c];
+          const V4 w0 = *reinterpret_cast<const V4*>(r + boff), w1 = *reinterpret_cast<const V4*>(r + boff + 4);
+          part[0] += wgt * w0.x;
+          part[1] += wgt * w0.y;
+          part[2] += wgt * w0.z;
+          part[3] += wgt * w0.w;
+          part[4] += wgt * w1.x;
+          part[5] += wgt * w1.y;
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) kahan_add(acc[v][c], cmp[v][c], part[c]);
@@ -1441,7 +1453,7 @@ int launch_l2pt(fmm_plan_s* P, cudaStream_t s) {
     if (int rc = set_smem(k_l2pt<T, NV>)) return rc;
     attr = true;
   }
-  const size_t smem = (size_t)256 * (3 * P->np1 + 6) * sizeof(T);
+  const size_t smem = (size_t)256 * (((3 * P->np1 + 3) & ~3) + 8) * sizeof(T);
   using V4 = typename Vec4<T>::type;
   k_l2pt<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pl), ws_ptr<V4>(P, L.wle),
                                                         ws_ptr<V4>(P, L.wlb), ws_ptr<int64_t>(P, L.nstart),

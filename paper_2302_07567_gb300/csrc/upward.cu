@@ -111,8 +111,12 @@ __global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __res
                                              T* __restrict__ M) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  using V4 = typename Vec4<T>::type;
   const int np1 = ch.np1;
-  const int stride = 3 * np1 + 4;
+  // per particle: the three 1-D bases, then (a, b~) at a 4-aligned offset
+  // (one vector load in the inner loop)
+  const int boff = (3 * np1 + 3) & ~3;
+  const int stride = boff + 4;
   const int64_t leaf = ((int64_t)1 << kappa) + blockIdx.x;
   const int64_t st = nstart[leaf], cnt = ncount[leaf];
   const NodeGeo g = geo[leaf];
@@ -140,10 +144,9 @@ __global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __res
       const typename Vec4<T>::type u = px[st + j], w = pb[st + j];
       const T rel[3] = {u.x, u.y, u.z};
       for (int k = 0; k < 3; ++k) bary_basis<T>(rel[k] * invh[k], deg[k], ch, row + k * np1);
-      row[3 * np1 + 0] = u.w;
-      row[3 * np1 + 1] = w.x;
-      row[3 * np1 + 2] = w.y;
-      row[3 * np1 + 3] = w.z;
+      V4 mass;
+      mass.x = u.w; mass.y = w.x; mass.z = w.y; mass.w = w.z;
+      *reinterpret_cast<V4*>(row + boff) = mass;
     }
     __syncthreads();
     const int nj = (int)min64(blockDim.x, cnt - base);
@@ -157,8 +160,11 @@ __global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __res
         for (int jj = j0; jj < j1; ++jj) {
           const T* r = sm + (size_t)jj * stride;
           const T wgt = r[nu1[v]] * r[np1 + nu2[v]] * r[2 * np1 + nu3[v]];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) part[c] += wgt * r[3 * np1 + c];
+          const V4 ms = *reinterpret_cast<const V4*>(r + boff);
+          part[0] += wgt * ms.x;
+          part[1] += wgt * ms.y;
+          part[2] += wgt * ms.z;
+          part[3] += wgt * ms.w;
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) kahan_add(acc[v][c], cmp[v][c], part[c]);
@@ -206,7 +212,7 @@ __global__ void k_srctab(const T* __restrict__ M, const NodeGeo* __restrict__ ge
 template <typename T, int NV>
 int launch_p2m(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
-  const size_t smem = (size_t)256 * (3 * P->np1 + 4) * sizeof(T);
+  const size_t smem = (size_t)256 * (((3 * P->np1 + 3) & ~3) + 4) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m<T, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
