@@ -336,7 +336,9 @@ int run_m2l(fmm_plan_s* P, cudaStream_t s) {
     switch (P->np1) {
       case 3: return launch_fast<3, 3, 1>(P, s);
       case 5: return launch_fast<5, 5, 1>(P, s);
-      case 7: return launch_fast<7, 4, 2>(P, s);
+      // 2 threads per (mu1, mu2), 4 mu3 chunks per cluster: 0.132 ms against
+      // 0.140 for (4, 2) at 2^9 leaves
+      case 7: return launch_fast<7, 2, 4>(P, s);
       case 9: return launch_fast<9, 3, 3>(P, s);
       default: break;
     }
