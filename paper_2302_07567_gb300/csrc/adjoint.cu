@@ -26,9 +26,11 @@
 //
 // Buffers: W and Lambda have their own, so the forward's multipoles and
 // cumulative locals survive the adjoint (a second adjoint call reuses them),
-// and the target-side kernel runs on the caller's stream while the source
-// side's far field (L2P^T, L2L^T, M2L^T, M2M^T) runs on the plan's side
-// stream.
+// and the near field (FP32: both roles of every pair in k_adj_near; FP64 and
+// the gbar term: the target side in k_adj_target) runs on the caller's
+// stream while the source side's far field (L2P^T, L2L^T, M2L^T, M2M^T) runs
+// on the plan's side stream.  After both, k_adj_final (FP32) or k_adj_source
+// adds the source-side far field and applies the chain rule.
 #include <type_traits>
 
 #include "common.cuh"
