@@ -125,7 +125,10 @@ int fmm_plan_set_workspace(fmm_plan_t plan, void* device_ptr, size_t bytes);
  *   E, B  device, [N,3]; float64 for FMM_FP64 plans, float32 for FMM_FP32 plans
  * Rows of E and B follow the input order.  The call queues work on `stream`,
  * waits once on it after the traversal (to read the list sizes and the device
- * error flags) and returns; the remaining kernels may still be running.
+ * error flags) and returns; the remaining kernels may still be running.  In
+ * FP32 plans part of the work (M2L, L2L) runs on a second stream the plan
+ * owns, beside the near field; the call joins it into `stream`, so work
+ * queued later on `stream` is ordered after all of it.
  * On FMM_EOVERFLOW / FMM_ENONFINITE nothing is written to E and B. */
 int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q,
               void* E, void* B, void* stream);
@@ -155,11 +158,14 @@ typedef struct fmm_stats {
   /* stage times of the last calls in ms (FMM_TIMING only, else 0):
      forward: 0 setup, 1 tree, 2 upward pass, 3 traversal with the ordering
      of the lists, 4 the host read of the list sizes, 5 M2L, 6 L2L,
-     7 P2P+L2P, 13 whole forward;  adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T,
-     11 target-side particle kernel (near + far), 12 source-side particle kernel
-     (near + far + chain rule), 14 whole adjoint, 15 source-major lists and any
-     recomputation */
-  double stage_ms[16];
+     7 P2P+L2P (FP32: the near-field P2P, which runs beside M2L and L2L),
+     16 FP32: L2P and the output after both, 13 whole forward;
+     adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T, 11 near-field particle
+     kernel (FP32: both roles; else the target side with its far field),
+     12 source side (FP32: far field and chain rule; else near + far + chain
+     rule), 14 whole adjoint, 15 source-major lists and any recomputation;
+     17 unused */
+  double stage_ms[18];
 } fmm_stats;
 
 /* Copy the plan's dimensions, list sizes and stage times (synchronises the

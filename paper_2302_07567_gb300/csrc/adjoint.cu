@@ -1319,26 +1319,7 @@ constexpr int kFinalThreads = 128;
 template <int NP1>
 __device__ __forceinline__ void basis_deriv_n(float t, bool deg, const Cheb& ch, const ChebD& cd, float (&l)[NP1],
                                               float (&dl)[NP1]) {
-  int hit = deg ? 0 : -1;
-  if (!deg) {
-#pragma unroll
-    for (int k = 0; k < NP1; ++k)
-      if (hit < 0 && fabsf(t - (float)ch.t[k]) <= 1e-30f) hit = k;
-  }
-  if (hit >= 0) {
-#pragma unroll
-    for (int k = 0; k < NP1; ++k) l[k] = (k == hit) ? 1.f : 0.f;
-  } else {
-    float sum = 0.f;
-#pragma unroll
-    for (int k = 0; k < NP1; ++k) {
-      l[k] = (float)ch.w[k] / (t - (float)ch.t[k]);
-      sum += l[k];
-    }
-    const float inv = 1.f / sum;
-#pragma unroll
-    for (int k = 0; k < NP1; ++k) l[k] *= inv;
-  }
+  bary_basis_n<NP1>(t, deg, ch, l);
 #pragma unroll
   for (int k = 0; k < NP1; ++k) {
     float acc = 0.f;

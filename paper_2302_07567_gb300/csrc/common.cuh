@@ -121,13 +121,14 @@ struct fmm_plan_s {
   int64_t p2p_count = 0, m2l_count = 0;
   double gbar = 0.0, lunit = 1.0, munit = 1.0;
   cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[18] = {};
+  cudaEvent_t ev[20] = {};
   bool ev_made = false;
   cudaStream_t side = nullptr;    // second stream for independent branches (higher priority)
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* hpin = nullptr;           // pinned host copy of the counters and scalars after the traversal
   cudaEvent_t trav_ev = nullptr;  // recorded after that copy
-  double stage_ms[16] = {};
+  double stage_ms[18] = {};
+  bool split_fwd = false;  // the last forward ran the FP32 near field beside M2L and L2L
 };
 
 namespace fmm {
@@ -214,6 +215,32 @@ __device__ __forceinline__ void bary_basis(T t, bool degenerate, const Cheb& ch,
   for (int k = 0; k < np1; ++k) out[k] *= inv;
 }
 
+// bary_basis in FP32 with the points per axis fixed at compile time (the
+// same formula), so that callers keep the values in registers.
+template <int NP1>
+__device__ __forceinline__ void bary_basis_n(float t, bool degenerate, const Cheb& ch, float (&out)[NP1]) {
+  int hit = degenerate ? 0 : -1;
+  if (!degenerate) {
+#pragma unroll
+    for (int k = 0; k < NP1; ++k)
+      if (hit < 0 && fabsf(t - (float)ch.t[k]) <= 1e-30f) hit = k;
+  }
+  if (hit >= 0) {
+#pragma unroll
+    for (int k = 0; k < NP1; ++k) out[k] = (k == hit) ? 1.f : 0.f;
+    return;
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < NP1; ++k) {
+    out[k] = (float)ch.w[k] / (t - (float)ch.t[k]);
+    sum += out[k];
+  }
+  const float inv = 1.f / sum;
+#pragma unroll
+  for (int k = 0; k < NP1; ++k) out[k] *= inv;
+}
+
 // s + e = a + b exactly (Knuth's two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -284,8 +311,12 @@ int ensure_side(fmm_plan_s* P);
 // synchronises the stream, FMM_EBOUNDS on any violation
 int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
-int run_l2l(fmm_plan_s* P, cudaStream_t s);
+int run_l2l(fmm_plan_s* P, cudaStream_t s, bool per_level = false);
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);
+// FP32 forward split: near-field P2P into the adjoint's per-particle buffers
+// (free during the forward call), then L2P with the output transform
+int run_p2p_near(fmm_plan_s* P, cudaStream_t s);
+int run_l2p_far(fmm_plan_s* P, void* E, void* B, cudaStream_t s);
 int run_adjoint(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE,
                 const void* wB, double* dx, double* dp, double* dq, cudaStream_t s);
 // stable LSD radix sort of 64-bit keys with 32-bit values over bits

@@ -31,6 +31,7 @@
 // leaf's cumulative local field (Eq. 2.8), converts from stretched, scaled
 // units to SI (E_z / gbar, B_z * gbar, prefactors 1/(4 pi eps0) and 1/c0) and
 // writes the row of the particle's input index.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     const typename Vec4<T>::type* __restrict__ pb, const float4* __restrict__ pl,  // Vec4<T> rows
     const void* __restrict__ pdc_raw, const T* __restrict__ Lcum, Cheb ch, int m,
     const int32_t* __restrict__ perm, const double* __restrict__ scal, int groups, int chunks, T* __restrict__ Eout,
-    T* __restrict__ Bout) {
+    T* __restrict__ Bout, float4* __restrict__ near_out, float4* __restrict__ near_out2) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;  // hi + lo separations
   constexpr int kRow = kSplit ? 4 : 2;                      // V4 per staged source particle
@@ -78,7 +79,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     deg[d] = !(gt.h[d] > 0.0);
     invh[d] = deg[d] ? T(0) : (T)(1.0 / gt.h[d]);
   }
-  if (kappa > 0) {  // the leaf's cumulative local field, for L2P below
+  // near_out (FP32): near field only, written per particle in leaf order as
+  // (E'x, E'y, E'z, B'x) and (B'y, B'z, 0, 0) in near_out2; L2P and the
+  // output follow in k_l2p_far
+  const bool far = kappa > 0 && near_out == nullptr;
+  if (far) {  // the leaf's cumulative local field, for L2P below
     const T* Lt = Lcum + (size_t)t * 6 * m;
     for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
   }
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      if (valid[k] && kappa > 0) {  // far field: L2P from the cumulative local field of the leaf
+      if (valid[k] && far) {  // far field: L2P from the cumulative local field of the leaf
         T lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1];
         const T lof = kSplit ? T(1) : T(0);
         bary_basis<T>((ri[k][0] + lof * rl[k][0]) * invh[0], deg[0], ch, lx);
@@ -307,6 +312,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
     for (int k = 0; k < KPT; ++k) {
       if (grp != 0 || !valid[k]) continue;
       const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
+      if (near_out != nullptr) {
+        near_out[pos] = make_float4((float)acc[k][0], (float)acc[k][1], (float)acc[k][2], (float)acc[k][3]);
+        near_out2[pos] = make_float4((float)acc[k][4], (float)acc[k][5], 0.f, 0.f);
+        continue;
+      }
       const int64_t i = perm[pos];
       Eout[3 * i + 0] = (T)(kE * (double)acc[k][0]);
       Eout[3 * i + 1] = (T)(kE * (double)acc[k][1]);
@@ -318,8 +328,97 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
   }
 }
 
+// FP32 far field after the near-field-only P2P (which ran beside M2L and
+// L2L): L2P (Alg. 14, Eq. 2.8) from the leaf's cumulative local field, one
+// thread per particle of a leaf chunk of 128, the local field staged with
+// its six components side by side (two 16-byte shared loads per point); the
+// near field is added and the sum converted to SI and written to the
+// particle's input row as in k_p2p_l2p.  NP1 > 0 fixes the points per axis
+// at compile time (basis values in registers); 0 reads them from ch.
+constexpr int kFarThreads = 128;
+template <int NP1>
+__global__ void __launch_bounds__(kFarThreads) k_l2p_far(
+    const unsigned int* __restrict__ err, const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount,
+    int kappa, const NodeGeo* __restrict__ geo, const float4* __restrict__ px, const float4* __restrict__ pl,
+    const float* __restrict__ Lcum, Cheb ch, int m, int chunks, const float4* __restrict__ near,
+    const float4* __restrict__ near2, const int32_t* __restrict__ perm, const double* __restrict__ scal, float* __restrict__ Eout,
+    float* __restrict__ Bout) {
+  extern __shared__ float4 slc[];  // [m][2]: (L0, L1, L2, L3), (L4, L5, 0, 0)
+  if (*err) return;  // the traversal failed: nothing is written
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * kFarThreads;
+  const int64_t st = nstart[t], cnt = ncount[t];
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
+  const bool far = kappa > 0;
+  if (far) {
+    const float* Lt = Lcum + (size_t)t * 6 * m;
+    for (int o = threadIdx.x; o < m; o += blockDim.x) {
+      slc[2 * o] = make_float4(Lt[o], Lt[m + o], Lt[2 * m + o], Lt[3 * m + o]);
+      slc[2 * o + 1] = make_float4(Lt[4 * m + o], Lt[5 * m + o], 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  const int64_t j = c0 + threadIdx.x;
+  if (j >= cnt) return;
+  const int64_t pos = st + j;
+  float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (far) {
+    const NodeGeo g = geo[t];
+    const float4 u = px[pos], l = pl[pos];
+    const float xr[3] = {u.x + l.x, u.y + l.y, u.z + l.z};
+    constexpr int K = NP1 > 0 ? NP1 : kMaxNp1;
+    const int np1 = NP1 > 0 ? NP1 : ch.np1;
+    float lx[K], ly[K], lz[K];
+    float* lb[3] = {lx, ly, lz};
+    for (int d = 0; d < 3; ++d) {
+      const bool deg = !(g.h[d] > 0.0);
+      const float tt = deg ? 0.f : xr[d] * (float)(1.0 / g.h[d]);
+      if constexpr (NP1 > 0) {
+        if (d == 0) bary_basis_n<K>(tt, deg, ch, lx);
+        else if (d == 1) bary_basis_n<K>(tt, deg, ch, ly);
+        else bary_basis_n<K>(tt, deg, ch, lz);
+      } else {
+        bary_basis<float>(tt, deg, ch, lb[d]);
+      }
+    }
+    int mu = 0;
+    for (int a3 = 0; a3 < np1; ++a3) {
+      for (int a2 = 0; a2 < np1; ++a2) {
+        const float w = lz[a3] * ly[a2];
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;
+#pragma unroll
+        for (int a1 = 0; a1 < (NP1 > 0 ? NP1 : np1); ++a1, ++mu) {
+          const float4 A = slc[2 * mu], Bv = slc[2 * mu + 1];
+          g0 += lx[a1] * A.x;
+          g1 += lx[a1] * A.y;
+          g2 += lx[a1] * A.z;
+          g3 += lx[a1] * A.w;
+          g4 += lx[a1] * Bv.x;
+          g5 += lx[a1] * Bv.y;
+        }
+        f[0] += w * g0;
+        f[1] += w * g1;
+        f[2] += w * g2;
+        f[3] += w * g3;
+        f[4] += w * g4;
+        f[5] += w * g5;
+      }
+    }
+  }
+  const float4 n0 = near[pos], n1 = near2[pos];
+  const double gbar = scal[0], kE = scal[4], kB = scal[5];
+  const int64_t i = perm[pos];
+  Eout[3 * i + 0] = (float)(kE * (double)(n0.x + f[0]));
+  Eout[3 * i + 1] = (float)(kE * (double)(n0.y + f[1]));
+  Eout[3 * i + 2] = (float)(kE * (double)(n0.z + f[2]) / gbar);
+  Bout[3 * i + 0] = (float)(kB * (double)(n0.w + f[3]));
+  Bout[3 * i + 1] = (float)(kB * (double)(n1.x + f[4]));
+  Bout[3 * i + 2] = (float)(kB * (double)(n1.y + f[5]) * gbar);
+}
+
 template <typename T, int KPT, bool POLY>
-int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
+int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s, float4* near_out = nullptr,
+           float4* near_out2 = nullptr) {
   const Layout& L = P->lay;
   int NT, groups, chunks;
   particle_shape(P->leaf, KPT, &NT, &groups, &chunks);
@@ -339,7 +438,7 @@ int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb), ws_ptr<float4>(P, L.pl),
       P->ws + L.p2p_dc, ws_ptr<T>(P, L.local), P->cheb, P->m, ws_ptr<int32_t>(P, L.perm),
-      ws_ptr<double>(P, L.scal), groups, chunks, static_cast<T*>(E), static_cast<T*>(B));
+      ws_ptr<double>(P, L.scal), groups, chunks, static_cast<T*>(E), static_cast<T*>(B), near_out, near_out2);
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -357,6 +456,37 @@ int p2p_t(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
 
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
   return P->precision == FMM_FP32 ? p2p_t<float>(P, E, B, s) : p2p_t<double>(P, E, B, s);
+}
+
+int run_p2p_near(fmm_plan_s* P, cudaStream_t s) {
+  if (P->precision != FMM_FP32) return FMM_EINVAL;
+  return launch<float, 1, false>(P, nullptr, nullptr, s, ws_ptr<float4>(P, P->lay.adj_part),
+                                 ws_ptr<float4>(P, P->lay.adj_part2));
+}
+
+int run_l2p_far(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
+  if (P->precision != FMM_FP32) return FMM_EINVAL;
+  const Layout& L = P->lay;
+  const int64_t most = *std::max_element(P->node_count.begin() + P->nleaves, P->node_count.end());
+  const int chunks = (int)div_up(most, kFarThreads);
+  const size_t smem = sizeof(float4) * 2 * P->m;
+  auto kern = k_l2p_far<0>;
+  switch (P->np1) {
+    case 3: kern = k_l2p_far<3>; break;
+    case 5: kern = k_l2p_far<5>; break;
+    case 7: kern = k_l2p_far<7>; break;
+    case 9: kern = k_l2p_far<9>; break;
+    default: break;
+  }
+  FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)(P->nleaves * chunks), kFarThreads, smem, s>>>(
+      &ws_ptr<Counters>(P, L.counters)->err, ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa,
+      ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pl), ws_ptr<float>(P, L.local),
+      P->cheb, P->m, chunks, ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2), ws_ptr<int32_t>(P, L.perm),
+      ws_ptr<double>(P, L.scal),
+      static_cast<float*>(E), static_cast<float*>(B));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
 }
 
 }  // namespace fmm

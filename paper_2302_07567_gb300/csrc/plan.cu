@@ -335,12 +335,38 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   }
   if ((rc = record(P, 4, s)) != FMM_OK) return rc;
   if ((rc = record(P, 5, s)) != FMM_OK) return rc;
-  if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
-  if ((rc = record(P, 6, s)) != FMM_OK) return rc;
-  if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
-  if ((rc = record(P, 7, s)) != FMM_OK) return rc;
-  if ((rc = run_p2p_l2p(P, E, B, s)) != FMM_OK) return rc;
-  if ((rc = record(P, 8, s)) != FMM_OK) return rc;
+  // FP32: the near-field P2P needs only the lists, so it runs on the
+  // caller's stream while M2L and L2L (launched per level, as a cooperative
+  // launch would wait for the P2P kernel) run on the plan's high-priority
+  // side stream; L2P and the output follow when both are done.  FP64 and the
+  // polynomial test kernel keep the fused P2P + L2P after M2L and L2L.
+  const bool split = P->precision == FMM_FP32 && !(P->flags & FMM_TEST_POLY_KERNEL) && P->kappa > 0;
+  if (split) {
+    if ((rc = ensure_side(P)) != FMM_OK) return rc;
+    cudaStream_t t = P->side;
+    FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
+    if ((rc = record(P, 5, t)) != FMM_OK) return rc;
+    if ((rc = run_m2l(P, t)) != FMM_OK) return rc;
+    if ((rc = record(P, 6, t)) != FMM_OK) return rc;
+    if ((rc = run_l2l(P, t, true)) != FMM_OK) return rc;
+    if ((rc = record(P, 7, t)) != FMM_OK) return rc;
+    FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
+    if ((rc = run_p2p_near(P, s)) != FMM_OK) return rc;
+    if ((rc = record(P, 18, s)) != FMM_OK) return rc;
+    FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
+    if ((rc = record(P, 19, s)) != FMM_OK) return rc;
+    if ((rc = run_l2p_far(P, E, B, s)) != FMM_OK) return rc;
+    if ((rc = record(P, 8, s)) != FMM_OK) return rc;
+  } else {
+    if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
+    if ((rc = record(P, 6, s)) != FMM_OK) return rc;
+    if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
+    if ((rc = record(P, 7, s)) != FMM_OK) return rc;
+    if ((rc = run_p2p_l2p(P, E, B, s)) != FMM_OK) return rc;
+    if ((rc = record(P, 8, s)) != FMM_OK) return rc;
+  }
+  P->split_fwd = split;
   if (!wait_first && (rc = read_back()) != FMM_OK) return rc;
   P->have_forward = true;
   P->transposed_valid = false;
@@ -405,7 +431,13 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[4] = el(3, 5);   // copy of the list sizes to the host
     P->stage_ms[5] = el(5, 6);
     P->stage_ms[6] = el(6, 7);
-    P->stage_ms[7] = el(7, 8);
+    if (P->split_fwd) {
+      P->stage_ms[7] = el(5, 18);   // near-field P2P beside M2L and L2L
+      P->stage_ms[16] = el(19, 8);  // L2P and the output
+    } else {
+      P->stage_ms[7] = el(7, 8);
+      P->stage_ms[16] = 0.0;
+    }
     P->stage_ms[13] = el(0, 8);
     if (P->flags & 0x100u) {  // adjoint events recorded
       // the target side runs on the caller's stream while L2P^T .. M2M^T run
@@ -423,7 +455,7 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
       P->stage_ms[14] = el(15, 14);  // whole adjoint call
       P->stage_ms[15] = el(15, 16);  // source-major lists, recompute if asked, weights
     }
-    for (int k = 0; k < 16; ++k) out->stage_ms[k] = P->stage_ms[k];
+    for (int k = 0; k < 18; ++k) out->stage_ms[k] = P->stage_ms[k];
   }
   return FMM_OK;
 }

@@ -286,9 +286,9 @@ int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
                                   : upward_t<double>(P, s, xfer_cap, per_level);
 }
 
-int run_l2l(fmm_plan_s* P, cudaStream_t s) {
-  return P->precision == FMM_FP32 ? run_transfer<float, 6, false>(P, ws_ptr<float>(P, P->lay.local), s)
-                                  : run_transfer<double, 6, false>(P, ws_ptr<double>(P, P->lay.local), s);
+int run_l2l(fmm_plan_s* P, cudaStream_t s, bool per_level) {
+  return P->precision == FMM_FP32 ? run_transfer<float, 6, false>(P, ws_ptr<float>(P, P->lay.local), s, 4, per_level)
+                                  : run_transfer<double, 6, false>(P, ws_ptr<double>(P, P->lay.local), s, 4, per_level);
 }
 
 }  // namespace fmm

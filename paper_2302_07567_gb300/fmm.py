@@ -27,7 +27,8 @@ FMM_FP64, FMM_FP32 = 0, 1
 FMM_RECOMPUTE, FMM_BOUNDS_CHECK, FMM_TIMING, FMM_SIZE_AWARE, FMM_TEST_POLY_KERNEL, FMM_GBAR_TERM = 1, 2, 4, 8, 16, 32
 EXPORT = dict(gbar=0, perm=1, nodes=2, bbox=3, axis=4, p2p=5, m2l=6, multipole=7, local=8)
 STAGES = ["setup", "tree", "upward", "traversal", "host_wait", "m2l", "l2l", "p2p_l2p",
-          "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_near", "adj_source", "total", "adj_total", "adj_lists"]
+          "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_near", "adj_source", "total", "adj_total", "adj_lists",
+          "l2p", "unused"]
 
 _lib = None
 
@@ -49,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
                 ("p2p_interactions", ctypes.c_double), ("m2l_interactions", ctypes.c_double),
                 ("cap_p2p", ctypes.c_int64), ("cap_m2l", ctypes.c_int64), ("cap_frontier", ctypes.c_int64),
-                ("stage_ms", ctypes.c_double * 16)]
+                ("stage_ms", ctypes.c_double * 18)]
 
 
 def lib():
@@ -205,7 +206,7 @@ class Plan:
         if rc != FMM_OK:
             raise FMMError(rc, "fmm_plan_stats")
         d = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "stage_ms"}
-        d["stage_ms"] = {STAGES[k]: s.stage_ms[k] for k in range(16)}
+        d["stage_ms"] = {STAGES[k]: s.stage_ms[k] for k in range(18)}
         return d
 
     def export(self, what: str) -> np.ndarray:
