@@ -51,7 +51,7 @@ HOT_SPLIT = {"adj_near": (46.0, "p2p_interactions"), "adj_source": (67.0, "p2p_i
 # fwd+adj step, from one `ncu --set full` capture per kernel (summary and
 # command in profiles/hot_kernels_cylinder64k.md).  Valid only while the
 # kernel is unchanged since that capture; reported for that workload only.
-TRAFFIC_CYL64K = {"m2l": 2674688, "adj_m2lt": 3963392, "adj_near": 9885696 + 15360}
+TRAFFIC_CYL64K = {"m2l": 2674688, "adj_m2lt": 3963392, "adj_near": 9885696 + 15360, "p2p_l2p": 3494144}
 CONCURRENT = ("adj_near", "adj_m2lt")  # stages that overlap each other (two streams)
 CONCURRENT_FP32_FWD = ("p2p_l2p", "m2l")  # FP32 forward: near-field P2P beside M2L and L2L
 SMS = 152          # GB300 streaming multiprocessors
