@@ -961,9 +961,8 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
 
 // Source side: near field over the source-major P2P list, far field from the
 // pushed-down Lambda, plus the target-side part; then the chain rule to
-// physical (x, p, q), written in input order.  With `fused` the near field of
-// both roles is already in gtarget = (dL/dx', dL/da') and g2 = (dL/db~', 0)
-// (k_adj_near) and the list walk is skipped.
+// physical (x, p, q), written in input order (FP64, and FP32 with the gbar
+// term; the FP32 adjoint otherwise uses k_adj_near and k_adj_final).
 template <typename T, int KPT>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift,
@@ -974,8 +973,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
     const typename Vec4<T>::type* __restrict__ wlb, const T* __restrict__ Lam, Cheb ch, ChebD cd, int m,
     const typename Vec4<T>::type* __restrict__ gtarget, const int32_t* __restrict__ perm,
     const double* __restrict__ scal, const double* __restrict__ p, const double* __restrict__ q, int groups,
-    int chunks, int gbar_term, int fused, const typename Vec4<T>::type* __restrict__ g2,
-    double* __restrict__ dx_out, double* __restrict__ dp_out, double* __restrict__ dq_out) {
+    int chunks, int gbar_term, double* __restrict__ dx_out, double* __restrict__ dp_out,
+    double* __restrict__ dq_out) {
   using V4 = typename Vec4<T>::type;
   constexpr bool kSplit = std::is_same<T, float>::value;
   constexpr int kRow = kSplit ? 4 : 3;
@@ -990,7 +989,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
   if (c0 >= cnt) return;  // the leaf is smaller than this chunk
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const NodeGeo gs = geo[s];
-  const int b = fused ? 0 : off[s], e = fused ? 0 : off[s + 1];
+  const int b = off[s], e = off[s + 1];
   const int np1 = ch.np1;
   T invh[3];
   bool deg[3];
@@ -1232,14 +1231,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 1) k_adj_source(
       if (grp != 0 || !valid[k]) continue;
       const int64_t pos = st + pass0 + lt + (int64_t)k * NT;
       const V4 gt = gtarget[pos];
-      V4 gs;  // the fused near field's dL/db~' (zero otherwise)
-      gs.x = gs.y = gs.z = gs.w = T(0);
-      if (fused) gs = g2[pos];
-      const double ga = fused ? (double)gt.w : 0.0;
       // internal (a', b~', x') -> physical (a, b, x)
-      const double dA = ((double)acc[k][0] + ga) / mu_u;
-      const double dB[3] = {((double)acc[k][1] + (double)gs.x) / (gbar * mu_u),
-                            ((double)acc[k][2] + (double)gs.y) / (gbar * mu_u), ((double)acc[k][3] + (double)gs.z) / mu_u};
+      const double dA = (double)acc[k][0] / mu_u;
+      const double dB[3] = {(double)acc[k][1] / (gbar * mu_u), (double)acc[k][2] / (gbar * mu_u),
+                            (double)acc[k][3] / mu_u};
       const double dX[3] = {((double)acc[k][4] + (double)gt.x) / ell, ((double)acc[k][5] + (double)gt.y) / ell,
                             gbar * ((double)acc[k][6] + (double)gt.z) / ell};
       const int64_t i = perm[pos];
@@ -1598,7 +1593,7 @@ int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, doub
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
       ws_ptr<V4>(P, L.pl), P->ws + L.p2p_sdc, ws_ptr<V4>(P, L.wle), ws_ptr<V4>(P, L.wlb), ws_ptr<T>(P, L.lbuf),
       P->cheb, P->chebd, P->m, ws_ptr<V4>(P, L.adj_part), ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), p,
-      q, groups, chunks, gbar_term ? 1 : 0, fused ? 1 : 0, ws_ptr<V4>(P, L.adj_part2), dx, dp, dq);
+      q, groups, chunks, gbar_term ? 1 : 0, dx, dp, dq);
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -1703,6 +1698,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   // FP32 without the gbar term: both near-field roles in one kernel
   const bool fused = std::is_same<T, float>::value && !gb;
   if (fused) rc = launch_adj_near(P, s);
+  else if constexpr (std::is_same<T, float>::value) rc = launch_adj_target<T, true>(P, s);  // FP32: only with the gbar term
   else rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
   if (rc != FMM_OK) return rc;
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
