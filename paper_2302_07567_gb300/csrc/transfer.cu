@@ -231,9 +231,12 @@ int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm, boo
   const int64_t blocks = (int64_t)std::min(per_sm, cap_per_sm) * sms;
   const T* tm = ws_ptr<T>(P, P->lay.tmat);
   if (per_level) {  // one ordinary launch per level (no grid barrier is reached)
+    // with no grid barrier the deep levels take up to 8 blocks per SM
+    // (measured at 2^9 leaves: 1.2% faster step than 4, 2 slower)
+    const int64_t lblocks = (int64_t)std::min(per_sm, 8) * sms;
     for (int i = 0; i < P->kappa; ++i) {
       const int level = UP ? P->kappa - 1 - i : i;
-      const int grid = (int)std::min<int64_t>(blocks, ((int64_t)1 << level) * nc);
+      const int grid = (int)std::min<int64_t>(lblocks, ((int64_t)1 << level) * nc);
       kern<<<grid, 256, 0, s>>>(level, level, nc, tm, buf);
       FMM_LAUNCH_CHECK();
     }
