@@ -171,6 +171,8 @@ typedef struct fmm_stats {
 /* Copy the plan's dimensions, list sizes and stage times (synchronises the
  * stream of the last call when FMM_TIMING is set). */
 int fmm_plan_stats(fmm_plan_t plan, fmm_stats* out);
+/* sizeof(fmm_stats) in this build, for bindings to check their layout. */
+size_t fmm_stats_bytes(void);
 
 /* Inspection of intermediate results of the last fmm_field, copied to host
  * memory (synchronous).  `bytes` must be at least the size given below, with

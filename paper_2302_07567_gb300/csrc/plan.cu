@@ -189,6 +189,8 @@ extern "C" {
 
 int fmm_version(void) { return 1; }
 
+size_t fmm_stats_bytes(void) { return sizeof(fmm_stats); }
+
 int64_t fmm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 const char* fmm_last_cuda_error(void) { return g_last_cuda_error.c_str(); }

@@ -76,6 +76,7 @@ def lib():
         "fmm_strerror": (ctypes.c_char_p, [I32]),
         "fmm_last_cuda_error": (ctypes.c_char_p, []),
         "fmm_version": (I32, []),
+        "fmm_stats_bytes": (ctypes.c_size_t, []),
         "fmm_kernel_launches": (I64, []),
         "fmm_gamma_bar_noalloc": (I32, [P, I64, P, P]),
     }
@@ -83,6 +84,9 @@ def lib():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
+    if L.fmm_stats_bytes() != ctypes.sizeof(Stats):
+        raise RuntimeError(f"fmm_stats layout mismatch: library {L.fmm_stats_bytes()} bytes, "
+                           f"binding {ctypes.sizeof(Stats)}")
     _lib = L
     return L
 

@@ -45,6 +45,12 @@ def test_host_side_argument_checks(libpath):
     for N, n, leaf, eta, prec in bad:
         assert lib.fmm_plan_create(ctypes.byref(h), N, n, leaf, eta, prec, 0) == 1
     assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 0x100) == 1  # unknown flag bit
+    assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 64) == 1  # unknown flag bit
+    assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 16) == 1  # the test kernel is FP64 only
+    lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
+    for flags in (32, 32 | 8 | 2 | 1):  # gbar term, with size-aware lists, bounds checks, recompute
+        assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, flags) == 0
+        lib.fmm_plan_destroy(h)
     assert lib.fmm_plan_create(ctypes.byref(h), 4096, 4, 64, 0.5, 1, 0) == 0
     lib.fmm_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     nb = ctypes.c_size_t()
@@ -55,3 +61,14 @@ def test_host_side_argument_checks(libpath):
     lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.fmm_plan_destroy(h)
     assert lib.fmm_strerror(3) == b"interaction-list capacity exceeded"
+
+
+def test_stats_layout_matches_the_binding(libpath):
+    """The binding's ctypes fmm_stats has the size of the library's struct,
+    and one stage name per stage slot."""
+    from paper_2302_07567_gb300 import fmm
+    lib = ctypes.CDLL(libpath)
+    lib.fmm_stats_bytes.restype = ctypes.c_size_t
+    assert lib.fmm_stats_bytes() == ctypes.sizeof(fmm.Stats)
+    slots = dict(fmm.Stats._fields_)["stage_ms"]._length_
+    assert slots == len(fmm.STAGES) == 18
