@@ -223,9 +223,12 @@ int64_t fmm_kernel_launches(void);
  * until exit).
  *   p     device [N,3] float64 momenta;  gbar  device double[1] output
  *   N     1 .. FMM_NOALLOC_MAX_N, else FMM_EINVAL (nothing is launched)
- * The first call on a device looks up the scratch address (cudaGetSymbolAddress)
- * and should come before any stream capture.  All calls share the scratch array:
- * calls whose work overlaps on the GPU race on it. */
+ * The work runs on the device current in the calling thread, and `stream` must
+ * belong to that device (FMM_EINVAL otherwise).  The first call on a device looks
+ * up the scratch address (cudaGetSymbolAddress) and should come before any stream
+ * capture; a cudaDeviceReset invalidates that address, so do not call this entry
+ * point on a device after resetting it.  All calls share the scratch array: calls
+ * whose work overlaps on the GPU race on it. */
 #define FMM_NOALLOC_MAX_N 16777216
 int fmm_gamma_bar_noalloc(const double* p, int64_t N, double* gbar, void* stream);
 

@@ -1417,21 +1417,17 @@ __global__ void __launch_bounds__(kFinalThreads) k_adj_final(
 }
 
 // ---------------------------------------------------------------- launchers
+// Raise the kernel's dynamic shared-memory limit to what this launch needs.
 template <typename K>
-int set_smem(K kernel) {
-  FMM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  return FMM_OK;
+int set_smem(K* kernel, size_t smem) {
+  return smem_limit(kernel, (int)smem);
 }
 
 template <typename T, int NV>
 int launch_l2pt(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
-  static bool attr = false;
-  if (!attr) {
-    if (int rc = set_smem(k_l2pt<T, NV>)) return rc;
-    attr = true;
-  }
   const size_t smem = (size_t)256 * (((3 * P->np1 + 3) & ~3) + 8) * sizeof(T);
+  if (int rc = set_smem(k_l2pt<T, NV>, smem)) return rc;
   using V4 = typename Vec4<T>::type;
   k_l2pt<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pl), ws_ptr<V4>(P, L.wle),
                                                         ws_ptr<V4>(P, L.wlb), ws_ptr<int64_t>(P, L.nstart),
@@ -1459,12 +1455,8 @@ int l2pt(fmm_plan_s* P, cudaStream_t s) {
 template <typename T, int KPT, bool GB>
 int launch_adj_m2l(fmm_plan_s* P, int nt, cudaStream_t s) {
   const Layout& L = P->lay;
-  static bool attr = false;
-  if (!attr) {
-    if (int rc = set_smem(k_adj_m2l<T, KPT, GB>)) return rc;
-    attr = true;
-  }
   const size_t smem = (size_t)3 * P->m * sizeof(typename Vec4<T>::type);
+  if (int rc = set_smem(k_adj_m2l<T, KPT, GB>, smem)) return rc;
   unsigned grid = 0;
   if (int rc = resident_blocks(k_adj_m2l<T, KPT, GB>, nt, smem, P->C, &grid)) return rc;
   k_adj_m2l<T, KPT, GB><<<grid, nt, smem, s>>>(
@@ -1530,14 +1522,12 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
   const size_t smem = stage_bytes<T>(kSplit ? 4 : 2, 1, GB ? 8 : 6, groups, NT) + sizeof(T) * 6 * P->m;
-  static bool attr = false;
-  if (!attr) { if (int rc = set_smem(k_adj_target<T, 1, GB>)) return rc; attr = true; }
+  if (int rc = set_smem(k_adj_target<T, 1, GB>, smem)) return rc;
   // beside the source side's far field (side stream) the target side keeps
   // to half of the SMs' block slots, so the other branch finds room
   if (P->kappa > 0) {
-    int dev = 0, sms = 0;
-    FMM_CUDA_TRY(cudaGetDevice(&dev));
-    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int sms = 0;
+    if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
   }
   k_adj_target<T, 1, GB><<<grid, nt, smem, s>>>(
@@ -1564,7 +1554,7 @@ int launch_adj_final(fmm_plan_s* P, const double* p, const double* q, double* dx
     case 9: kern = k_adj_final<9>; break;
     default: break;
   }
-  FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc = smem_limit(kern, (int)smem)) return rc;
   kern<<<(unsigned)(P->nleaves * chunks), kFinalThreads, smem, s>>>(
       ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
       ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb), ws_ptr<float4>(P, L.pl), ws_ptr<float>(P, L.lbuf), P->cheb,
@@ -1586,8 +1576,7 @@ int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, doub
   const int nt = groups * NT;
   const unsigned grid = (unsigned)(P->nleaves * chunks);
   const size_t smem = stage_bytes<T>(kSplit ? 4 : 3, 1, 14, groups, NT) + sizeof(T) * 4 * P->m;
-  static bool attr = false;
-  if (!attr) { if (int rc = set_smem(k_adj_source<T, 1>)) return rc; attr = true; }
+  if (int rc = set_smem(k_adj_source<T, 1>, smem)) return rc;
   k_adj_source<T, 1><<<grid, nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p_src), ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
       ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<V4>(P, L.px), ws_ptr<V4>(P, L.pb),
@@ -1609,12 +1598,10 @@ int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
   const size_t smem = stage_bytes<float>(6, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;
-  static bool attr = false;
-  if (!attr) { if (int rc = set_smem(k_adj_near)) return rc; attr = true; }
+  if (int rc = set_smem(k_adj_near, smem)) return rc;
   if (P->kappa > 0) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
-    int dev = 0, sms = 0;
-    FMM_CUDA_TRY(cudaGetDevice(&dev));
-    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int sms = 0;
+    if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)3 * sms);
   }
   k_adj_near<<<grid, nt, smem, s>>>(
@@ -1687,11 +1674,11 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if ((rc = l2pt<T>(P, t)) != FMM_OK) return rc;
     // beside the particle kernel the transfers are launched once per level: a
     // cooperative launch would wait for the particle kernel to end
-    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, 4, true)) != FMM_OK) return rc;  // L2L^T
+    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, kLevelTransferCap, true)) != FMM_OK) return rc;  // L2L^T
     if ((rc = record(P, 11, t)) != FMM_OK) return rc;
     if ((rc = adj_m2l<T>(P, gb, t)) != FMM_OK) return rc;
     if ((rc = record(P, 12, t)) != FMM_OK) return rc;
-    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, 4, true)) != FMM_OK) return rc;  // M2M^T
+    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, kLevelTransferCap, true)) != FMM_OK) return rc;  // M2M^T
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
     FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
   }

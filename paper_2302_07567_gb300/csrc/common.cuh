@@ -41,6 +41,13 @@ enum : unsigned {
 // Blocks a cooperative traversal launch may use (scan partials reserved per list).
 constexpr int64_t kTravPartials = 4096;
 constexpr int kGbarBlocks = 512;  // most blocks of the dL/dgbar partial sums
+// Blocks per SM of the transfer launches (M2M, L2L and their transposes):
+// the cooperative launch over all levels takes at most 4 (more make its
+// grid-wide barriers dearer than the extra blocks help the deepest levels),
+// the per-level launches beside another kernel at most 8 (no grid barrier;
+// measured at 2^9 leaves: 1.2% faster step than 4, 2 slower).
+constexpr int kCoopTransferCap = 4;
+constexpr int kLevelTransferCap = 8;
 
 struct Counters {
   unsigned long long p2p_count;
@@ -257,15 +264,36 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   sum = t;
 }
 
+// Launch facts of kernels on the current device.  A kernel's attributes
+// (the raised dynamic shared-memory limit) and its occupancy belong to one
+// device context, so they are kept per (device, kernel) in tables guarded by
+// a mutex: plans on several devices of one process, or on several host
+// threads, each get their own.  Every function works on the device that is
+// current in the calling thread.
+int device_sms(int* sms);
+// Raise the kernel's dynamic shared-memory limit to at least `bytes` (once
+// per device and kernel).
+int smem_limit_raw(const void* kern, int bytes);
+// Resident blocks per SM of the kernel at `threads` threads and `smem`
+// dynamic shared bytes (computed once per device, kernel and shape).
+int blocks_per_sm_raw(const void* kern, int threads, size_t smem, int* per_sm);
+
+template <typename K>
+inline int smem_limit(K* kern, int bytes) {
+  return smem_limit_raw(reinterpret_cast<const void*>(kern), bytes);
+}
+template <typename K>
+inline int blocks_per_sm(K* kern, int threads, size_t smem, int* per_sm) {
+  return blocks_per_sm_raw(reinterpret_cast<const void*>(kern), threads, smem, per_sm);
+}
+
 // Blocks of a grid-stride launch of `kern`: as many as are resident at once
 // at `threads` threads and `smem` dynamic shared bytes, at most `items`.
 template <typename K>
-inline int resident_blocks(K kern, int threads, size_t smem, int64_t items, unsigned* grid) {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
-    return FMM_ECUDA;
+inline int resident_blocks(K* kern, int threads, size_t smem, int64_t items, unsigned* grid) {
+  int sms = 0, per_sm = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  if (int rc = blocks_per_sm(kern, threads, smem, &per_sm)) return rc;
   if (per_sm < 1) return FMM_EINVAL;
   *grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, items));
   return FMM_OK;
@@ -301,7 +329,7 @@ int run_setup(fmm_plan_s* P, const double* x, const double* p, const double* q, 
 int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s);
 int run_prep(fmm_plan_s* P, const double* x, const double* p, const double* q, cudaStream_t s);
 // P2M, M2M (at most xfer_cap blocks per SM in the transfer) and the M2L source table
-int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap = 4, bool per_level = false);
+int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap = kCoopTransferCap, bool per_level = false);
 // traversal and both target-major lists (sorted, CSR, centre offsets), one launch
 int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
@@ -331,7 +359,7 @@ int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, 
 // levels (see transfer.cu)
 int run_tmats(fmm_plan_s* P, cudaStream_t s);
 template <typename T, int NC, bool UP>
-int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm = 4, bool per_level = false);
+int run_transfer(fmm_plan_s* P, T* buf, cudaStream_t s, int max_blocks_per_sm, bool per_level);
 int64_t radix_tiles(int64_t n);
 int64_t scan_tmp_words(int64_t n);
 }  // namespace fmm

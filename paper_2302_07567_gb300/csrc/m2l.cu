@@ -300,11 +300,7 @@ template <typename T, int KPT, bool POLY>
 int launch(fmm_plan_s* P, int nt, cudaStream_t s) {
   const Layout& L = P->lay;
   const size_t smem = (size_t)2 * P->m * sizeof(typename Vec4<T>::type);
-  static bool attr_set = false;
-  if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l<T, KPT, POLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  if (int rc = smem_limit(k_m2l<T, KPT, POLY>, (int)smem)) return rc;
   unsigned grid = 0;
   if (int rc = resident_blocks(k_m2l<T, KPT, POLY>, nt, smem, P->C, &grid)) return rc;
   k_m2l<T, KPT, POLY><<<grid, nt, smem, s>>>(ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off),

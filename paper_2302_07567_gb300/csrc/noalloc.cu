@@ -75,10 +75,16 @@ __global__ void k_na_gbar(const double* __restrict__ sums, int64_t comp, int64_t
 }
 
 // Device address of the scratch array for the current device (looked up once).
-int scratch_address(double** out) {
+// The stream must belong to that device: the address is only valid there.
+int scratch_address(cudaStream_t s, double** out) {
   int dev = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNaMaxDevices) return FMM_EINVAL;
+  if (s != nullptr) {
+    int sdev = -1;
+    FMM_CUDA_TRY(cudaStreamGetDevice(s, &sdev));
+    if (sdev != dev) return FMM_EINVAL;
+  }
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (!g_na_addr[dev]) {
     void* ptr = nullptr;
@@ -95,10 +101,10 @@ int scratch_address(double** out) {
 extern "C" int fmm_gamma_bar_noalloc(const double* p, int64_t N, double* gbar, void* stream) {
   using namespace fmm;
   if (!p || !gbar || N < 1 || N > kNaMaxN) return FMM_EINVAL;
-  double* scratch = nullptr;
-  int rc = scratch_address(&scratch);
-  if (rc != FMM_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  int rc = scratch_address(s, &scratch);
+  if (rc != FMM_OK) return rc;
   // level 1 reads p (stride 3 between particles, 1 between components) into
   // region A; further levels alternate A <-> B until one sum per component is left
   double* region[2] = {scratch, scratch + kNaLevel1};

@@ -427,11 +427,7 @@ int launch(fmm_plan_s* P, void* E, void* B, cudaStream_t s, float4* near_out = n
   const size_t stage = std::max(sizeof(typename Vec4<T>::type) * row * nt,
                                 sizeof(T) * (size_t)(groups - 1) * KPT * 12 * NT);
   const size_t smem = stage + sizeof(T) * 6 * P->m;
-  static bool attr_set = false;
-  if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2p_l2p<T, KPT, POLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  if (int rc = smem_limit(k_p2p_l2p<T, KPT, POLY>, (int)smem)) return rc;
   k_p2p_l2p<T, KPT, POLY><<<(unsigned)(P->nleaves * chunks), nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1,
       &ws_ptr<Counters>(P, L.counters)->err, ws_ptr<int64_t>(P, L.nstart),
@@ -478,7 +474,7 @@ int run_l2p_far(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
     case 9: kern = k_l2p_far<9>; break;
     default: break;
   }
-  FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc = smem_limit(kern, (int)smem)) return rc;
   kern<<<(unsigned)(P->nleaves * chunks), kFarThreads, smem, s>>>(
       &ws_ptr<Counters>(P, L.counters)->err, ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa,
       ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pl), ws_ptr<float>(P, L.local),

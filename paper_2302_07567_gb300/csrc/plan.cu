@@ -2,7 +2,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -15,6 +18,56 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_cuda_error(cudaError_t e) {
   g_last_cuda_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+}
+
+namespace {
+
+std::mutex g_launch_mutex;
+std::map<int, int> g_sms;                                           // device -> SMs
+std::map<std::pair<int, const void*>, int> g_smem_limit;           // (device, kernel) -> raised limit
+std::map<std::tuple<int, const void*, int, size_t>, int> g_per_sm;  // (device, kernel, threads, smem)
+
+}  // namespace
+
+int device_sms(int* sms) {
+  int dev = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_launch_mutex);
+  auto it = g_sms.find(dev);
+  if (it == g_sms.end()) {
+    int v = 0;
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    it = g_sms.emplace(dev, v).first;
+  }
+  *sms = it->second;
+  return FMM_OK;
+}
+
+int smem_limit_raw(const void* kern, int bytes) {
+  int dev = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_launch_mutex);
+  int& cur = g_smem_limit[{dev, kern}];
+  if (cur < bytes) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    cur = bytes;
+  }
+  return FMM_OK;
+}
+
+int blocks_per_sm_raw(const void* kern, int threads, size_t smem, int* per_sm) {
+  int dev = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_launch_mutex);
+  const auto key = std::make_tuple(dev, kern, threads, smem);
+  auto it = g_per_sm.find(key);
+  if (it == g_per_sm.end()) {
+    int v = 0;
+    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem));
+    it = g_per_sm.emplace(key, v).first;
+  }
+  *per_sm = it->second;
+  return FMM_OK;
 }
 
 namespace {

@@ -300,14 +300,10 @@ int radix_sort_batched(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint3
   if (nt * nbatch > max_tiles) return FMM_EINVAL;
   const int passes = (end_bit - begin_bit + 7) / 8;
   if (nt <= kFusedTiles) {  // one cooperative launch for every pass
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-      int dev = 0;
-      FMM_CUDA_TRY(cudaGetDevice(&dev));
-      FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_coop, kSortThreads, 0));
-      if (per_sm < 1) return FMM_EINVAL;
-    }
+    int per_sm = 0, sms = 0;
+    if (int rc = device_sms(&sms)) return rc;
+    if (int rc = blocks_per_sm(k_radix_coop, kSortThreads, 0, &per_sm)) return rc;
+    if (per_sm < 1) return FMM_EINVAL;
     int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, nt * nbatch);
     void* args[] = {&keys, &keys_alt, &vals, &vals_alt, &stride, &nbatch, &n, &begin_bit, &end_bit,
                     (void*)&nt, &hist};

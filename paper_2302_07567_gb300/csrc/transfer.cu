@@ -215,28 +215,20 @@ __global__ void __launch_bounds__(256) k_transfer_np(int level_first, int level_
 
 template <typename T, int NP1, bool UP>
 int launch_np(fmm_plan_s* P, int nc, T* buf, cudaStream_t s, int cap_per_sm, bool per_level) {
-  static int per_sm = 0, sms = 0;
+  int per_sm = 0, sms = 0;
   auto kern = k_transfer_np<T, NP1, UP>;
-  if (per_sm == 0) {
-    int dev = 0;
-    FMM_CUDA_TRY(cudaGetDevice(&dev));
-    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-    if (per_sm < 1) return FMM_EINVAL;
-  }
-  // at most cap_per_sm (4 by default) blocks per SM: more make the grid-wide
-  // barriers dearer than the extra blocks help the deepest levels (measured
-  // at 2^9 leaves); a transfer beside another kernel takes fewer
+  if (int rc = device_sms(&sms)) return rc;
+  if (int rc = blocks_per_sm(kern, 256, 0, &per_sm)) return rc;
+  if (per_sm < 1) return FMM_EINVAL;
+  // at most cap_per_sm blocks per SM (kCoopTransferCap for the cooperative
+  // launch, kLevelTransferCap for the per-level launches)
   const int64_t most = ((int64_t)1 << (P->kappa - 1)) * nc;
   const int64_t blocks = (int64_t)std::min(per_sm, cap_per_sm) * sms;
   const T* tm = ws_ptr<T>(P, P->lay.tmat);
   if (per_level) {  // one ordinary launch per level (no grid barrier is reached)
-    // with no grid barrier the deep levels take up to 8 blocks per SM
-    // (measured at 2^9 leaves: 1.2% faster step than 4, 2 slower)
-    const int64_t lblocks = (int64_t)std::min(per_sm, 8) * sms;
     for (int i = 0; i < P->kappa; ++i) {
       const int level = UP ? P->kappa - 1 - i : i;
-      const int grid = (int)std::min<int64_t>(lblocks, ((int64_t)1 << level) * nc);
+      const int grid = (int)std::min<int64_t>(blocks, ((int64_t)1 << level) * nc);
       kern<<<grid, 256, 0, s>>>(level, level, nc, tm, buf);
       FMM_LAUNCH_CHECK();
     }
@@ -259,17 +251,11 @@ int launch_all(fmm_plan_s* P, T* buf, cudaStream_t s) {
   int group = NC;
   while (group > 1 && mats + (size_t)6 * group * P->m * sizeof(T) > budget) --group;
   const size_t smem = mats + (size_t)6 * group * P->m * sizeof(T);
-  static bool attr = false;
-  static int per_sm = 0, sms = 0;
+  int per_sm = 0, sms = 0;
   auto kern = k_transfer_all<T, NC, UP>;
-  if (!attr) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
-    int dev = 0;
-    FMM_CUDA_TRY(cudaGetDevice(&dev));
-    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    attr = true;
-  }
-  FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+  if (int rc = smem_limit(kern, (int)budget)) return rc;
+  if (int rc = device_sms(&sms)) return rc;
+  if (int rc = blocks_per_sm(kern, 256, smem, &per_sm)) return rc;
   if (per_sm < 1) return FMM_EINVAL;
   const int ngroups = (NC + group - 1) / group;
   const int64_t most = ((int64_t)1 << (P->kappa - 1)) * ngroups;

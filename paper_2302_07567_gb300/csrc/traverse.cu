@@ -358,11 +358,10 @@ __global__ void __launch_bounds__(kTravThreads) k_lists_src(ListArgs a) {
 // barrier costs more the more blocks arrive at it, and a small tree's
 // frontier fits in few blocks.
 template <typename K>
-int coop_grid(K kern, int64_t cap, int64_t items, int64_t per_block, int* grid) {
-  int dev = 0, sms = 0, per_sm = 0;
-  FMM_CUDA_TRY(cudaGetDevice(&dev));
-  FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTravThreads, 0));
+int coop_grid(K* kern, int64_t cap, int64_t items, int64_t per_block, int* grid) {
+  int sms = 0, per_sm = 0;
+  if (int rc = device_sms(&sms)) return rc;
+  if (int rc = blocks_per_sm(kern, kTravThreads, 0, &per_sm)) return rc;
   if (per_sm < 1) return FMM_EINVAL;
   const int64_t want = std::max<int64_t>(sms, div_up(items, per_block));
   *grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, cap, want});

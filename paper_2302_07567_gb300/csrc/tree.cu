@@ -600,12 +600,7 @@ int run_tree(fmm_plan_s* P, const double* x, cudaStream_t s) {
     int32_t* t = cur; cur = nxt; nxt = t;
   }
   {
-    static bool attr = false;
-    if (!attr) {
-      FMM_CUDA_TRY(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(SubtreeSmem)));
-      attr = true;
-    }
+    if (int rc = smem_limit(k_subtree, (int)sizeof(SubtreeSmem))) return rc;
     k_subtree<<<(unsigned)((int64_t)1 << ls), kSubThreads, sizeof(SubtreeSmem), s>>>(
         x, cur, rank, N, nstart, ncount, ls, P->kappa, scal, nlo, nhi, naxis, nmed);
     FMM_LAUNCH_CHECK();

@@ -213,11 +213,7 @@ template <typename T, int NV>
 int launch_p2m(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
   const size_t smem = (size_t)256 * (((3 * P->np1 + 3) & ~3) + 4) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m<T, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  if (int rc = smem_limit(k_p2m<T, NV>, (int)smem)) return rc;
   k_p2m<T, NV><<<(unsigned)P->nleaves, 256, smem, s>>>(
       ws_ptr<typename Vec4<T>::type>(P, L.px), ws_ptr<typename Vec4<T>::type>(P, L.pb),
       ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
@@ -287,8 +283,9 @@ int run_upward(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
 }
 
 int run_l2l(fmm_plan_s* P, cudaStream_t s, bool per_level) {
-  return P->precision == FMM_FP32 ? run_transfer<float, 6, false>(P, ws_ptr<float>(P, P->lay.local), s, 4, per_level)
-                                  : run_transfer<double, 6, false>(P, ws_ptr<double>(P, P->lay.local), s, 4, per_level);
+  const int cap = per_level ? kLevelTransferCap : kCoopTransferCap;
+  return P->precision == FMM_FP32 ? run_transfer<float, 6, false>(P, ws_ptr<float>(P, P->lay.local), s, cap, per_level)
+                                  : run_transfer<double, 6, false>(P, ws_ptr<double>(P, P->lay.local), s, cap, per_level);
 }
 
 }  // namespace fmm
