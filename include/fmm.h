@@ -214,6 +214,17 @@ int fmm_version(void);
  * (all plans, all threads); differences around a region count its launches. */
 int64_t fmm_kernel_launches(void);
 
+/* Measurement helper (the paper has no counterpart): the FP32 fused
+ * multiply-add rate of the current device in TFLOP/s (FMA = 2 flop), the peak
+ * the library's ALU-bound kernels are reported against.  A kernel on every SM
+ * runs independent FMA chains, in the scalar form (paired = 0: one FMA per
+ * lane per instruction) or the paired form (paired = 1: two per lane per
+ * instruction, as the particle kernels issue their arithmetic); the best of
+ * three timed launches after one warm-up counts.  Synchronous, a few ms.
+ *   sink  device memory of at least SMs x 8 x 256 floats (written, never read;
+ *         FMM_EINVAL if smaller or NULL) */
+int fmm_fp32_fma_rate(void* sink, size_t sink_bytes, int paired, double* tflops, void* stream);
+
 /* gbar of a beam without allocating anything (the paper has no counterpart;
  * the value is the gbar of Eq. 3.2 that fmm_field computes, bit for bit).
  * For callers that cannot allocate device memory or attach a workspace: code

@@ -79,6 +79,7 @@ def lib():
         "fmm_stats_bytes": (ctypes.c_size_t, []),
         "fmm_kernel_launches": (I64, []),
         "fmm_gamma_bar_noalloc": (I32, [P, I64, P, P]),
+        "fmm_fp32_fma_rate": (I32, [P, SZ, I32, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -243,6 +244,19 @@ class Plan:
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().fmm_kernel_launches())
+
+
+def fp32_fma_rate(paired: bool, device=None) -> float:
+    """Measured FP32 FMA throughput of the device in TFLOP/s (FMA = 2 flop)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float32, device=dev)
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        rc = lib().fmm_fp32_fma_rate(_ptr(sink), sink.numel() * 4, int(bool(paired)), ctypes.byref(out), _stream(dev))
+    if rc != FMM_OK:
+        raise FMMError(rc, "fmm_fp32_fma_rate")
+    return float(out.value)
 
 
 def direct_field(x, p, q, gbar: float, targets=None):
