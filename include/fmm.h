@@ -82,6 +82,15 @@ typedef enum fmm_flags {
                             evaluated directly, as P2P of all leaf pairs under it,
                             instead of by M2L: fewer operations and no truncation
                             error for that pair                                     */
+  FMM_SERIAL = 64u,      /* run every stage on the caller's stream, one kernel after
+                            another.  By default independent branches share the GPU
+                            on a second stream the plan owns (FP32 forward: near-field
+                            P2P beside M2L and L2L; adjoint: the near field beside the
+                            source side's far-field chain), which is faster at every
+                            size measured; the serial order gives each kernel the GPU
+                            to itself, so its stage time is its own duration (for
+                            attributing time per kernel), and each kernel then takes
+                            every resident block slot.  Results are bitwise equal.   */
   FMM_GBAR_TERM = 32u    /* adjoint only (not in the paper): gbar is the function
                             sqrt(1 + pbar.pbar), pbar = (1/N) sum_j p_j, of Section 3
                             instead of a constant, so dL/dp gains

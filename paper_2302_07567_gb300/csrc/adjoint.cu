@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_adj_m2l_fast(const uint64_
 #pragma unroll
           for (int k = 0; k < KPT; ++k) {
             const float d = fmaxf(Dx[m1] + dyz[k], 5.169878828456423e-26f);
-            const float inv = rsqrtf(d);
+            const float inv = rsqrt_normal(d);
             const float r3 = inv * inv * inv;
             T1[k] = fmaf(wa.x * Rx[m1], r3, T1[k]);
             T2[k] = fmaf(wa.y, r3, T2[k]);
@@ -435,6 +435,171 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_adj_m2l_fast(const uint64_
     for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + nu] = sacc[k][c][tid];
   }
   }  // work items
+}
+
+// FP32 M2L^T with paired arithmetic and regrouped x sums, the counterpart of
+// k_m2l_pair: a thread owns two source points of the cluster, nu_a = P and
+// nu_b = P + H, and evaluates both against each target point mu with paired
+// FP32 instructions.  In the mu1 loop R_x = t_x[mu1] - X is the only varying
+// component (R = xi_S,mu - xi_s,nu), and the sums that carry R_x are split:
+// sum w r3 R_x = sum (w t_x) r3 - X sum w r3, with the products w t_x of the
+// node weights and the x offset of their point staged once per target
+// cluster.  A point pair then costs 12 FMA-pipe operations (|R|^2 1, r^-3 2,
+// nine sums) instead of 15.  Staged per target point, duplicated for the two
+// lanes: (WEx, ., WEy, .), (WEz, ., WBx, .), (WBy, ., WBz, .),
+// (WEx t_x, ., WBy t_x, .), (WBz t_x, ., 0, 0).
+template <int NP1, int NT>
+__global__ void __launch_bounds__(NT, 3) k_adj_m2l_pair(const uint64_t* __restrict__ keys,
+                                                       const int32_t* __restrict__ off, int shift,
+                                                       const int32_t* __restrict__ order, int64_t nitems,
+                                                       unsigned int* __restrict__ work,
+                                                       const NodeGeo* __restrict__ geo,
+                                                       const float4* __restrict__ sdc, Cheb ch,
+                                                       const float* __restrict__ W, float* __restrict__ Lam) {
+  constexpr int m = NP1 * NP1 * NP1;
+  constexpr int H = (m + 1) / 2;
+  constexpr int SPLIT = (H + NT - 1) / NT;
+  extern __shared__ float4 dsm[];
+  float4* sw = dsm;                                        // [m][5] staged target points
+  float2* sacc = reinterpret_cast<float2*>(dsm + 5 * m);   // [8][NT] Kahan sums, compensations
+  __shared__ float sxyz[3][NP1];                           // target point offsets per axis
+  __shared__ int64_t s_item;
+  const int tid = threadIdx.x;
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  for (;;) {  // items (source, chunk of NT point pairs) in the work order: longest lists first
+    if (tid == 0) s_item = (int64_t)atomicAdd(work, 1u);
+    __syncthreads();
+    const int64_t w = s_item;
+    __syncthreads();
+    if (w >= nitems) break;
+    const int64_t s = order[w / SPLIT];
+    const int P = (int)(w % SPLIT) * NT + tid;
+    const int nua = P < H ? P : 0, nub = P + H < m ? P + H : 0;
+    const uint64_t mask = ((uint64_t)1 << shift) - 1;
+    const int b = off[s], e = off[s + 1];
+    const NodeGeo gs = geo[s];
+    const float2 xs = make_float2((float)(gs.h[0] * ch.t[nua % NP1]), (float)(gs.h[0] * ch.t[nub % NP1]));
+    const float2 ys = make_float2((float)(gs.h[1] * ch.t[(nua / NP1) % NP1]),
+                                  (float)(gs.h[1] * ch.t[(nub / NP1) % NP1]));
+    const float2 zs = make_float2((float)(gs.h[2] * ch.t[nua / (NP1 * NP1)]),
+                                  (float)(gs.h[2] * ch.t[nub / (NP1 * NP1)]));
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sacc[c * NT + tid] = make_float2(0.f, 0.f);
+    for (int it = b; it < e; ++it) {
+      const int64_t S = (int64_t)(keys[it] & mask);
+      const float4 dh = sdc[2 * it];  // c_s - c_S
+      const NodeGeo gS = geo[S];
+      __syncthreads();
+      const float* Ws = W + (size_t)S * 6 * m;
+      for (int o = tid; o < m; o += NT) {
+        const float ex = Ws[o], ey = Ws[m + o], ez = Ws[2 * m + o];
+        const float bx = Ws[3 * m + o], by = Ws[4 * m + o], bz = Ws[5 * m + o];
+        const float tx = (float)(gS.h[0] * ch.t[o % NP1]);
+        const float vx = ex * tx, vy = by * tx, vz = bz * tx;
+        sw[5 * o] = make_float4(ex, ex, ey, ey);
+        sw[5 * o + 1] = make_float4(ez, ez, bx, bx);
+        sw[5 * o + 2] = make_float4(by, by, bz, bz);
+        sw[5 * o + 3] = make_float4(vx, vx, vy, vy);
+        sw[5 * o + 4] = make_float4(vz, vz, 0.f, 0.f);
+      }
+      if (tid < 3 * NP1) {
+        const int d = tid / NP1, k = tid - d * NP1;
+        sxyz[d][k] = (float)(gS.h[d] * ch.t[k]);
+      }
+      __syncthreads();
+      // this thread's two source points relative to the target-cluster centre
+      const float2 X = __fadd2_rn(make_float2(dh.x, dh.x), xs);
+      const float2 Y = __fadd2_rn(make_float2(dh.y, dh.y), ys);
+      const float2 Z = __fadd2_rn(make_float2(dh.z, dh.z), zs);
+      const float2 nX = __fmul2_rn(X, neg1);
+      float2 Rx[NP1];
+#pragma unroll
+      for (int k = 0; k < NP1; ++k) Rx[k] = __fadd2_rn(make_float2(sxyz[0][k], sxyz[0][k]), nX);
+      float2 part[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[c] = make_float2(0.f, 0.f);
+      for (int m3 = 0; m3 < NP1; ++m3) {
+        const float2 rz = __fadd2_rn(make_float2(sxyz[2][m3], sxyz[2][m3]), __fmul2_rn(Z, neg1));
+        const float2 nrz = __fmul2_rn(rz, neg1);
+        const float2 dz = __fmul2_rn(rz, rz);
+        const float4* row = sw + 5 * m3 * NP1 * NP1;
+#pragma unroll
+        for (int m2 = 0; m2 < NP1; ++m2) {
+          const float2 ry = __fadd2_rn(make_float2(sxyz[1][m2], sxyz[1][m2]), __fmul2_rn(Y, neg1));
+          const float2 dyz = __ffma2_rn(ry, ry, dz);
+          const float2 z0 = make_float2(0.f, 0.f);
+          float2 T1 = z0, T2 = z0, T3 = z0, T4 = z0, T5 = z0, T6 = z0, V1 = z0, V5 = z0, V6 = z0;
+#pragma unroll
+          for (int m1 = 0; m1 < NP1; ++m1) {
+            const float4* q = row + 5 * (m2 * NP1 + m1);
+            const float4 A = q[0], Bq = q[1], C = q[2], D = q[3], F = q[4];
+            float2 d = __ffma2_rn(Rx[m1], Rx[m1], dyz);
+            d.x = fmaxf(d.x, tiny_sep2<float>());
+            d.y = fmaxf(d.y, tiny_sep2<float>());
+            const float2 inv = make_float2(rsqrt_normal(d.x), rsqrt_normal(d.y));
+            const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+            T1 = __ffma2_rn(make_float2(A.x, A.y), r3, T1);
+            T2 = __ffma2_rn(make_float2(A.z, A.w), r3, T2);
+            T3 = __ffma2_rn(make_float2(Bq.x, Bq.y), r3, T3);
+            T4 = __ffma2_rn(make_float2(Bq.z, Bq.w), r3, T4);
+            T5 = __ffma2_rn(make_float2(C.x, C.y), r3, T5);
+            T6 = __ffma2_rn(make_float2(C.z, C.w), r3, T6);
+            V1 = __ffma2_rn(make_float2(D.x, D.y), r3, V1);
+            V5 = __ffma2_rn(make_float2(D.z, D.w), r3, V5);
+            V6 = __ffma2_rn(make_float2(F.x, F.y), r3, V6);
+          }
+          // sum w r3 R_x = sum (w t_x) r3 - X sum w r3
+          const float2 T1R = __ffma2_rn(nX, T1, V1), T5R = __ffma2_rn(nX, T5, V5), T6R = __ffma2_rn(nX, T6, V6);
+          // Lambda^a += sum r3 W^E_x R_x + R_y sum r3 W^E_y + R_z sum r3 W^E_z
+          // Lambda^b += (R_y sum r3 W^B_z - R_z sum r3 W^B_y, R_z sum r3 W^B_x - sum r3 W^B_z R_x,
+          //              sum r3 W^B_y R_x - R_y sum r3 W^B_x)
+          part[0] = __fadd2_rn(part[0], T1R);
+          part[0] = __ffma2_rn(ry, T2, part[0]);
+          part[0] = __ffma2_rn(rz, T3, part[0]);
+          part[1] = __ffma2_rn(ry, T6, part[1]);
+          part[1] = __ffma2_rn(nrz, T5, part[1]);
+          part[2] = __ffma2_rn(rz, T4, part[2]);
+          part[2] = __ffma2_rn(T6R, neg1, part[2]);
+          part[3] = __fadd2_rn(part[3], T5R);
+          part[3] = __ffma2_rn(__fmul2_rn(ry, neg1), T4, part[3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float2 sum = sacc[c * NT + tid], comp = sacc[(4 + c) * NT + tid];
+        kahan_add(sum.x, comp.x, part[c].x);
+        kahan_add(sum.y, comp.y, part[c].y);
+        sacc[c * NT + tid] = sum;
+        sacc[(4 + c) * NT + tid] = comp;
+      }
+    }
+    if (P < H) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + P] = sacc[c * NT + tid].x;
+    }
+    if (P + H < m) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Lam[((size_t)s * 4 + c) * m + P + H] = sacc[c * NT + tid].y;
+    }
+  }  // work items
+}
+
+template <int NP1, int NT>
+int launch_adj_m2l_pair(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  constexpr int m = NP1 * NP1 * NP1, H = (m + 1) / 2, SPLIT = (H + NT - 1) / NT;
+  const size_t smem = sizeof(float4) * 5 * m + sizeof(float2) * 8 * NT;
+  if (int rc = smem_limit(k_adj_m2l_pair<NP1, NT>, (int)smem)) return rc;
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_adj_m2l_pair<NP1, NT>, NT, smem, P->C * SPLIT, &grid)) return rc;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  FMM_CUDA_TRY(cudaMemsetAsync(&cnt->work[1], 0, sizeof(unsigned int), s));
+  k_adj_m2l_pair<NP1, NT><<<grid, NT, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l_src), ws_ptr<int32_t>(P, L.m2l_soff), P->kappa + 1,
+      ws_ptr<int32_t>(P, L.m2l_sorder), P->C * SPLIT, &cnt->work[1], ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.m2l_sdc), P->cheb, ws_ptr<float>(P, L.wbuf), ws_ptr<float>(P, L.lbuf));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
 }
 
 template <int NP1, int G, int SPLIT>
@@ -1504,7 +1669,7 @@ int adj_m2l(fmm_plan_s* P, bool gbar_term, cudaStream_t s) {
       // a whole cluster per block: the shortest adjoint beside the near-field
       // kernel (0.612 against 0.623 ms for (4, 2) at 2^9 leaves)
       case 7: return launch_adj_m2l_fast<7, 7, 1>(P, s);
-      case 9: return launch_adj_m2l_fast<9, 3, 3>(P, s);
+      case 9: return launch_adj_m2l_pair<9, 128>(P, s);
       default: break;
     }
   }
@@ -1524,11 +1689,14 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   const size_t smem = stage_bytes<T>(kSplit ? 4 : 2, 1, GB ? 8 : 6, groups, NT) + sizeof(T) * 6 * P->m;
   if (int rc = set_smem(k_adj_target<T, 1, GB>, smem)) return rc;
   // beside the source side's far field (side stream) the target side keeps
-  // to half of the SMs' block slots, so the other branch finds room
-  if (P->kappa > 0) {
+  // to half of the SMs' block slots, so the other branch finds room; alone
+  // it takes every resident slot
+  if (P->kappa > 0 && P->overlap) {
     int sms = 0;
     if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
+  } else if (int rc = resident_blocks(k_adj_target<T, 1, GB>, nt, smem, items, &grid)) {
+    return rc;
   }
   k_adj_target<T, 1, GB><<<grid, nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart),
@@ -1599,10 +1767,12 @@ int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
   unsigned grid = (unsigned)items;
   const size_t smem = stage_bytes<float>(6, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;
   if (int rc = set_smem(k_adj_near, smem)) return rc;
-  if (P->kappa > 0) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
+  if (P->kappa > 0 && P->overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;
     if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)3 * sms);
+  } else if (int rc = resident_blocks(k_adj_near, nt, smem, items, &grid)) {  // alone: every resident slot
+    return rc;
   }
   k_adj_near<<<grid, nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), ws_ptr<uint64_t>(P, L.p2p_src),
@@ -1664,23 +1834,29 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   // plan's side stream, the target-side particle kernel (ALU-bound) on the
   // caller's stream.  They share no buffer that either writes: W and Lambda
   // have their own, the target side reads the forward's locals.
+  // With FMM_SERIAL the chain runs first on the caller's stream.
   const bool chain = P->kappa > 0;
   const bool gb = (P->flags & FMM_GBAR_TERM) != 0;
+  const bool ov = chain && P->overlap;
   if (chain) {
-    if ((rc = ensure_side(P)) != FMM_OK) return rc;
-    cudaStream_t t = P->side;
-    FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
-    if ((rc = l2pt<T>(P, t)) != FMM_OK) return rc;
+    cudaStream_t t = s;
+    if (ov) {
+      if ((rc = ensure_side(P)) != FMM_OK) return rc;
+      t = P->side;
+      FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
+      FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
+    }
     // beside the particle kernel the transfers are launched once per level: a
     // cooperative launch would wait for the particle kernel to end
-    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, kLevelTransferCap, true)) != FMM_OK) return rc;  // L2L^T
+    const int cap = ov ? kLevelTransferCap : kCoopTransferCap;
+    if ((rc = l2pt<T>(P, t)) != FMM_OK) return rc;
+    if ((rc = run_transfer<T, 6, true>(P, ws_ptr<T>(P, L.wbuf), t, cap, ov)) != FMM_OK) return rc;  // L2L^T
     if ((rc = record(P, 11, t)) != FMM_OK) return rc;
     if ((rc = adj_m2l<T>(P, gb, t)) != FMM_OK) return rc;
     if ((rc = record(P, 12, t)) != FMM_OK) return rc;
-    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, kLevelTransferCap, true)) != FMM_OK) return rc;  // M2M^T
+    if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, cap, ov)) != FMM_OK) return rc;  // M2M^T
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
-    FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
+    if (ov) FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
   }
   // FP32 without the gbar term: both near-field roles in one kernel
   const bool fused = std::is_same<T, float>::value && !gb;
@@ -1689,12 +1865,13 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   else rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
   if (rc != FMM_OK) return rc;
   if ((rc = record(P, 10, s)) != FMM_OK) return rc;
-  if (chain) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
+  if (ov) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
   if (gb && (rc = gbar_sum<T>(P, chain, s)) != FMM_OK) return rc;
   if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, fused, s)) != FMM_OK) return rc;
   if ((rc = record(P, 14, s)) != FMM_OK) return rc;
   (void)x;
-  if (P->flags & FMM_TIMING) P->flags = (P->flags & ~0x300u) | 0x100u | (chain ? 0x200u : 0u);
+  P->adj_timed = (P->flags & FMM_TIMING) != 0;
+  P->adj_chain = chain;
   return FMM_OK;
 }
 

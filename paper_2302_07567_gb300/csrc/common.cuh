@@ -135,7 +135,10 @@ struct fmm_plan_s {
   void* hpin = nullptr;           // pinned host copy of the counters and scalars after the traversal
   cudaEvent_t trav_ev = nullptr;  // recorded after that copy
   double stage_ms[18] = {};
-  bool split_fwd = false;  // the last forward ran the FP32 near field beside M2L and L2L
+  bool overlap = true;     // independent branches on two streams (no FMM_SERIAL)
+  bool split_fwd = false;  // the last forward ran the FP32 near field and L2P as kernels of their own
+  bool adj_timed = false;  // the last adjoint recorded its stage events
+  bool adj_chain = false;  // ... and had a far-field chain (kappa > 0)
 };
 
 namespace fmm {
@@ -177,8 +180,18 @@ template <> struct Vec4<double> { using type = double4; };
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
+// 1/sqrt(x) by the hardware approximation (rsqrt.approx) for a normal
+// positive float.  rsqrtf also rescales subnormal inputs, which costs extra
+// instructions in the inner loops; every FP32 caller here passes
+// x >= tiny_sep2<float>() = 2^-84 (masked or clamped), far above the
+// subnormal range, where the flush-to-zero form returns the same value.
+__device__ __forceinline__ float rsqrt_normal(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_normal(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* _
 #pragma unroll
           for (int k = 0; k < KPT; ++k) {
             const float d = fmaxf(Dx[n1] + dyz[k], 5.169878828456423e-26f);
-            const float inv = rsqrtf(d);
+            const float inv = rsqrt_normal(d);
             const float r3 = inv * inv * inv;
             const float ar3 = src.x * r3;
             Ta[k] += ar3;
@@ -258,6 +258,181 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* _
     for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + mu] = sacc[k][c][tid];
   }
   }  // work items
+}
+
+// FP32 M2L with paired arithmetic and regrouped x sums (eta <= 1/2, points
+// per axis NP1 fixed).
+//
+// Two changes against k_m2l_fast, which issues about 18 instructions per
+// point pair, 14 of them on the FMA pipe:
+// - A thread owns two target points of the cluster, mu_a = P and
+//   mu_b = P + H (H = ceil(m / 2)), and evaluates both against each source
+//   point with paired FP32 instructions (__fadd2_rn, __fmul2_rn,
+//   __ffma2_rn: two lanes per instruction), so one instruction stream serves
+//   two point pairs.
+// - In the nu1 loop R_x = X - s_x[nu1] is the only varying component, and
+//   the sums that carry R_x are split: sum q r3 R_x = X sum q r3 - sum
+//   (q s_x) r3.  The products q s_x of the source's effective masses with
+//   the x offset of their point are staged once per source cluster, so a
+//   point pair costs 10 FMA-pipe operations (|R|^2 1, r^-3 2, seven sums)
+//   instead of 13.  The split loses no more than a few units of the last
+//   place relative to the pair's field: |X| and |s_x| are at most |R| plus
+//   the two boxes' half widths, and admissible boxes are at least their
+//   radii apart.
+// Staged per source point, every value duplicated for the two lanes:
+// (a, a, b~x, b~x), (b~y, b~y, b~z, b~z), (-a s_x, ., -b~y s_x, .),
+// (-b~z s_x, ., 0, 0).  The running sums across sources are Kahan-compensated
+// in shared memory, in the same per-source groups as the other M2L kernels.
+// Items are (target, chunk of NT point pairs), fetched from the work counter
+// in the work order (longest source lists first).
+template <int NP1, int NT>
+__global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
+                                                   int shift, const unsigned int* __restrict__ err,
+                                                   const int32_t* __restrict__ order, int64_t nitems,
+                                                   unsigned int* __restrict__ work, const NodeGeo* __restrict__ geo,
+                                                   const float4* __restrict__ pdc, Cheb ch,
+                                                   const float* __restrict__ M, float* __restrict__ Lout) {
+  constexpr int m = NP1 * NP1 * NP1;
+  constexpr int H = (m + 1) / 2;               // point pairs per cluster
+  constexpr int SPLIT = (H + NT - 1) / NT;     // items per cluster
+  extern __shared__ float4 dsm[];
+  float4* sm = dsm;                                           // [m][4] staged source points
+  float2* sacc = reinterpret_cast<float2*>(dsm + 4 * m);      // [12][NT] Kahan sums, compensations
+  __shared__ float sxyz[3][NP1];               // source point offsets per axis
+  __shared__ int64_t s_item;
+  if (*err) return;  // the traversal failed: the lists are incomplete
+  const int tid = threadIdx.x;
+  const float2 neg1 = make_float2(-1.f, -1.f);
+  for (;;) {
+    if (tid == 0) s_item = (int64_t)atomicAdd(work, 1u);
+    __syncthreads();
+    const int64_t w = s_item;
+    __syncthreads();
+    if (w >= nitems) break;
+    const int64_t t = order[w / SPLIT];
+    const int P = (int)(w % SPLIT) * NT + tid;
+    const int mua = P < H ? P : 0, mub = P + H < m ? P + H : 0;
+    const uint64_t mask = ((uint64_t)1 << shift) - 1;
+    const int b = off[t], e = off[t + 1];
+    const NodeGeo gt = geo[t];
+    // target point offsets from the cluster centre, lanes (mu_a, mu_b)
+    const float2 xt = make_float2((float)(gt.h[0] * ch.t[mua % NP1]), (float)(gt.h[0] * ch.t[mub % NP1]));
+    const float2 yt = make_float2((float)(gt.h[1] * ch.t[(mua / NP1) % NP1]),
+                                  (float)(gt.h[1] * ch.t[(mub / NP1) % NP1]));
+    const float2 zt = make_float2((float)(gt.h[2] * ch.t[mua / (NP1 * NP1)]),
+                                  (float)(gt.h[2] * ch.t[mub / (NP1 * NP1)]));
+#pragma unroll
+    for (int c = 0; c < 12; ++c) sacc[c * NT + tid] = make_float2(0.f, 0.f);
+    for (int it = b; it < e; ++it) {
+      const int64_t s = (int64_t)(keys[it] & mask);
+      const float4 dh = pdc[2 * it];
+      const NodeGeo gs = geo[s];
+      __syncthreads();
+      const float* Ms = M + (size_t)s * 4 * m;
+      for (int o = tid; o < m; o += NT) {
+        const float a = Ms[o], bx = Ms[m + o], by = Ms[2 * m + o], bz = Ms[3 * m + o];
+        const float sx = (float)(gs.h[0] * ch.t[o % NP1]);
+        const float ua = -a * sx, uy = -by * sx, uz = -bz * sx;
+        sm[4 * o] = make_float4(a, a, bx, bx);
+        sm[4 * o + 1] = make_float4(by, by, bz, bz);
+        sm[4 * o + 2] = make_float4(ua, ua, uy, uy);
+        sm[4 * o + 3] = make_float4(uz, uz, 0.f, 0.f);
+      }
+      if (tid < 3 * NP1) {
+        const int d = tid / NP1, k = tid - d * NP1;
+        sxyz[d][k] = (float)(gs.h[d] * ch.t[k]);
+      }
+      __syncthreads();
+      // this thread's two target points relative to the source-cluster centre
+      const float2 X = __fadd2_rn(make_float2(dh.x, dh.x), xt);
+      const float2 Y = __fadd2_rn(make_float2(dh.y, dh.y), yt);
+      const float2 Z = __fadd2_rn(make_float2(dh.z, dh.z), zt);
+      float2 Rx[NP1];
+#pragma unroll
+      for (int k = 0; k < NP1; ++k) Rx[k] = __fadd2_rn(X, make_float2(-sxyz[0][k], -sxyz[0][k]));
+      float2 part[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) part[c] = make_float2(0.f, 0.f);
+      for (int n3 = 0; n3 < NP1; ++n3) {
+        const float2 rz = __fadd2_rn(Z, make_float2(-sxyz[2][n3], -sxyz[2][n3]));
+        const float2 nrz = __fmul2_rn(rz, neg1);
+        const float2 dz = __fmul2_rn(rz, rz);
+        const float4* row = sm + 4 * n3 * NP1 * NP1;
+#pragma unroll
+        for (int n2 = 0; n2 < NP1; ++n2) {
+          const float2 ry = __fadd2_rn(Y, make_float2(-sxyz[1][n2], -sxyz[1][n2]));
+          const float2 dyz = __ffma2_rn(ry, ry, dz);
+          const float2 z0 = make_float2(0.f, 0.f);
+          float2 Ta = z0, Ua = z0, Tbx = z0, Tby = z0, Uby = z0, Tbz = z0, Ubz = z0;
+#pragma unroll
+          for (int n1 = 0; n1 < NP1; ++n1) {
+            const float4* q = row + 4 * (n2 * NP1 + n1);
+            const float4 A = q[0], Bq = q[1], C = q[2], D = q[3];
+            float2 d = __ffma2_rn(Rx[n1], Rx[n1], dyz);
+            d.x = fmaxf(d.x, tiny_sep2<float>());
+            d.y = fmaxf(d.y, tiny_sep2<float>());
+            const float2 inv = make_float2(rsqrt_normal(d.x), rsqrt_normal(d.y));
+            const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+            Ta = __ffma2_rn(make_float2(A.x, A.y), r3, Ta);
+            Tbx = __ffma2_rn(make_float2(A.z, A.w), r3, Tbx);
+            Tby = __ffma2_rn(make_float2(Bq.x, Bq.y), r3, Tby);
+            Tbz = __ffma2_rn(make_float2(Bq.z, Bq.w), r3, Tbz);
+            Ua = __ffma2_rn(make_float2(C.x, C.y), r3, Ua);
+            Uby = __ffma2_rn(make_float2(C.z, C.w), r3, Uby);
+            Ubz = __ffma2_rn(make_float2(D.x, D.y), r3, Ubz);
+          }
+          // sum q r3 R_x = X sum q r3 - sum (q s_x) r3
+          const float2 TaR = __ffma2_rn(X, Ta, Ua), TbyR = __ffma2_rn(X, Tby, Uby), TbzR = __ffma2_rn(X, Tbz, Ubz);
+          // E += (sum a r3 R_x, R_y sum a r3, R_z sum a r3)
+          // B += (R_z sum b~y r3 - R_y sum b~z r3, sum b~z r3 R_x - R_z sum b~x r3,
+          //       R_y sum b~x r3 - sum b~y r3 R_x)
+          part[0] = __fadd2_rn(part[0], TaR);
+          part[1] = __ffma2_rn(ry, Ta, part[1]);
+          part[2] = __ffma2_rn(rz, Ta, part[2]);
+          part[3] = __ffma2_rn(rz, Tby, part[3]);
+          part[3] = __ffma2_rn(__fmul2_rn(ry, neg1), Tbz, part[3]);
+          part[4] = __fadd2_rn(part[4], TbzR);
+          part[4] = __ffma2_rn(nrz, Tbx, part[4]);
+          part[5] = __ffma2_rn(ry, Tbx, part[5]);
+          part[5] = __ffma2_rn(TbyR, neg1, part[5]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float2 sum = sacc[c * NT + tid], comp = sacc[(6 + c) * NT + tid];
+        kahan_add(sum.x, comp.x, part[c].x);
+        kahan_add(sum.y, comp.y, part[c].y);
+        sacc[c * NT + tid] = sum;
+        sacc[(6 + c) * NT + tid] = comp;
+      }
+    }
+    if (P < H) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + P] = sacc[c * NT + tid].x;
+    }
+    if (P + H < m) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Lout[((size_t)t * 6 + c) * m + P + H] = sacc[c * NT + tid].y;
+    }
+  }  // work items
+}
+
+template <int NP1, int NT>
+int launch_pair(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  constexpr int m = NP1 * NP1 * NP1, H = (m + 1) / 2, SPLIT = (H + NT - 1) / NT;
+  const size_t smem = sizeof(float4) * 4 * m + sizeof(float2) * 12 * NT;
+  if (int rc = smem_limit(k_m2l_pair<NP1, NT>, (int)smem)) return rc;
+  unsigned grid = 0;
+  if (int rc = resident_blocks(k_m2l_pair<NP1, NT>, NT, smem, P->C * SPLIT, &grid)) return rc;
+  Counters* cnt = ws_ptr<Counters>(P, L.counters);
+  FMM_CUDA_TRY(cudaMemsetAsync(&cnt->work[0], 0, sizeof(unsigned int), s));
+  k_m2l_pair<NP1, NT><<<grid, NT, smem, s>>>(
+      ws_ptr<uint64_t>(P, L.m2l), ws_ptr<int32_t>(P, L.m2l_off), P->kappa + 1, &cnt->err,
+      ws_ptr<int32_t>(P, L.m2l_order), P->C * SPLIT, &cnt->work[0], ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.m2l_dc), P->cheb, ws_ptr<float>(P, L.mpole), ws_ptr<float>(P, L.local));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
 }
 
 template <int NP1, int G, int SPLIT>
@@ -335,7 +510,7 @@ int run_m2l(fmm_plan_s* P, cudaStream_t s) {
       // 2 threads per (mu1, mu2), 4 mu3 chunks per cluster: 0.132 ms against
       // 0.140 for (4, 2) at 2^9 leaves
       case 7: return launch_fast<7, 2, 4>(P, s);
-      case 9: return launch_fast<9, 3, 3>(P, s);
+      case 9: return launch_pair<9, 128>(P, s);
       default: break;
     }
   }

@@ -272,7 +272,7 @@ int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, doubl
   if (!(eta > 0.0) || !std::isfinite(eta)) return FMM_EINVAL;
   if (precision != FMM_FP32 && precision != FMM_FP64) return FMM_EINVAL;
   if (flags & ~(unsigned)(FMM_RECOMPUTE | FMM_BOUNDS_CHECK | FMM_TIMING | FMM_SIZE_AWARE | FMM_TEST_POLY_KERNEL |
-                          FMM_GBAR_TERM))
+                          FMM_GBAR_TERM | FMM_SERIAL))
     return FMM_EINVAL;
   if ((flags & FMM_TEST_POLY_KERNEL) && precision != FMM_FP64) return FMM_EINVAL;
   fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
@@ -292,6 +292,7 @@ int fmm_plan_create(fmm_plan_t* out, int64_t N, int degree, int leaf_size, doubl
   P->kappa = kappa;
   P->C = ((int64_t)2 << kappa) - 1;
   P->nleaves = (int64_t)1 << kappa;
+  P->overlap = !(flags & FMM_SERIAL);
   default_caps(P);
   make_tables(P);
   make_layout(P);
@@ -393,23 +394,27 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   // FP32: the near-field P2P needs only the lists, so it runs on the
   // caller's stream while M2L and L2L (launched per level, as a cooperative
   // launch would wait for the P2P kernel) run on the plan's high-priority
-  // side stream; L2P and the output follow when both are done.  FP64 and the
+  // side stream (with FMM_SERIAL the three run in turn on the caller's
+  // stream).  L2P and the output follow when both are done.  FP64 and the
   // polynomial test kernel keep the fused P2P + L2P after M2L and L2L.
   const bool split = P->precision == FMM_FP32 && !(P->flags & FMM_TEST_POLY_KERNEL) && P->kappa > 0;
   if (split) {
-    if ((rc = ensure_side(P)) != FMM_OK) return rc;
-    cudaStream_t t = P->side;
-    FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
-    FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
-    if ((rc = record(P, 5, t)) != FMM_OK) return rc;
+    cudaStream_t t = s;
+    if (P->overlap) {
+      if ((rc = ensure_side(P)) != FMM_OK) return rc;
+      t = P->side;
+      FMM_CUDA_TRY(cudaEventRecord(P->fork_ev, s));
+      FMM_CUDA_TRY(cudaStreamWaitEvent(t, P->fork_ev, 0));
+      if ((rc = record(P, 5, t)) != FMM_OK) return rc;
+    }
     if ((rc = run_m2l(P, t)) != FMM_OK) return rc;
     if ((rc = record(P, 6, t)) != FMM_OK) return rc;
-    if ((rc = run_l2l(P, t, true)) != FMM_OK) return rc;
+    if ((rc = run_l2l(P, t, P->overlap)) != FMM_OK) return rc;
     if ((rc = record(P, 7, t)) != FMM_OK) return rc;
-    FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
+    if (P->overlap) FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
     if ((rc = run_p2p_near(P, s)) != FMM_OK) return rc;
     if ((rc = record(P, 18, s)) != FMM_OK) return rc;
-    FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
+    if (P->overlap) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
     if ((rc = record(P, 19, s)) != FMM_OK) return rc;
     if ((rc = run_l2p_far(P, E, B, s)) != FMM_OK) return rc;
     if ((rc = record(P, 8, s)) != FMM_OK) return rc;
@@ -487,23 +492,25 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[5] = el(5, 6);
     P->stage_ms[6] = el(6, 7);
     if (P->split_fwd) {
-      P->stage_ms[7] = el(5, 18);   // near-field P2P beside M2L and L2L
+      // near-field P2P: beside M2L and L2L, or after them
+      P->stage_ms[7] = P->overlap ? el(5, 18) : el(7, 18);
       P->stage_ms[16] = el(19, 8);  // L2P and the output
     } else {
       P->stage_ms[7] = el(7, 8);
       P->stage_ms[16] = 0.0;
     }
     P->stage_ms[13] = el(0, 8);
-    if (P->flags & 0x100u) {  // adjoint events recorded
-      // the target side runs on the caller's stream while L2P^T .. M2M^T run
-      // on the side stream, both from event 16; the source side starts when
-      // both have finished
-      P->stage_ms[11] = el(16, 10);  // near-field particle kernel (both roles in FP32, else the target side)
-      if (P->flags & 0x200u) {
+    if (P->adj_timed) {
+      // the near-field kernel runs on the caller's stream from event 16 while
+      // L2P^T .. M2M^T run on the side stream, or after them (no overlap);
+      // the source side starts when both have finished
+      const bool ov = P->overlap && P->adj_chain;
+      P->stage_ms[11] = ov || !P->adj_chain ? el(16, 10) : el(13, 10);  // near-field particle kernel
+      if (P->adj_chain) {
         P->stage_ms[8] = el(16, 11);   // L2P^T + L2L^T
         P->stage_ms[9] = el(11, 12);   // M2L^T
         P->stage_ms[10] = el(12, 13);  // M2M^T
-        P->stage_ms[12] = std::min(el(10, 14), el(13, 14));  // source side + chain rule
+        P->stage_ms[12] = ov ? std::min(el(10, 14), el(13, 14)) : el(10, 14);  // source side + chain rule
       } else {
         P->stage_ms[12] = el(10, 14);
       }

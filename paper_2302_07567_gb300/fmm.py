@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfmm_gb300.so")
 FMM_OK, FMM_EINVAL, FMM_ENOWORKSPACE, FMM_EOVERFLOW, FMM_ENONFINITE, FMM_ESTATE, FMM_ECUDA, FMM_EBOUNDS = range(8)
 FMM_FP64, FMM_FP32 = 0, 1
 FMM_RECOMPUTE, FMM_BOUNDS_CHECK, FMM_TIMING, FMM_SIZE_AWARE, FMM_TEST_POLY_KERNEL, FMM_GBAR_TERM = 1, 2, 4, 8, 16, 32
+FMM_SERIAL = 64
 EXPORT = dict(gbar=0, perm=1, nodes=2, bbox=3, axis=4, p2p=5, m2l=6, multipole=7, local=8)
 STAGES = ["setup", "tree", "upward", "traversal", "host_wait", "m2l", "l2l", "p2p_l2p",
           "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_near", "adj_source", "total", "adj_total", "adj_lists",

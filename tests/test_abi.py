@@ -45,10 +45,10 @@ def test_host_side_argument_checks(libpath):
     for N, n, leaf, eta, prec in bad:
         assert lib.fmm_plan_create(ctypes.byref(h), N, n, leaf, eta, prec, 0) == 1
     assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 0x100) == 1  # unknown flag bit
-    assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 64) == 1  # unknown flag bit
+    assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 128) == 1  # unknown flag bit
     assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, 16) == 1  # the test kernel is FP64 only
     lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
-    for flags in (32, 32 | 8 | 2 | 1):  # gbar term, with size-aware lists, bounds checks, recompute
+    for flags in (32, 32 | 8 | 2 | 1, 64 | 4):  # gbar term, with size-aware lists, bounds checks, recompute; serial
         assert lib.fmm_plan_create(ctypes.byref(h), 100, 4, 64, 0.5, 1, flags) == 0
         lib.fmm_plan_destroy(h)
     assert lib.fmm_plan_create(ctypes.byref(h), 4096, 4, 64, 0.5, 1, 0) == 0

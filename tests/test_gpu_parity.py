@@ -12,7 +12,7 @@ import torch
 
 from oracle import bldtt, metrics, physics
 from paper_2302_07567_gb300 import fmm
-from paper_2302_07567_gb300.workloads import make_beam, random_beam
+from paper_2302_07567_gb300.workloads import make_beam, make_weights, random_beam
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -161,6 +161,25 @@ def test_runs_are_bitwise_deterministic(prec):
     E1, B1 = E1.clone(), B1.clone()
     E2, B2 = plan.field(X, Pm, Q)
     assert torch.equal(E1, E2) and torch.equal(B1, B2)
+
+
+@pytest.mark.parametrize("prec,n,leaf", [("fp32", 8, 256), ("fp32", 6, 128), ("fp64", 4, 64)])
+def test_serial_stage_order_is_bitwise_equal(prec, n, leaf):
+    """FMM_SERIAL runs the independent branches one after another on one
+    stream; every sum keeps its order, so fields and gradients are equal."""
+    N = 20000
+    x, p, q = make_beam("corehalo16m", N=N)
+    wE, wB = make_weights(N)
+    X, Pm, Q = dev(x, p, q)
+    out = []
+    for flags in (0, fmm.FMM_SERIAL):
+        plan = fmm.Plan(N, n, leaf, 0.5, precision=prec, flags=flags)
+        E, B = plan.field(X, Pm, Q)
+        WE, WB = (torch.as_tensor(w, device=DEV, dtype=plan.out_dtype) for w in (wE, wB))
+        out.append([E, B, *plan.adjoint(X, Pm, Q, WE, WB)])
+        plan.close()
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
 
 
 def test_edge_cases():
