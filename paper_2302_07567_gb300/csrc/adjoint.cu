@@ -1665,10 +1665,9 @@ int adj_m2l(fmm_plan_s* P, bool gbar_term, cudaStream_t s) {
   if (std::is_same<T, float>::value && P->eta <= 0.5) {
     switch (P->np1) {
       case 3: return launch_adj_m2l_fast<3, 3, 1>(P, s);
-      case 5: return launch_adj_m2l_fast<5, 5, 1>(P, s);
-      // a whole cluster per block: the shortest adjoint beside the near-field
-      // kernel (0.612 against 0.623 ms for (4, 2) at 2^9 leaves)
-      case 7: return launch_adj_m2l_fast<7, 7, 1>(P, s);
+      // paired kernels, the block sizes of the forward M2L
+      case 5: return launch_adj_m2l_pair<5, 64>(P, s);
+      case 7: return launch_adj_m2l_pair<7, 64>(P, s);
       case 9: return launch_adj_m2l_pair<9, 128>(P, s);
       default: break;
     }

@@ -506,10 +506,12 @@ int run_m2l(fmm_plan_s* P, cudaStream_t s) {
   if (P->precision == FMM_FP32 && P->eta <= 0.5 && !(P->flags & FMM_TEST_POLY_KERNEL)) {
     switch (P->np1) {
       case 3: return launch_fast<3, 3, 1>(P, s);
-      case 5: return launch_fast<5, 5, 1>(P, s);
-      // 2 threads per (mu1, mu2), 4 mu3 chunks per cluster: 0.132 ms against
-      // 0.140 for (4, 2) at 2^9 leaves
-      case 7: return launch_fast<7, 2, 4>(P, s);
+      // paired kernels, block sizes from sweeps of fwd+adj steps: n = 4 (64
+      // threads) 33.2 -> 32.1 ms on the 1.28e6 cube; n = 6 (64) 1.465 ->
+      // 1.432 ms at 2^16, 14.9 -> 14.3 ms at 2^18 (192: 14.0, 96: 14.6);
+      // n = 8 (128) with the x sums split 3.91 -> 3.47 s at 2^24
+      case 5: return launch_pair<5, 64>(P, s);
+      case 7: return launch_pair<7, 64>(P, s);
       case 9: return launch_pair<9, 128>(P, s);
       default: break;
     }
