@@ -168,12 +168,13 @@ typedef struct fmm_stats {
      forward: 0 setup, 1 tree, 2 upward pass, 3 traversal with the ordering
      of the lists, 4 the host read of the list sizes, 5 M2L, 6 L2L,
      7 P2P+L2P (FP32: the near-field P2P, which runs beside M2L and L2L),
-     16 FP32: L2P and the output after both, 13 whole forward;
+     16 FP32: L2P and the output after both, 13 whole forward, 17 P2M (part of 2);
      adjoint: 8 L2P^T + L2L^T, 9 M2L^T, 10 M2M^T, 11 near-field particle
      kernel (FP32: both roles; else the target side with its far field),
      12 source side (FP32: far field and chain rule; else near + far + chain
-     rule), 14 whole adjoint, 15 source-major lists and any recomputation;
-     17 unused */
+     rule), 14 whole adjoint, 15 source-major lists and any recomputation.
+     With FMM_SERIAL every stage has the GPU to itself, so a stage time is the
+     duration of its own kernels. */
   double stage_ms[18];
 } fmm_stats;
 

@@ -1799,11 +1799,7 @@ int gbar_sum(fmm_plan_s* P, bool far, cudaStream_t s) {
   return FMM_OK;
 }
 
-int record(fmm_plan_s* P, int k, cudaStream_t s) {
-  if (!(P->flags & FMM_TIMING) || !P->ev_made) return FMM_OK;
-  FMM_CUDA_TRY(cudaEventRecord(P->ev[k], s));
-  return FMM_OK;
-}
+int record(fmm_plan_s* P, int k, cudaStream_t s) { return record_stage(P, k, s); }
 
 template <typename T>
 int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, const void* wE, const void* wB,

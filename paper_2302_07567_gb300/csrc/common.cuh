@@ -57,6 +57,7 @@ struct Counters {
   unsigned int work[2];  // item counters of the dynamically scheduled M2L and M2L^T launches
   unsigned int pad[1];
   unsigned long long cover;  // FMM_BOUNDS_CHECK: sum of |S_t| |S_s| over the list pairs
+  unsigned long long p2p_work;  // sum of |S_t| |S_s| over the P2P pairs (traversal)
 };
 
 // Chebyshev points of the second kind t_k = cos(k pi / n) and their
@@ -126,6 +127,7 @@ struct fmm_plan_s {
   size_t ws_bytes = 0;
   bool have_forward = false;
   int64_t p2p_count = 0, m2l_count = 0;
+  double p2p_work = 0.0;          // sum |S_t| |S_s| over the P2P pairs of the last forward
   double gbar = 0.0, lunit = 1.0, munit = 1.0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[20] = {};
@@ -348,6 +350,8 @@ int run_traverse(fmm_plan_s* P, cudaStream_t s);
 int run_list_transpose(fmm_plan_s* P, cudaStream_t s);
 // the plan's side stream and its fork / join events (created on first use)
 int ensure_side(fmm_plan_s* P);
+// FMM_TIMING: record the plan's stage event k on stream s (no-op otherwise)
+int record_stage(fmm_plan_s* P, int k, cudaStream_t s);
 // FMM_BOUNDS_CHECK: node tables, leaf order and lists (target- or source-major);
 // synchronises the stream, FMM_EBOUNDS on any violation
 int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);

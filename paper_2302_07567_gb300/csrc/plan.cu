@@ -217,13 +217,15 @@ int ensure_events(fmm_plan_s* P) {
   return FMM_OK;
 }
 
-int record(fmm_plan_s* P, int k, cudaStream_t s) {
-  if (!(P->flags & FMM_TIMING)) return FMM_OK;
+int record(fmm_plan_s* P, int k, cudaStream_t s) { return record_stage(P, k, s); }
+
+}  // namespace
+
+int record_stage(fmm_plan_s* P, int k, cudaStream_t s) {
+  if (!(P->flags & FMM_TIMING) || !P->ev_made) return FMM_OK;
   FMM_CUDA_TRY(cudaEventRecord(P->ev[k], s));
   return FMM_OK;
 }
-
-}  // namespace
 
 int ensure_side(fmm_plan_s* P) {
   if (P->side) return FMM_OK;
@@ -375,6 +377,7 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
     FMM_CUDA_TRY(cudaEventSynchronize(P->trav_ev));
     P->p2p_count = (int64_t)hc->p2p_count;
     P->m2l_count = (int64_t)hc->m2l_count;
+    P->p2p_work = (double)hc->p2p_work;
     if (hc->err & kErrNonFinite) return FMM_ENONFINITE;
     if ((hc->err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || P->p2p_count > P->cap_p2p ||
         P->m2l_count > P->cap_m2l)
@@ -463,16 +466,8 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
   out->cap_m2l = P->cap_m2l;
   out->cap_frontier = P->cap_frontier;
   out->m2l_interactions = (double)P->m2l_count * (double)P->m * (double)P->m;
-  if (P->have_forward && P->p2p_count > 0 && P->ws) {
-    std::vector<uint64_t> keys((size_t)P->p2p_count);
-    FMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
-    FMM_CUDA_TRY(cudaMemcpy(keys.data(), P->ws + P->lay.p2p, 8 * keys.size(), cudaMemcpyDeviceToHost));
-    const int shift = P->kappa + 1;
-    const uint64_t mask = ((uint64_t)1 << shift) - 1;
-    double tot = 0.0;
-    for (uint64_t k : keys) tot += (double)P->node_count[k >> shift] * (double)P->node_count[k & mask];
-    out->p2p_interactions = tot - (double)P->N;
-  }
+  // sum |S_t| |S_s| over the P2P pairs, counted by the traversal kernel
+  if (P->have_forward) out->p2p_interactions = P->p2p_work - (double)P->N;
   if ((P->flags & FMM_TIMING) && P->ev_made) {
     FMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
     for (int k = 0; k < 16; ++k) P->stage_ms[k] = 0.0;
@@ -487,6 +482,7 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[0] = el(0, 1);
     P->stage_ms[1] = el(1, 2);
     P->stage_ms[2] = el(2, 17);  // upward pass
+    P->stage_ms[17] = el(2, 9);  // its P2M
     P->stage_ms[3] = el(17, 3);  // traversal and lists
     P->stage_ms[4] = el(3, 5);   // copy of the list sizes to the host
     P->stage_ms[5] = el(5, 6);

@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
     cnt->frontier_count[2] = 0;
     cnt->p2p_count = 0;
     cnt->m2l_count = 0;
+    cnt->p2p_work = 0;
   }
   grid.sync();
+  unsigned long long work = 0;  // this thread's share of sum |S_t| |S_s| over the P2P pairs
   const int leaf0 = 1 << a.kappa;
   const int shift = a.lists.shift;
   const double* ncen = a.lists.ncen;
@@ -295,6 +297,7 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
       const bool lt = t >= leaf0, lu = u >= leaf0;
       if (lt && lu) {
         push(&cnt->p2p_count, a.cap_p2p, a.p2p, ((uint64_t)t << shift) | (uint64_t)u, &cnt->err, kErrOvfP2P);
+        work += (unsigned long long)(a.ncount[t] * a.ncount[u]);
         continue;
       }
       const double rt = a.ndiam[t], ru = a.ndiam[u];
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
           const int64_t t0 = (int64_t)t << dt, u0 = (int64_t)u << du;
           const int64_t nt = (int64_t)1 << dt, nu = (int64_t)1 << du;
           const unsigned long long at = atomicAdd(&cnt->p2p_count, (unsigned long long)(nt * nu));
+          work += (unsigned long long)(a.ncount[t] * a.ncount[u]);  // all leaf pairs under (t, u)
           if ((int64_t)at + nt * nu <= a.cap_p2p) {
             for (int64_t i = 0; i < nt; ++i)
               for (int64_t k = 0; k < nu; ++k)
@@ -342,6 +346,9 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
     }
     grid.sync();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) work += __shfl_down_sync(0xffffffffu, work, o);
+  if ((threadIdx.x & 31) == 0 && work) atomicAdd(&cnt->p2p_work, work);
   // every block sees the same final flags: on any error no list is ordered
   if (__ldcg(&cnt->err) != 0u) return;
   order_lists<kFP32>(grid, a.lists);

@@ -238,6 +238,8 @@ int upward_t(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
     default: rc = launch_p2m<T, 9>(P, s); break;
   }
   if (rc != FMM_OK) return rc;
+  // P2M done (stage event of the forward call, not of a recomputation)
+  if (!P->have_forward && (rc = record_stage(P, 9, s)) != FMM_OK) return rc;
   const Layout& L = P->lay;
   rc = run_transfer<T, 4, true>(P, ws_ptr<T>(P, L.mpole), s, xfer_cap, per_level);  // M2M, all levels
   if (rc != FMM_OK) return rc;

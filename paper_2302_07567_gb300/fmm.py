@@ -29,7 +29,7 @@ FMM_SERIAL = 64
 EXPORT = dict(gbar=0, perm=1, nodes=2, bbox=3, axis=4, p2p=5, m2l=6, multipole=7, local=8)
 STAGES = ["setup", "tree", "upward", "traversal", "host_wait", "m2l", "l2l", "p2p_l2p",
           "adj_l2pt_l2lt", "adj_m2lt", "adj_m2mt", "adj_near", "adj_source", "total", "adj_total", "adj_lists",
-          "l2p", "unused"]
+          "l2p", "p2m"]
 
 _lib = None
 

@@ -101,6 +101,16 @@ def _node_rel(a, b):
     return np.where(den > 0, num / np.where(den > 0, den, 1), num)
 
 
+def test_p2p_interactions_counted_on_device(case, gpu64):
+    """stats()["p2p_interactions"] (sum |S_t||S_s| over the P2P list minus the
+    N self pairs, summed by the traversal kernel) against the exported list."""
+    plan = gpu64[0]
+    cnt = plan.export("nodes")[:, 1].astype(np.int64)
+    pairs = plan.export("p2p").astype(np.int64)
+    total = int(np.sum(cnt[pairs[:, 0] - 1] * cnt[pairs[:, 1] - 1])) - len(case["x"])
+    assert plan.stats()["p2p_interactions"] == total
+
+
 def test_multipoles_and_locals_fp64(case, gpu64):
     plan = gpu64[0]
     ref, rp = case["ref"], case["ref_plan"]
@@ -272,6 +282,9 @@ def test_size_aware_variant_matches_oracle(name):
     E, B = plan.field(X, Pm, Q)
     np.testing.assert_array_equal(plan.export("p2p"), np.array(sorted(ref.p2p), dtype=np.int32))
     np.testing.assert_array_equal(plan.export("m2l"), np.array(sorted(ref.m2l), dtype=np.int32).reshape(-1, 2))
+    cnt = plan.export("nodes")[:, 1].astype(np.int64)
+    pairs = plan.export("p2p").astype(np.int64)
+    assert plan.stats()["p2p_interactions"] == int(np.sum(cnt[pairs[:, 0] - 1] * cnt[pairs[:, 1] - 1])) - N
     Er, Br = bldtt.fmm_fields(x, p, q, n, leaf, eta, plan=ref)
     assert metrics.field_error(E.cpu().numpy(), B.cpu().numpy(), Er.numpy(), Br.numpy()) < 1e-12
     rng = np.random.default_rng(5)
