@@ -1,18 +1,28 @@
 """Benchmark of the GB300 relativistic space-charge FMM.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--passes fwd|fwd+adj]
-                [--impl ours|reference]
+                [--impl ours|reference] [--eta E] [--eta-alt E2] [--recompute] [--no-extras]
 
 A step is one pass of the whole hot path on one batch of synthetic input:
-setup (gbar), tree build, upward pass, dual tree traversal, list sort, M2L,
-L2L, P2P + L2P (the forward field), and with --passes fwd+adj the adjoint
-(the gradients of sum wE.E + wB.B with respect to x, p and q).  The metric
-is particles per second of that step.  Inputs are resident on the GPU when
-the timed region starts; L2 is flushed (a 512 MiB write) before every timed
-step because one batch is smaller than L2.  Under torchrun every rank runs
-its own replica of the workload (the problems are independent, no data-path
-collective) and the reported value is the sum over ranks of particles per
-second at the slowest rank's time ("scaling": "weak").
+setup (gbar), tree build, upward pass, dual tree traversal with the list
+ordering, M2L, L2L, P2P and L2P (the forward field), and with --passes
+fwd+adj the adjoint (the gradients of sum wE.E + wB.B with respect to x, p
+and q).  The metric is particles per second of that step.  The default
+workload is the largest single-GPU beam: 2^24 particles of a core-halo
+bunch at gamma 200 (n = 8, N0 = 256, eta = 0.5), FP32, forward + adjoint.
+Inputs are resident on the GPU when the timed region starts; they are
+larger than L2, and L2 is flushed (a 512 MiB write) before every timed step
+anyway.  Under torchrun every rank runs its own replica of the workload (the
+problems are independent, no data-path collective) and the reported value is
+the sum over ranks of particles per second at the slowest rank's time
+("scaling": "weak").
+
+Beside the timed steps rank 0 measures, each bounded in time: the FP32 FMA
+rate of the GPU (the roofline peak); every hot kernel alone, in a plan that
+runs the stages one after another (the roofline's kernel durations); the
+same beam at a second admissibility parameter with its own error; the FP64
+GPU FMM against FP32 on a 2^20 draw of the beam; and the CPU oracle on all
+host cores and on one core.
 
 --impl reference times the FP64 CPU oracle (serial BLDTT + autograd adjoint)
 on the host cores on a bounded sample of the same workload; it is a
@@ -38,24 +48,23 @@ if ROOT not in sys.path:
 from paper_2302_07567_gb300.workloads import WORKLOADS, make_beam, make_weights, sample_targets  # noqa: E402
 
 METRIC = "particles/s (E,B on all N; fwd and fwd+adjoint) at fixed rel. L2 error vs FP64"
-# hot kernels: stage name -> (algorithmic flop per unit, stats key counting the units).
-# The FP32 adjoint without the gbar term evaluates both roles of every
-# near-field pair in one kernel (stage adj_near, 84 flop per pair; its
-# adj_source stage is then the far field and the chain rule only); otherwise
-# adj_near is the target side (46) and adj_source the source side (67).
+# ALU-bound hot kernels: stage name -> (algorithmic flop per unit, stats key
+# counting the units).  The FP32 adjoint without the gbar term evaluates both
+# roles of every near-field pair in one kernel (stage adj_near, 84 flop per
+# pair; its adj_source stage is then the far field and the chain rule only);
+# otherwise adj_near is the target side (46) and adj_source the source side (67).
 HOT = {"m2l": (32.0, "m2l_interactions"), "p2p_l2p": (32.0, "p2p_interactions"),
        "adj_m2lt": (32.0, "m2l_interactions")}
 HOT_FUSED = {"adj_near": (84.0, "p2p_interactions")}
 HOT_SPLIT = {"adj_near": (46.0, "p2p_interactions"), "adj_source": (67.0, "p2p_interactions")}
-# DRAM bytes (read + write) per launch of each hot kernel on the cylinder64k
-# fwd+adj step, from one `ncu --set full` capture per kernel (summary and
-# command in profiles/hot_kernels_cylinder64k.md).  Valid only while the
-# kernel is unchanged since that capture; reported for that workload only.
-TRAFFIC_CYL64K = {"m2l": 2674688, "adj_m2lt": 3963392, "adj_near": 9885696 + 15360, "p2p_l2p": 3494144}
-CONCURRENT = ("adj_near", "adj_m2lt")  # stages that overlap each other (two streams)
+# Stage name of each hot kernel in the DRAM capture summary
+KERNEL_OF = {"m2l": "k_m2l_pair", "p2p_l2p": "k_p2p_l2p", "adj_m2lt": "k_adj_m2l_pair", "adj_near": "k_adj_near"}
+CONCURRENT = ("adj_near", "adj_m2lt")  # stages that share the GPU by default (two streams)
 CONCURRENT_FP32_FWD = ("p2p_l2p", "m2l")  # FP32 forward: near-field P2P beside M2L and L2L
-SMS = 152          # GB300 streaming multiprocessors
-FP32_LANES = 128   # FP32 FMA lanes per SM
+# HBM-bound stages: algorithmic bytes per particle (reads + writes of the
+# data each stage must move once, FP32 plans; the bytes of the tree follow
+# the passes of its algorithm, see hbm_bytes below)
+HBM_FALLBACK_GBS = 6800.0  # only if the driver's measured peaks are absent
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -64,9 +73,17 @@ SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.act
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="cylinder64k", choices=sorted(WORKLOADS))
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="corehalo16m", choices=sorted(WORKLOADS))
+    ap.add_argument("--N", type=int, default=None, help="particles (default: the workload's); a draw of the same beam")
+    ap.add_argument("--eta", type=float, default=None, help="admissibility parameter (default: the workload's)")
+    ap.add_argument("--eta-alt", type=float, default=0.4,
+                    help="second admissibility parameter measured beside the line, with its own error (0: none)")
+    ap.add_argument("--recompute", action="store_true",
+                    help="FMM_RECOMPUTE: the per-level expansions are not kept between the forward and the adjoint")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the serial per-kernel pass, the second eta, the FP64 side leg and the CPU baselines")
     ap.add_argument("--passes", default="fwd+adj", choices=["fwd", "fwd+adj"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -152,6 +169,70 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
+def hbm_peak():
+    """Measured STREAM-style copy bandwidth of the GB300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def hbm_bytes(st, w, N):
+    """Algorithmic bytes of the HBM-bound stages of one FP32 forward.
+
+    tree: the presort (8 passes of 8-bit digits over the 3N 12-byte (key,
+      index) records, each read and written once per pass: 576 B/particle),
+      the partition levels above the 4096-slot subtrees (per level each of the
+      3 index arrays is read and written and its ranks read: 36 B/particle)
+      and the subtree pass (the 3 index arrays and x read, the leaf order
+      written: 40 B/particle);
+    p2m: the particles' positions and masses (two float4) read once and the
+      leaves' multipoles written once (4 m floats per leaf);
+    l2p: positions (two float4) and near-field partial sums (two float4) read,
+      the leaf's cumulative local (6 m floats) read once per leaf, the leaf
+      order index read, E and B (6 floats) written.
+    """
+    kappa, m = st["kappa"], (w.n + 1) ** 3
+    leaves = 1 << kappa
+    top = max(0, kappa - max(0, (4096 // max(1, w.leaf)).bit_length() - 1))
+    tree = N * (576 + 36 * top + 40)
+    p2m = N * 32 + leaves * 4 * m * 4
+    l2p = N * (32 + 32 + 4 + 24) + leaves * 6 * m * 4
+    return {"tree": tree, "p2m": p2m, "l2p": l2p}
+
+
+def fp32_peak(fmm, dev):
+    """FP32 FMA throughput measured on this GPU (scalar and paired forms)."""
+    r = {"scalar_tflops": fmm.fp32_fma_rate(False, dev), "paired_tflops": fmm.fp32_fma_rate(True, dev)}
+    r["tflops"] = max(r["scalar_tflops"], r["paired_tflops"])
+    return r
+
+
+def traffic_of(kernel_stage, workload, N):
+    """DRAM bytes per launch of a hot kernel from the committed ncu capture
+    summary, scaled from the captured size to N particles.  None when there is
+    no capture for this workload, or when the kernel's source changed since it
+    was taken (the summary records the SHA-256 of the source file)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_corehalo.json")
+    try:
+        with open(path) as f:
+            cap = json.load(f)
+    except (OSError, ValueError):
+        return None, "no capture summary"
+    k = KERNEL_OF.get(kernel_stage)
+    e = cap.get("kernels", {}).get(k)
+    if e is None or cap.get("workload") != workload:
+        return None, f"no capture of {k} on {workload}"
+    src = os.path.join(ROOT, "paper_2302_07567_gb300", "csrc", e["source"])
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if sha != e["source_sha256"]:
+        return None, f"{e['source']} changed since the capture"
+    return e["bytes"] * N / cap["N"], f"ncu capture at N={cap['N']} scaled by N ({e['source']} unchanged)"
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -163,32 +244,38 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = WORKLOADS[args.workload]
-    N = w.N
-    x, p, q = make_beam(args.workload)
+    N = w.N if args.N is None else int(args.N)
+    eta = w.eta if args.eta is None else args.eta
+    x, p, q = make_beam(args.workload, N=N)
     wE, wB = make_weights(N)
     out_dt = torch.float32 if args.precision == "fp32" else torch.float64
     X, Pm, Q = (torch.as_tensor(a, device=dev) for a in (x, p, q))
     WE, WB = torch.as_tensor(wE, device=dev, dtype=out_dt), torch.as_tensor(wB, device=dev, dtype=out_dt)
     adj = args.passes == "fwd+adj"
-    sa_flag = fmm.FMM_SIZE_AWARE if args.size_aware else 0
-    gb_flag = fmm.FMM_GBAR_TERM if args.gbar_term else 0
-    plan = fmm.Plan(N, w.n, w.leaf, w.eta, precision=args.precision, flags=fmm.FMM_TIMING | sa_flag | gb_flag)
+    flags = (fmm.FMM_SIZE_AWARE if args.size_aware else 0) | (fmm.FMM_GBAR_TERM if args.gbar_term else 0)
+    flags |= fmm.FMM_RECOMPUTE if args.recompute else 0
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    peak32 = fp32_peak(fmm, dev) if args.precision == "fp32" and not args.profile else None
 
-    def step():
-        E, B = plan.field(X, Pm, Q)
+    def make_plan(extra=0, e=eta):
+        return fmm.Plan(N, w.n, w.leaf, e, precision=args.precision, flags=flags | extra)
+
+    plan = make_plan(fmm.FMM_TIMING)
+
+    def step(pl):
+        E, B = pl.field(X, Pm, Q)
         if adj:
-            return plan.adjoint(X, Pm, Q, WE, WB)
+            return pl.adjoint(X, Pm, Q, WE, WB)
         return E, B
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        step(plan)
     torch.cuda.synchronize()
     st0 = plan.stats()
     hot = dict(HOT, **(HOT_FUSED if args.precision == "fp32" and not args.gbar_term else HOT_SPLIT))
-    stage_hist = {k: [] for k in hot}
-    step_ms = []
+    stage_hist = {}
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = fmm.kernel_launches()
@@ -199,11 +286,10 @@ def run_ours(args, rank, world, local):
         for k in range(args.steps):
             flush.zero_()
             ev0[k].record(stream)
-            step()
+            step(plan)
             ev1[k].record(stream)
-            st = plan.stats()  # stage events of this step (same stream)
-            for k in hot:
-                stage_hist[k].append(st["stage_ms"][k])
+            for name, v in plan.stats()["stage_ms"].items():  # this step's stage events (same stream)
+                stage_hist.setdefault(name, []).append(v)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     launches = fmm.kernel_launches() - launches0
@@ -211,22 +297,25 @@ def run_ours(args, rank, world, local):
     if args.profile:
         plan.close()
         return
-    for k in range(args.steps):
-        step_ms.append(ev0[k].elapsed_time(ev1[k]))
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     t_steps = sum(step_ms) / 1e3
     t_max = max_over_ranks(t_steps, world, dev)
     value = N * world * args.steps / t_max
+    stage_med = {k: statistics.median(v) for k, v in stage_hist.items()}
 
     # end to end through the public API with host buffers: H2D of the step's
     # inputs from pinned memory, the step, D2H of its results into pinned
     # memory, all inside the timed region, and the host waits for the results
-    # at the end of every step (as a host-side integrator must)
+    # at the end of every step (as a host-side integrator must).  The plan is
+    # warm from the device-resident timing: one more warm-up step, then up to
+    # five timed steps.
     hx, hp, hq = (torch.as_tensor(a).pin_memory() for a in (x, p, q))
     hwE, hwB = torch.as_tensor(wE, dtype=out_dt).pin_memory(), torch.as_tensor(wB, dtype=out_dt).pin_memory()
     outs = None
     h2d = (hx.numel() + hp.numel() + hq.numel()) * 8 + ((hwE.numel() + hwB.numel()) * hwE.element_size() if adj else 0)
+    e2e_steps = min(args.steps, 5)
     e2e_ms = []
-    for k in range(max(args.warmup, 3) + args.steps):
+    for k in range(1 + e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -241,103 +330,192 @@ def run_ours(args, rank, world, local):
         for o, r in zip(outs, res):
             o.copy_(r, non_blocking=True)
         torch.cuda.synchronize()
-        if k >= max(args.warmup, 3):
+        if k >= 1:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del Xd, Pd, Qd, res, E, B
     d2h = sum(o.numel() * o.element_size() for o in outs)
     e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world, dev)
-    e2e_value = N * world * args.steps / e2e_t
-
-    # accuracy of this configuration against the FP64 brute force on sampled targets
-    tg = torch.as_tensor(sample_targets(N, 4096), device=dev)
-    E, B = plan.field(X, Pm, Q)
-    st = plan.stats()
-    Ed, Bd = fmm.direct_field(X, Pm, Q, gbar=st["gbar"], targets=tg)
+    e2e_value = N * world * e2e_steps / e2e_t
+    del outs, hx, hp, hq, hwE, hwB
 
     def rel(a, b):
         return float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))
 
+    # accuracy of this configuration against the FP64 brute force on sampled targets
+    tg = torch.as_tensor(sample_targets(N, 4096), device=dev)
+    E, B = plan.field(X, Pm, Q)
+    gbar = plan.stats()["gbar"]
+    Ed, Bd = fmm.direct_field(X, Pm, Q, gbar=gbar, targets=tg)
     err = max(rel(E[tg], Ed), rel(B[tg], Bd))
+    del E, B
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
 
-    side = {}
-    if rank == 0 and not args.no_fp64_side and args.precision == "fp32":
-        p64 = fmm.Plan(N, w.n, w.leaf, w.eta, precision="fp64", flags=sa_flag)
-        for _ in range(2):
-            p64.field(X, Pm, Q)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
-        a.record(stream)
-        for _ in range(reps):
-            E64, B64 = p64.field(X, Pm, Q)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t64 = a.elapsed_time(b) / 1e3 / reps
-        err64 = max(rel(E64[tg], Ed), rel(B64[tg], Bd))
-        side = {"fp64_fwd_particles_per_s": N / t64, "fp64_fwd_err": err64, "fp32_fwd_err": err}
-        p64.close()
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        extra = run_extras(args, fmm, torch, dev, w, N, eta, x, p, q, X, Pm, Q, WE, WB, adj, flags, step, rel, tg,
+                           Ed, Bd, hot, st0)
+    del X, Pm, Q, WE, WB
+    torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel, ALU bound: FP32 SIMT peak
-    # = SMs x 128 lanes x 2 flop x SM clock (median sampled under load)
+    # roofline of the dominant kernel: the ALU-bound kernels against the
+    # measured FP32 FMA rate, each timed alone in the serial pass (its own
+    # duration), beside the stage time it takes inside the overlapped step
     clocks = clk.summary()
-    mhz = clocks["sm_mhz"] or 2070.0
-    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12 if args.precision == "fp32" else None
     kernels = {}
-    for k, (per, unit) in hot.items():
-        ms = statistics.median(stage_hist[k]) if stage_hist[k] else 0.0
-        if ms <= 0.0:
-            continue
-        flop = per * st0[unit]
-        traffic = (TRAFFIC_CYL64K.get(k) if args.workload == "cylinder64k" and args.precision == "fp32" and not args.size_aware
-                   and not args.gbar_term and args.passes == "fwd+adj" else None)
-        kernels[k] = {"ms": ms, "tflops": flop / (ms / 1e3) / 1e12,
-                      "frac": (flop / (ms / 1e3) / 1e12 / peak) if peak else None, "traffic": traffic}
-    # the adjoint runs its target side and M2L^T on two streams at once: their
-    # stage times are shared-GPU times, so the dominant kernel is chosen among
-    # the stages that have the GPU to themselves
+    serial = extra.get("serial_stage_ms", {})
     conc = set(CONCURRENT) | (set(CONCURRENT_FP32_FWD) if args.precision == "fp32" else set())
-    for k in conc:
-        if k in kernels:
-            kernels[k]["concurrent"] = True
-    # the longest stage that has the GPU to itself, else (every hot stage
-    # overlapping another) the longest stage, measured while sharing the GPU
-    alone = [k for k in kernels if k not in conc]
-    dom = max(alone or list(kernels), key=lambda k: kernels[k]["ms"])
-    roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"], "peak": peak, "unit": "TFLOP/s",
-            "frac": kernels[dom]["frac"], "traffic": kernels[dom]["traffic"],
-            "concurrent": kernels[dom].get("concurrent", False),
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock)",
-            "flop_basis": "algorithmic flop per pair (FMA = 2): M2L and M2L^T 32 per point pair, P2P 32, "
-                          "adjoint near field 84 per particle pair for both roles in one kernel (FP32), "
-                          "else 46 (target side) and 67 (source side)",
-            "kernels": kernels}
+    for k, (per, unit) in hot.items():
+        flop = per * st0[unit]
+        in_step = stage_med.get(k, 0.0)
+        alone = serial.get(k, 0.0)
+        d = {"flop": flop, "ms_in_step": in_step, "shares_gpu_in_step": k in conc}
+        if alone > 0:
+            d.update(ms=alone, tflops=flop / (alone / 1e3) / 1e12)
+            if peak32:
+                d["frac"] = d["tflops"] / peak32["tflops"]
+        if in_step > 0 and peak32:
+            d["frac_in_step"] = flop / (in_step / 1e3) / 1e12 / peak32["tflops"]
+        kernels[k] = d
+    timed = [k for k in kernels if "ms" in kernels[k]]
+    roof = None
+    if timed:
+        dom = max(timed, key=lambda k: kernels[k]["ms"])
+        traffic, traffic_basis = traffic_of(dom, args.workload, N)
+        roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["tflops"],
+                "peak": peak32["tflops"] if peak32 else None, "unit": "TFLOP/s",
+                "frac": kernels[dom].get("frac"), "traffic": traffic, "traffic_basis": traffic_basis,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "timing": "kernel alone: stage events of an FMM_SERIAL plan (every stage on one stream, "
+                          "one kernel after another), median of its steps",
+                "peak_basis": (f"measured: FP32 FMA-rate kernel on this GPU, {peak32['scalar_tflops']:.1f} TFLOP/s "
+                               f"scalar, {peak32['paired_tflops']:.1f} paired; SM clock median "
+                               f"{clocks['sm_mhz']} MHz during the timed steps") if peak32 else None,
+                "flop_basis": "algorithmic flop per pair (FMA = 2): M2L and M2L^T 32 per point pair, P2P 32, "
+                              "adjoint near field 84 per particle pair for both roles in one kernel (FP32), "
+                              "else 46 (target side) and 67 (source side)",
+                "kernels": kernels}
+
+    # HBM-bound stages of the forward (tree with its presort, P2M, L2P)
+    hpk, hbasis = hbm_peak()
+    hbm = {}
+    if args.precision == "fp32":
+        for k, b in hbm_bytes(st0, w, N).items():
+            ms = stage_med.get({"tree": "tree", "p2m": "p2m", "l2p": "l2p"}[k], 0.0)
+            if ms > 0:
+                hbm[k] = {"ms": ms, "bytes": b, "gbs": b / (ms / 1e3) / 1e9, "frac": b / (ms / 1e3) / 1e9 / hpk}
+        hbm["peak_gbs"] = hpk
+        hbm["peak_basis"] = hbasis
+        hbm["bytes_basis"] = hbm_bytes.__doc__.split("\n\n")[0] + " (see bench.py hbm_bytes)"
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "warmup": warm, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic (seeded beam generator)",
-            "config": {"workload": args.workload, "N": N, "degree": w.n, "leaf": w.leaf, "eta": w.eta,
+            "config": {"workload": args.workload, "N": N, "degree": w.n, "leaf": w.leaf, "eta": eta,
                        "passes": args.passes, "precision": args.precision, "replicas": world,
+                       "recompute": bool(args.recompute),
                        "lists": "size-aware (M2L -> P2P below m^2 pairs)" if args.size_aware else "paper (Alg. 17)",
                        "adjoint_gbar": "gbar(p) live" if args.gbar_term else "gbar held fixed",
-                       "l2": "flushed before every timed step (512 MiB write)", "note": w.note},
+                       "l2": ("inputs larger than L2, and L2 flushed before every timed step (512 MiB write)"
+                              if N * 56 > (129 << 20) else "L2 flushed before every timed step (512 MiB write)"),
+                       "note": w.note},
             "rel_l2_error_vs_fp64_direct": err, "error_targets": 4096,
-            "stage_ms": {k: round(v, 4) for k, v in st0["stage_ms"].items() if v},
-            "lists": {"p2p_pairs": st0["p2p_pairs"], "m2l_pairs": st0["m2l_pairs"], "kappa": st0["kappa"]},
+            "stage_ms": {k: round(v, 4) for k, v in stage_med.items() if v},
+            "lists": {"p2p_pairs": st0["p2p_pairs"], "m2l_pairs": st0["m2l_pairs"], "kappa": st0["kappa"],
+                      "p2p_interactions": st0["p2p_interactions"], "m2l_interactions": st0["m2l_interactions"]},
             "wall_ms_per_step": 1e3 * t_wall / args.steps,
-            "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
             "gpu_launches": launches, "launches_per_step": launches / args.steps,
-            "roofline": roof, "clocks": clocks, **side,
+            "roofline": roof, "hbm": hbm, "fp32_peak": peak32, "clocks": clocks,
+            **{k: v for k, v in extra.items() if k not in ("serial_stage_ms", "cpu_baseline")},
         }
-        if world == 1:
-            line["cpu_baseline"] = cpu_baseline(args.workload, adj)
+        if "cpu_baseline" in extra:
+            line["cpu_baseline"] = extra["cpu_baseline"]
         print(json.dumps(line), flush=True)
-    plan.close()
+    barrier(world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_extras(args, fmm, torch, dev, w, N, eta, x, p, q, X, Pm, Q, WE, WB, adj, flags, step, rel, tg, Ed, Bd, hot,
+               st0):
+    """Rank 0: per-kernel attribution, the second eta, the FP64 side leg and
+    the CPU baselines (each bounded so the whole bench ends in minutes)."""
+    out = {}
+    # every kernel timed alone: a serial plan, one warm-up and two timed steps
+    sp = fmm.Plan(N, w.n, w.leaf, eta, precision=args.precision, flags=flags | fmm.FMM_SERIAL | fmm.FMM_TIMING)
+    step(sp)
+    hist = {}
+    for _ in range(2):
+        step(sp)
+        for k, v in sp.stats()["stage_ms"].items():
+            hist.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    out["serial_stage_ms"] = {k: statistics.median(v) for k, v in hist.items()}
+    out["serial_stage_ms_report"] = {k: round(v, 3) for k, v in out["serial_stage_ms"].items() if v}
+    sp.close()
+    del sp
+    torch.cuda.empty_cache()
+
+    # the same beam at a second admissibility parameter, with its own error
+    if args.eta_alt and args.eta_alt != eta:
+        ap = fmm.Plan(N, w.n, w.leaf, args.eta_alt, precision=args.precision, flags=flags)
+        step(ap)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        a.record()
+        for _ in range(reps):
+            step(ap)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        E, B = ap.field(X, Pm, Q)
+        e2 = max(rel(E[tg], Ed), rel(B[tg], Bd))
+        out["eta_alt"] = {"eta": args.eta_alt, "value": N / (ms / 1e3), "unit": "particles/s", "ms_per_step": ms,
+                          "steps": reps, "rel_l2_error_vs_fp64_direct": e2, "error_targets": 4096}
+        del E, B
+        ap.close()
+        del ap
+        torch.cuda.empty_cache()
+
+    # FP64 GPU FMM against FP32 on a 2^20 draw of the same beam (the FP64
+    # forward at 2^24 would take minutes)
+    if args.precision == "fp32" and not args.no_fp64_side:
+        Ns = min(N, 1 << 20)
+        xs, ps, qs = make_beam(args.workload, N=Ns)
+        Xs, Ps, Qs = (torch.as_tensor(v, device=dev) for v in (xs, ps, qs))
+        tgs = torch.as_tensor(sample_targets(Ns, 4096), device=dev)
+        side = {"sample": f"{args.workload} beam drawn at N={Ns} (same distribution), forward only, "
+                          f"error vs FP64 brute force on 4096 sampled targets"}
+        ref = None
+        for prec in ("fp32", "fp64"):
+            pl = fmm.Plan(Ns, w.n, w.leaf, eta, precision=prec)
+            pl.field(Xs, Ps, Qs)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            E, B = pl.field(Xs, Ps, Qs)
+            b.record()
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = fmm.direct_field(Xs, Ps, Qs, gbar=pl.stats()["gbar"], targets=tgs)
+            side[f"{prec}_fwd_particles_per_s"] = Ns / (a.elapsed_time(b) / 1e3)
+            side[f"{prec}_fwd_err"] = max(rel(E[tgs], ref[0]), rel(B[tgs], ref[1]))
+            pl.close()
+            del pl, E, B
+            torch.cuda.empty_cache()
+        out["fp64_side"] = side
+        del Xs, Ps, Qs
+
+    out["cpu_baseline"] = cpu_baseline(args.workload, adj)
+    return out
 
 
 def _oracle_step(x, p, q, wE, wB, w, adj):
@@ -349,12 +527,12 @@ def _oracle_step(x, p, q, wE, wB, w, adj):
         bldtt.fmm_fields(x, p, q, w.n, w.leaf, w.eta, plan=plan)
 
 
-def cpu_baseline(workload: str, adj: bool, budget_s: float = 12.0):
-    """The oracle, as it stands, on a bounded sample of the workload on the host cores."""
+def _cpu_leg(workload: str, adj: bool, budget_s: float, threads: int, Ns: int):
+    """Time the oracle on fresh draws of Ns particles until budget_s of CPU time is spent (at most 3 draws)."""
     import torch
-    torch.set_num_threads(os.cpu_count() or 1)
+    torch.set_num_threads(threads)
     w = WORKLOADS[workload]
-    Ns = min(w.N, 16384)
+    Ns = min(w.N, Ns)
     done, t_all, n_all = 0, 0.0, 0
     while t_all < budget_s and done < 3:
         x, p, q = make_beam(workload, N=Ns, seed_offset=done)
@@ -367,6 +545,25 @@ def cpu_baseline(workload: str, adj: bool, budget_s: float = 12.0):
     return {"value": n_all / t_all, "unit": "particles/s", "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"{done} x serial FP64 BLDTT {'forward+autograd adjoint' if adj else 'forward'} on "
                       f"N={Ns} draws of {workload} (n={w.n}, leaf={w.leaf}, eta={w.eta}); {t_all:.1f} s of CPU time"}
+
+
+def cpu_baseline(workload: str, adj: bool, budget_s: float = 10.0):
+    """The oracle, as it stands, on bounded samples of the workload: on all the
+    host's cores, and on one core (the paper's CPU baseline is a single core,
+    Section 11), the latter in a child process pinned to one CPU with one
+    thread in every numerical library."""
+    allc = _cpu_leg(workload, adj, budget_s, os.cpu_count() or 1, 16384)
+    code = ("import os, sys, json; os.sched_setaffinity(0, {min(os.sched_getaffinity(0))}); "
+            f"sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench._cpu_leg({workload!r}, {bool(adj)}, {budget_s}, 1, 4096)))")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+        one = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else {"error": r.stderr[-300:]}
+    except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+        one = {"error": str(e)[:300]}
+    allc["single_core"] = one
+    return allc
 
 
 def run_reference(args, rank, world):

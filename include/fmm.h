@@ -49,7 +49,8 @@ typedef enum fmm_status {
   FMM_EOVERFLOW = 3,    /* an interaction-list capacity was exceeded; raise it with
                            fmm_plan_set_capacity, re-attach a workspace, call again  */
   FMM_ENONFINITE = 4,   /* x or p holds NaN or Inf                                   */
-  FMM_ESTATE = 5,       /* fmm_field_adjoint before a successful fmm_field           */
+  FMM_ESTATE = 5,       /* fmm_field_adjoint before a successful fmm_field; export of
+                           expansions an FMM_RECOMPUTE adjoint overwrote            */
   FMM_ECUDA = 6,        /* a CUDA runtime call failed (see fmm_last_cuda_error)      */
   FMM_EBOUNDS = 7       /* an index check of FMM_BOUNDS_CHECK failed                 */
 } fmm_status;
@@ -62,8 +63,19 @@ typedef enum fmm_precision {
 } fmm_precision;
 
 typedef enum fmm_flags {
-  FMM_RECOMPUTE = 1u,    /* the adjoint recomputes multipoles and local fields instead
-                            of reusing those of the forward call                      */
+  FMM_RECOMPUTE = 1u,    /* one set of per-level expansions instead of two: the
+                            adjoint's node weights W and adjoint moments Lambda are
+                            written over the forward's locals L and multipoles M
+                            (with FMM_GBAR_TERM, whose M2L^T reads M, Lambda keeps a
+                            buffer of its own), so fmm_plan_workspace_bytes shrinks
+                            by about 7.5 (n+1)^3 x (number of clusters) bytes
+                            (FP32).  The adjoint's near field, which reads the leaf
+                            locals, runs before the far-field chain that overwrites
+                            them, on the caller's stream (no second stream).  A
+                            further adjoint call without a new fmm_field recomputes
+                            the upward pass, M2L and L2L first; fmm_plan_export of
+                            multipoles or locals after an adjoint returns
+                            FMM_ESTATE                                               */
   FMM_BOUNDS_CHECK = 2u, /* after the traversal (and the adjoint's source-major lists)
                             check on the device: node tables, the leaf order is a
                             permutation, list pairs in range, sorted and matching

@@ -1690,7 +1690,7 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   // beside the source side's far field (side stream) the target side keeps
   // to half of the SMs' block slots, so the other branch finds room; alone
   // it takes every resident slot
-  if (P->kappa > 0 && P->overlap) {
+  if (P->kappa > 0 && P->adj_overlap) {
     int sms = 0;
     if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)4 * sms);  // 3-4 measured best at 2^9 leaves
@@ -1766,7 +1766,7 @@ int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
   unsigned grid = (unsigned)items;
   const size_t smem = stage_bytes<float>(6, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;
   if (int rc = set_smem(k_adj_near, smem)) return rc;
-  if (P->kappa > 0 && P->overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
+  if (P->kappa > 0 && P->adj_overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;
     if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)3 * sms);
@@ -1813,10 +1813,13 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if ((P->flags & FMM_BOUNDS_CHECK) && (rc = run_bounds_check(P, true, s)) != FMM_OK) return rc;
     P->transposed_valid = true;
   }
-  if (!P->locals_valid || (P->flags & FMM_RECOMPUTE)) {  // the forward's multipoles and locals again
+  // the forward's multipoles and locals again, where an FMM_RECOMPUTE
+  // adjoint has overwritten them (W over L, Lambda over M)
+  if (!P->locals_valid) {
     if ((rc = run_upward(P, s)) != FMM_OK) return rc;
     if ((rc = run_m2l(P, s)) != FMM_OK) return rc;
     if ((rc = run_l2l(P, s)) != FMM_OK) return rc;
+    P->locals_valid = true;
   }
   const int gs = (int)std::min<int64_t>(8192, div_up(P->N, 256));
   k_adj_prep<T><<<gs, 256, 0, s>>>(static_cast<const T*>(wE), static_cast<const T*>(wB), P->N,
@@ -1826,13 +1829,27 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   if ((rc = record(P, 16, s)) != FMM_OK) return rc;
   // Two independent branches from here: the far field of the source side
   // (L2P^T, L2L^T, M2L^T, M2M^T, mostly latency-bound transfers) on the
-  // plan's side stream, the target-side particle kernel (ALU-bound) on the
+  // plan's side stream, the near-field particle kernel (ALU-bound) on the
   // caller's stream.  They share no buffer that either writes: W and Lambda
-  // have their own, the target side reads the forward's locals.
-  // With FMM_SERIAL the chain runs first on the caller's stream.
+  // have their own, the near field reads the forward's leaf locals.
+  // With FMM_SERIAL the chain runs first on the caller's stream; with
+  // FMM_RECOMPUTE W is written over the locals, so the near field runs
+  // first and the chain after it, on the caller's stream.
   const bool chain = P->kappa > 0;
   const bool gb = (P->flags & FMM_GBAR_TERM) != 0;
-  const bool ov = chain && P->overlap;
+  const bool rec = (P->flags & FMM_RECOMPUTE) != 0;
+  const bool ov = chain && P->overlap && !rec;
+  P->adj_overlap = ov;
+  const bool fused = std::is_same<T, float>::value && !gb;  // FP32 without the gbar term: both roles in one kernel
+  auto near = [&]() -> int {
+    int r;
+    if (fused) r = launch_adj_near(P, s);
+    else if constexpr (std::is_same<T, float>::value) r = launch_adj_target<T, true>(P, s);  // FP32: only with the gbar term
+    else r = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
+    if (r != FMM_OK) return r;
+    return record(P, 10, s);
+  };
+  if (rec && (rc = near()) != FMM_OK) return rc;
   if (chain) {
     cudaStream_t t = s;
     if (ov) {
@@ -1852,14 +1869,9 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if ((rc = run_transfer<T, 4, false>(P, ws_ptr<T>(P, L.lbuf), t, cap, ov)) != FMM_OK) return rc;  // M2M^T
     if ((rc = record(P, 13, t)) != FMM_OK) return rc;
     if (ov) FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
+    if (rec) P->locals_valid = false;  // W and Lambda now hold what L and M held
   }
-  // FP32 without the gbar term: both near-field roles in one kernel
-  const bool fused = std::is_same<T, float>::value && !gb;
-  if (fused) rc = launch_adj_near(P, s);
-  else if constexpr (std::is_same<T, float>::value) rc = launch_adj_target<T, true>(P, s);  // FP32: only with the gbar term
-  else rc = gb ? launch_adj_target<T, true>(P, s) : launch_adj_target<T, false>(P, s);
-  if (rc != FMM_OK) return rc;
-  if ((rc = record(P, 10, s)) != FMM_OK) return rc;
+  if (!rec && (rc = near()) != FMM_OK) return rc;
   if (ov) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
   if (gb && (rc = gbar_sum<T>(P, chain, s)) != FMM_OK) return rc;
   if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, fused, s)) != FMM_OK) return rc;
@@ -1867,6 +1879,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   (void)x;
   P->adj_timed = (P->flags & FMM_TIMING) != 0;
   P->adj_chain = chain;
+  P->adj_order = ov ? 0 : (rec ? 2 : 1);
   return FMM_OK;
 }
 

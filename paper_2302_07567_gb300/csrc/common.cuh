@@ -122,7 +122,8 @@ struct fmm_plan_s {
   fmm::Cheb cheb;
   fmm::ChebD chebd;
   bool transposed_valid = false;  // source-major lists built for the current forward
-  bool locals_valid = false;      // multipole / local buffers hold the forward's values
+  bool locals_valid = false;      // multipole / local buffers hold the forward's values (an
+                                  // FMM_RECOMPUTE adjoint overwrites them with W and Lambda)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool have_forward = false;
@@ -141,6 +142,9 @@ struct fmm_plan_s {
   bool split_fwd = false;  // the last forward ran the FP32 near field and L2P as kernels of their own
   bool adj_timed = false;  // the last adjoint recorded its stage events
   bool adj_chain = false;  // ... and had a far-field chain (kappa > 0)
+  bool adj_overlap = false;  // the running adjoint has its two branches on two streams
+  int adj_order = 0;       // stage order of the last adjoint: 0 branches overlapped, 1 chain then
+                           // near field (FMM_SERIAL), 2 near field then chain (FMM_RECOMPUTE)
 };
 
 namespace fmm {
@@ -356,6 +360,9 @@ int record_stage(fmm_plan_s* P, int k, cudaStream_t s);
 // synchronises the stream, FMM_EBOUNDS on any violation
 int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
+// FP32 M2L with a kernel specialised on the points per axis (reads the
+// multipoles directly); otherwise the generic kernel reads the source table
+bool m2l_specialised(const fmm_plan_s* P);
 int run_l2l(fmm_plan_s* P, cudaStream_t s, bool per_level = false);
 int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s);
 // FP32 forward split: near-field P2P into the adjoint's per-particle buffers

@@ -502,8 +502,13 @@ int m2l_t(fmm_plan_s* P, cudaStream_t s) {
 
 }  // namespace
 
+bool m2l_specialised(const fmm_plan_s* P) {
+  return P->precision == FMM_FP32 && P->eta <= 0.5 && !(P->flags & FMM_TEST_POLY_KERNEL) &&
+         (P->np1 == 3 || P->np1 == 5 || P->np1 == 7 || P->np1 == 9);
+}
+
 int run_m2l(fmm_plan_s* P, cudaStream_t s) {
-  if (P->precision == FMM_FP32 && P->eta <= 0.5 && !(P->flags & FMM_TEST_POLY_KERNEL)) {
+  if (m2l_specialised(P)) {
     switch (P->np1) {
       case 3: return launch_fast<3, 3, 1>(P, s);
       // paired kernels, block sizes from sweeps of fwd+adj steps: n = 4 (64

@@ -122,9 +122,15 @@ void make_layout(fmm_plan_s* P) {
   L.px = take(N * V4);
   L.pb = take(N * V4);
   L.pl = take(N * V4);
+  // Expansions.  FMM_RECOMPUTE keeps one set: the adjoint's node weights W
+  // overwrite the locals L (both [C+1][6][m]) and its adjoint moments Lambda
+  // the multipoles M (both [C+1][4][m]; with the gbar term M2L^T reads M, so
+  // Lambda keeps a buffer of its own).  The M2L source table exists only for
+  // the generic M2L kernel.
+  const bool rec = (P->flags & FMM_RECOMPUTE) != 0;
   L.mpole = take(C1 * 4 * m * R);
   L.local = take(C1 * 6 * m * R);
-  L.srct = take(C1 * m * 2 * V4);
+  L.srct = take(m2l_specialised(P) ? 0 : C1 * m * 2 * V4);
   L.tmat = take(C1 * 3 * (size_t)P->np1 * P->np1 * R);
   L.front0 = take((size_t)P->cap_frontier * 8);
   L.front1 = take((size_t)P->cap_frontier * 8);
@@ -149,8 +155,8 @@ void make_layout(fmm_plan_s* P) {
   L.thist = take(4 * 256 * 4);
   L.m2l_order = take(C1 * 4);
   L.m2l_sorder = take(C1 * 4);
-  L.wbuf = take(C1 * 6 * m * R);
-  L.lbuf = take(C1 * 4 * m * R);
+  L.wbuf = rec ? L.local : take(C1 * 6 * m * R);
+  L.lbuf = rec && !(P->flags & FMM_GBAR_TERM) ? L.mpole : take(C1 * 4 * m * R);
   L.p2p_sdc = take((size_t)P->cap_p2p * 32);
   L.m2l_sdc = take((size_t)P->cap_m2l * 32);
   L.gfar = take(C1 * 8);
@@ -498,15 +504,16 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     P->stage_ms[13] = el(0, 8);
     if (P->adj_timed) {
       // the near-field kernel runs on the caller's stream from event 16 while
-      // L2P^T .. M2M^T run on the side stream, or after them (no overlap);
-      // the source side starts when both have finished
-      const bool ov = P->overlap && P->adj_chain;
-      P->stage_ms[11] = ov || !P->adj_chain ? el(16, 10) : el(13, 10);  // near-field particle kernel
+      // L2P^T .. M2M^T run on the side stream (order 0), after them (order
+      // 1, FMM_SERIAL) or before them (order 2, FMM_RECOMPUTE); the source
+      // side starts when both have finished
+      const int ord = P->adj_chain ? P->adj_order : 2;
+      P->stage_ms[11] = ord == 1 ? el(13, 10) : el(16, 10);  // near-field particle kernel
       if (P->adj_chain) {
-        P->stage_ms[8] = el(16, 11);   // L2P^T + L2L^T
+        P->stage_ms[8] = ord == 2 ? el(10, 11) : el(16, 11);  // L2P^T + L2L^T
         P->stage_ms[9] = el(11, 12);   // M2L^T
         P->stage_ms[10] = el(12, 13);  // M2M^T
-        P->stage_ms[12] = ov ? std::min(el(10, 14), el(13, 14)) : el(10, 14);  // source side + chain rule
+        P->stage_ms[12] = ord == 0 ? std::min(el(10, 14), el(13, 14)) : (ord == 1 ? el(10, 14) : el(13, 14));
       } else {
         P->stage_ms[12] = el(10, 14);
       }
@@ -585,6 +592,7 @@ int fmm_plan_export(fmm_plan_t P, int what, void* host, size_t bytes) {
     }
     case FMM_EXPORT_MULTIPOLE:
     case FMM_EXPORT_LOCAL: {
+      if (!P->locals_valid) return FMM_ESTATE;  // an FMM_RECOMPUTE adjoint overwrote them
       const int nc = what == FMM_EXPORT_MULTIPOLE ? 4 : 6;
       if (!need(sizeof(double) * C * nc * m)) return FMM_EINVAL;
       const size_t cnt = (size_t)(C + 1) * nc * m;

@@ -243,6 +243,7 @@ int upward_t(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
   const Layout& L = P->lay;
   rc = run_transfer<T, 4, true>(P, ws_ptr<T>(P, L.mpole), s, xfer_cap, per_level);  // M2M, all levels
   if (rc != FMM_OK) return rc;
+  if (m2l_specialised(P)) return FMM_OK;  // the specialised M2L reads the multipoles directly
   const int64_t total = (P->C + 1) * (int64_t)P->m;
   k_srctab<T><<<(unsigned)std::min<int64_t>(div_up(total, 256), 8192), 256, 0, s>>>(
       ws_ptr<T>(P, L.mpole), ws_ptr<NodeGeo>(P, L.ngeo), P->C, P->cheb, P->m,

@@ -55,6 +55,15 @@ def test_host_side_argument_checks(libpath):
     lib.fmm_plan_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     nb = ctypes.c_size_t()
     assert lib.fmm_plan_workspace_bytes(h, ctypes.byref(nb)) == 0 and nb.value > 4096 * 100
+    # FMM_RECOMPUTE: the adjoint's W and Lambda share the forward's L and M
+    # buffers, (C+1) (6 + 4) m floats less (C = 127 clusters, m = 125 here)
+    h2 = ctypes.c_void_p()
+    assert lib.fmm_plan_create(ctypes.byref(h2), 4096, 4, 64, 0.5, 1, 1) == 0
+    nb2 = ctypes.c_size_t()
+    assert lib.fmm_plan_workspace_bytes(h2, ctypes.byref(nb2)) == 0
+    assert nb.value - nb2.value >= 128 * 10 * 125 * 4
+    lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
+    lib.fmm_plan_destroy(h2)
     lib.fmm_field.argtypes = [ctypes.c_void_p] * 7
     one = ctypes.c_void_p(256)
     assert lib.fmm_field(h, one, one, one, one, one, None) == 2  # no workspace attached

@@ -113,6 +113,41 @@ def test_second_adjoint_recomputes_and_matches(case):
         assert float((v + w - u).norm() / u.norm()) < 1e-12
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_recompute_mode_matches_oracle_and_default(case, prec, tol):
+    """FMM_RECOMPUTE keeps one set of expansions: W and Lambda overwrite the
+    locals and multipoles, the near field runs before the far-field chain,
+    and a second adjoint recomputes the upward pass, M2L and L2L.  Its
+    gradients equal those of the default plan bit for bit (every sum keeps
+    its order) and so match the oracle's frozen-plan gradient."""
+    plan, dx, dp, dq = gpu_grad(case, prec, flags=fmm.FMM_RECOMPUTE)
+    _, ex, ep, eq = gpu_grad(case, prec)
+    gx, gp, gq = case["ref"]
+    for a, d, b in ((dx, ex, gx), (dp, ep, gp), (dq, eq, gq)):
+        np.testing.assert_array_equal(a, d)
+        assert rel(a, b) < tol, rel(a, b)
+    N = case["x"].shape[0]
+    X, Pm, Q = dev(case["x"], case["p"], case["q"])
+    odt = plan.out_dtype
+    WE, WB = dev(case["wE"], case["wB"], dtype=odt)
+    if plan.stats()["kappa"] > 0:  # the adjoint overwrote the expansions: no export
+        with pytest.raises(fmm.FMMError):
+            plan.export("local")
+    again = plan.adjoint(X, Pm, Q, WE, WB)  # recomputes the locals first
+    for a, d in zip(again, (dx, dp, dq)):
+        np.testing.assert_array_equal(a.cpu().numpy(), d)
+    plan.field(X, Pm, Q)
+    assert plan.export("local").shape[0] == plan.stats()["nodes"]
+
+
+def test_recompute_mode_shrinks_the_workspace():
+    N = 1 << 16
+    small = fmm.Plan(N, 8, 256, 0.5, precision="fp32", flags=fmm.FMM_RECOMPUTE).workspace_bytes
+    full = fmm.Plan(N, 8, 256, 0.5, precision="fp32").workspace_bytes
+    C, m = (1 << 9) - 1, 9 ** 3
+    assert full - small >= (C + 1) * 10 * m * 4  # W (6 m) and Lambda (4 m) floats per cluster
+
+
 def test_fp32_adjoint_within_truncation_of_direct_gradient():
     x, p, q = make_beam("gauss256k", N=4096)
     wE, wB = make_weights(4096)
@@ -173,3 +208,8 @@ def test_gbar_term_matches_oracle(name):
         assert rel(dq, gq.numpy()) < tol, (prec, rel(dq, gq.numpy()))
         _, dx0, dp0, dq0 = gpu_grad(c, prec)
         assert rel(dp - dp0, want) < ttol, (prec, rel(dp - dp0, want))
+        # one set of expansions (FMM_RECOMPUTE): Lambda keeps its own buffer
+        # beside the multipoles the gbar term reads; the same gradients
+        _, rx, rp, rq = gpu_grad(c, prec, flags=fmm.FMM_GBAR_TERM | fmm.FMM_RECOMPUTE)
+        for a, b in ((rx, dx), (rp, dp), (rq, dq)):
+            np.testing.assert_array_equal(a, b)
