@@ -939,10 +939,14 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
     const float4* __restrict__ sdc, const float4* __restrict__ wle, const float4* __restrict__ wlb,
     const float* __restrict__ Lcum, Cheb ch, ChebD cd, int m, int groups, int chunks, int64_t nitems,
     float4* __restrict__ g1, float4* __restrict__ g2) {
-  // staged partner pairs: 12 float4 (48 floats), 24 components as (partner
-  // 2q, partner 2q+1): -x_hi (3), -x_lo (3), a, b~ (3), -b~ (3), w^E (3),
-  // w^B (3), -w^B (3), 0, 0
-  constexpr int kRow = 6;  // float4 per staged partner
+  // staged partner pairs: 12 float4 (48 floats) at a 13-float4 stride, 24
+  // components as (partner 2q, partner 2q+1): -x_hi (3), -x_lo (3), a, b~ (3),
+  // -b~ (3), w^E (3), w^B (3), -w^B (3), 0, 0
+  // a staged pair takes 13 float4 (52 floats, 48 used): with a 52-float
+  // stride the scattered staging stores of a warp fall into 2 ways of the
+  // shared-memory banks instead of 8 (48 = 16 mod 32)
+  constexpr int kPairStride = 52;
+  constexpr int kRow = 7;  // float4 per staged partner, rounded up (6.5)
   constexpr int NC = 7;    // dL/dx' (3), dL/da', dL/db~' (3)
   extern __shared__ unsigned char smem_raw[];
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
@@ -1026,7 +1030,7 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
 #pragma unroll
           for (int q = 0; q < 24; ++q) c[q] = 0.f;
         }
-        float* f = reinterpret_cast<float*>(smem_raw) + (threadIdx.x >> 1) * 48 + (threadIdx.x & 1);
+        float* f = reinterpret_cast<float*>(smem_raw) + (threadIdx.x >> 1) * kPairStride + (threadIdx.x & 1);
 #pragma unroll
         for (int q = 0; q < 24; ++q) f[2 * q] = c[q];
       }
@@ -1035,7 +1039,7 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
       const int npq = (nj + 1) >> 1;
       const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
       for (int qq = grp * share2; qq < q1; ++qq) {
-        const float4* s4 = reinterpret_cast<const float4*>(smem_raw) + 12 * qq;
+        const float4* s4 = reinterpret_cast<const float4*>(smem_raw) + (kPairStride / 4) * qq;
         const float4 S0 = s4[0], S1 = s4[1], S2 = s4[2], S3 = s4[3], S4 = s4[4], S5 = s4[5];
         const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(S0.x, S0.y)), __fadd2_rn(L0, make_float2(S1.z, S1.w)));
         const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(S0.z, S0.w)), __fadd2_rn(L1, make_float2(S2.x, S2.y)));
@@ -1046,7 +1050,8 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
         inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
         const float2 inv2 = __fmul2_rn(inv, inv);
         const float2 r3 = __fmul2_rn(inv2, inv);
-        const float2 r5 = __fmul2_rn(r3, inv2);
+        // K = R / |R|^3 serves both roles
+        const float2 kx = __fmul2_rn(r3, rx), ky = __fmul2_rn(r3, ry), kz = __fmul2_rn(r3, rz);
         const float2 aj = make_float2(S3.x, S3.y);
         const float2 bx = make_float2(S3.z, S3.w), by = make_float2(S4.x, S4.y), bz = make_float2(S4.z, S4.w);
         const float2 nbx = make_float2(S5.x, S5.y), nby = make_float2(S5.z, S5.w);
@@ -1062,17 +1067,17 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
                           __ffma2_rn(NA, ey, __ffma2_rn(B2, wx, __fmul2_rn(B0, nwz))))));
         const float2 vz = __ffma2_rn(aj, WE2, __ffma2_rn(WB0, by, __ffma2_rn(WB1, nbx,
                           __ffma2_rn(NA, ez, __ffma2_rn(B0, wy, __fmul2_rn(B1, nwx))))));
+        // J v = r3 v - 3 r5 (R . v) R = r3 v + c K with c = -3 r^-2 (R . v)
         const float2 rv = __ffma2_rn(rz, vz, __ffma2_rn(ry, vy, __fmul2_rn(rx, vx)));
-        const float2 nc3 = __fmul2_rn(__fmul2_rn(r5, m3), rv);
-        pp[0] = __ffma2_rn(nc3, rx, __ffma2_rn(r3, vx, pp[0]));
-        pp[1] = __ffma2_rn(nc3, ry, __ffma2_rn(r3, vy, pp[1]));
-        pp[2] = __ffma2_rn(nc3, rz, __ffma2_rn(r3, vz, pp[2]));
+        const float2 c = __fmul2_rn(__fmul2_rn(inv2, m3), rv);
+        pp[0] = __ffma2_rn(c, kx, __ffma2_rn(r3, vx, pp[0]));
+        pp[1] = __ffma2_rn(c, ky, __ffma2_rn(r3, vy, pp[1]));
+        pp[2] = __ffma2_rn(c, kz, __ffma2_rn(r3, vz, pp[2]));
         // source role, summed with the sign flipped at the end: K . w^E_j, K x w^B_j
-        const float2 re = __ffma2_rn(rz, ez, __ffma2_rn(ry, ey, __fmul2_rn(rx, ex)));
-        pp[3] = __ffma2_rn(r3, re, pp[3]);
-        pp[4] = __ffma2_rn(r3, __ffma2_rn(ry, wz, __fmul2_rn(rz, nwy)), pp[4]);
-        pp[5] = __ffma2_rn(r3, __ffma2_rn(rz, wx, __fmul2_rn(rx, nwz)), pp[5]);
-        pp[6] = __ffma2_rn(r3, __ffma2_rn(rx, wy, __fmul2_rn(ry, nwx)), pp[6]);
+        pp[3] = __ffma2_rn(kz, ez, __ffma2_rn(ky, ey, __ffma2_rn(kx, ex, pp[3])));
+        pp[4] = __ffma2_rn(ky, wz, __ffma2_rn(kz, nwy, pp[4]));
+        pp[5] = __ffma2_rn(kz, wx, __ffma2_rn(kx, nwz, pp[5]));
+        pp[6] = __ffma2_rn(kx, wy, __ffma2_rn(ky, nwx, pp[6]));
       }
     }
 #pragma unroll
@@ -1764,7 +1769,7 @@ int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
   const int nt = groups * NT;
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
-  const size_t smem = stage_bytes<float>(6, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;
+  const size_t smem = stage_bytes<float>(7, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;  // kRow 7
   if (int rc = set_smem(k_adj_near, smem)) return rc;
   if (P->kappa > 0 && P->adj_overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;

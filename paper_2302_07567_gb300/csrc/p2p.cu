@@ -39,8 +39,10 @@
 namespace fmm {
 namespace {
 
+constexpr int kP2PPairLeaf = 256;  // near-field P2P with two targets per thread from this leaf size
+
 template <typename T, int KPT, bool POLY>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (KPT == 1 ? 8 : 4) : 1) k_p2p_l2p(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift, const unsigned int* __restrict__ err,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,
@@ -137,9 +139,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
       for (int k = 0; k < KPT; ++k)
 #pragma unroll
         for (int c = 0; c < 6; ++c) part[k][c] = T(0);
-      float2 pp2[6];  // paired partial sums (FP32 path): even and odd sources of the leaf
+      float2 pp2[KPT][6];  // paired partial sums (FP32 path): even and odd sources of the leaf
 #pragma unroll
-      for (int c = 0; c < 6; ++c) pp2[c] = make_float2(0.f, 0.f);
+      for (int k = 0; k < KPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pp2[k][c] = make_float2(0.f, 0.f);
       for (int64_t base = 0; base < scnt; base += blockDim.x) {
         __syncthreads();
         const int64_t j = base + threadIdx.x;
@@ -170,34 +174,42 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
         }
         __syncthreads();
         const int nj = (int)min64(blockDim.x, scnt - base);
-        if constexpr (kSplit && KPT == 1) {  // source pairs, paired arithmetic
+        if constexpr (kSplit) {  // source pairs, paired arithmetic, KPT targets per thread
           const int npq = (nj + 1) >> 1;
           const int share2 = (npq + groups - 1) / groups, q1 = min(npq, (grp + 1) * share2);
-          const float2 X0 = make_float2(X[0][0], X[0][0]), X1 = make_float2(X[0][1], X[0][1]),
-                       X2 = make_float2(X[0][2], X[0][2]);
-          const float2 L0 = make_float2(XL[0][0], XL[0][0]), L1 = make_float2(XL[0][1], XL[0][1]),
-                       L2 = make_float2(XL[0][2], XL[0][2]);
+          float2 X0[KPT], X1[KPT], X2[KPT], L0[KPT], L1[KPT], L2[KPT];
+#pragma unroll
+          for (int k = 0; k < KPT; ++k) {
+            X0[k] = make_float2(X[k][0], X[k][0]);
+            X1[k] = make_float2(X[k][1], X[k][1]);
+            X2[k] = make_float2(X[k][2], X[k][2]);
+            L0[k] = make_float2(XL[k][0], XL[k][0]);
+            L1[k] = make_float2(XL[k][1], XL[k][1]);
+            L2[k] = make_float2(XL[k][2], XL[k][2]);
+          }
           for (int q = grp * share2; q < q1; ++q) {
             const float4* s4 = reinterpret_cast<const float4*>(sp) + 7 * q;
             const float4 A = s4[0], Bq = s4[1], Cq = s4[2], Dq = s4[3], Eq = s4[4], Fq = s4[5], Gq = s4[6];
-            const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(A.x, A.y)), __fadd2_rn(L0, make_float2(Fq.x, Fq.y)));
-            const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(A.z, A.w)), __fadd2_rn(L1, make_float2(Fq.z, Fq.w)));
-            const float2 rz = __fadd2_rn(__fadd2_rn(X2, make_float2(Bq.x, Bq.y)), __fadd2_rn(L2, make_float2(Gq.x, Gq.y)));
-            const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
-            float2 inv;
-            inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
-            inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
-            const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
-            const float2 ar3 = __fmul2_rn(make_float2(Bq.z, Bq.w), r3);
-            pp2[0] = __ffma2_rn(ar3, rx, pp2[0]);
-            pp2[1] = __ffma2_rn(ar3, ry, pp2[1]);
-            pp2[2] = __ffma2_rn(ar3, rz, pp2[2]);
-            const float2 cx = __ffma2_rn(make_float2(Eq.z, Eq.w), ry, __fmul2_rn(make_float2(Cq.z, Cq.w), rz));
-            const float2 cy = __ffma2_rn(make_float2(Dq.z, Dq.w), rz, __fmul2_rn(make_float2(Dq.x, Dq.y), rx));
-            const float2 cz = __ffma2_rn(make_float2(Eq.x, Eq.y), rx, __fmul2_rn(make_float2(Cq.x, Cq.y), ry));
-            pp2[3] = __ffma2_rn(r3, cx, pp2[3]);
-            pp2[4] = __ffma2_rn(r3, cy, pp2[4]);
-            pp2[5] = __ffma2_rn(r3, cz, pp2[5]);
+#pragma unroll
+            for (int k = 0; k < KPT; ++k) {
+              const float2 rx = __fadd2_rn(__fadd2_rn(X0[k], make_float2(A.x, A.y)), __fadd2_rn(L0[k], make_float2(Fq.x, Fq.y)));
+              const float2 ry = __fadd2_rn(__fadd2_rn(X1[k], make_float2(A.z, A.w)), __fadd2_rn(L1[k], make_float2(Fq.z, Fq.w)));
+              const float2 rz = __fadd2_rn(__fadd2_rn(X2[k], make_float2(Bq.x, Bq.y)), __fadd2_rn(L2[k], make_float2(Gq.x, Gq.y)));
+              const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+              float2 inv;
+              inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+              inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+              // K = R / |R|^3; E += a K, B += b~ x K (12 operations per source pair)
+              const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+              const float2 kx = __fmul2_rn(r3, rx), ky = __fmul2_rn(r3, ry), kz = __fmul2_rn(r3, rz);
+              const float2 aa = make_float2(Bq.z, Bq.w);
+              pp2[k][0] = __ffma2_rn(aa, kx, pp2[k][0]);
+              pp2[k][1] = __ffma2_rn(aa, ky, pp2[k][1]);
+              pp2[k][2] = __ffma2_rn(aa, kz, pp2[k][2]);
+              pp2[k][3] = __ffma2_rn(make_float2(Eq.z, Eq.w), ky, __ffma2_rn(make_float2(Cq.z, Cq.w), kz, pp2[k][3]));
+              pp2[k][4] = __ffma2_rn(make_float2(Dq.z, Dq.w), kz, __ffma2_rn(make_float2(Dq.x, Dq.y), kx, pp2[k][4]));
+              pp2[k][5] = __ffma2_rn(make_float2(Eq.x, Eq.y), kx, __ffma2_rn(make_float2(Cq.x, Cq.y), ky, pp2[k][5]));
+            }
           }
           continue;
         }
@@ -235,9 +247,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_p2p_l2p(
           }
         }
       }
-      if constexpr (kSplit && KPT == 1) {
+      if constexpr (kSplit) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) part[0][c] = pp2[c].x + pp2[c].y;
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) part[k][c] = pp2[k][c].x + pp2[k][c].y;
       }
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
@@ -456,6 +470,12 @@ int run_p2p_l2p(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
 
 int run_p2p_near(fmm_plan_s* P, cudaStream_t s) {
   if (P->precision != FMM_FP32) return FMM_EINVAL;
+  // two targets per thread on leaves of 256 or more: each staged source pair
+  // then feeds two independent chains (2^24 core-halo beam, N0 = 256: P2P
+  // alone 457.6 -> 424.5 ms)
+  if (P->leaf >= kP2PPairLeaf)
+    return launch<float, 2, false>(P, nullptr, nullptr, s, ws_ptr<float4>(P, P->lay.adj_part),
+                                   ws_ptr<float4>(P, P->lay.adj_part2));
   return launch<float, 1, false>(P, nullptr, nullptr, s, ws_ptr<float4>(P, P->lay.adj_part),
                                  ws_ptr<float4>(P, P->lay.adj_part2));
 }

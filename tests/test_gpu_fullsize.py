@@ -172,3 +172,33 @@ def test_corehalo_shape_fp32_against_fp64_at_1m():
     e32 = metrics.field_error(res["fp32"][0][tg], res["fp32"][1][tg], Ed.numpy(), Bd.numpy())
     assert e64 < 1e-3 and e32 <= e64 + 1e-6, (e32, e64)
     assert metrics.field_error(*res["fp32"], *res["fp64"]) < 1e-5
+
+
+@pytest.mark.parametrize("eta", [0.3, 0.5])
+def test_paper_sweep_regime_cube_n10(eta):
+    """The regime of the paper's Fig. 2 sweep (Section 5): the uniform cube at
+    gamma = 50, degree n = 10 (a degree without specialised kernels) and
+    leaf size N0 = (n + 1)^3 = 1331, on a 16,384-particle draw.  FP64 within
+    1e-12 of the oracle's FMM, FP32 within 1e-5 of it and within the FMM's
+    truncation error + 1e-6 of the brute force."""
+    N, n, leaf = 16384, 10, 1331
+    x, p, q = make_beam("cube", N=N)
+    ref_plan = bldtt.build_plan(x, p, n, leaf, eta)
+    assert len(ref_plan.m2l) > 0
+    Er, Br = bldtt.fmm_fields(x, p, q, n, leaf, eta, plan=ref_plan)
+    Er, Br = Er.numpy(), Br.numpy()
+    X, Pm, Q = dev(x, p, q)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        plan = fmm.Plan(N, n, leaf, eta, precision=prec)
+        E, B = plan.field(X, Pm, Q)
+        np.testing.assert_array_equal(plan.export("m2l"), np.array(sorted(ref_plan.m2l), dtype=np.int32))
+        out[prec] = (E.double().cpu().numpy(), B.double().cpu().numpy())
+        plan.close()
+    assert metrics.field_error(*out["fp64"], Er, Br) < 1e-12
+    assert metrics.field_error(*out["fp32"], Er, Br) < 1e-5
+    tg = sample_targets(N, 2048, tag=11)
+    Ed, Bd = physics.direct_fields(x, p, q, targets=tg)
+    trunc = metrics.field_error(Er[tg], Br[tg], Ed.numpy(), Bd.numpy())
+    e32 = metrics.field_error(out["fp32"][0][tg], out["fp32"][1][tg], Ed.numpy(), Bd.numpy())
+    assert e32 < trunc + 1e-6, (e32, trunc)
