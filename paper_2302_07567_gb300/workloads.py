@@ -53,7 +53,8 @@ WORKLOADS = {
         "Gaussian sigma 1 mm, gamma 30 with 2% spread, p along z; Gaussian loss weights"),
     "corehalo16m": Workload(
         "corehalo16m", 5, 1 << 24, 8, 256, 0.5, "fwd+adj",
-        "95% Gaussian core sigma 0.1 mm, 5% uniform shell 0.3-0.6 mm, gamma 200, 0.1% spread"),
+        "95% Gaussian core sigma 0.1 mm, 5% uniform shell 0.3-0.6 mm, gamma 200, 0.1% spread",
+        {"recompute": True}),
     "cube": Workload(
         "cube", 6, 1_280_000, 4, 125, 0.5, "fwd",
         "the paper's Fig. 2/3 workload: uniform in [0,1]^3 m, gamma 50 along z"),
