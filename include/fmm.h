@@ -154,6 +154,38 @@ int fmm_plan_set_workspace(fmm_plan_t plan, void* device_ptr, size_t bytes);
 int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q,
               void* E, void* B, void* stream);
 
+/* Forward pass of a tracking step (not in the paper, whose Alg. 12 builds
+ * the tree and the lists for every field evaluation).  The tree's membership
+ * (which particles form each cluster) and the P2P and M2L lists of the last
+ * successful fmm_field or fmm_field_reuse on this plan are kept; gbar, every
+ * cluster's box (the bounding box of its unchanged members at the new
+ * positions, Section 2) and every stage after the tree are recomputed.  If
+ * every M2L pair is still admissible (Alg. 8) under the new boxes and gbar,
+ * the kept lists are used as they are: they still partition all N^2 particle
+ * pairs into direct and admissible pairs, so the result carries the FMM's
+ * error bound (Section 4), though it may differ from fmm_field on the same
+ * input, whose traversal can choose other pairs.  Otherwise, or with no
+ * earlier forward on the plan, the call builds tree and lists anew exactly as
+ * fmm_field does and sets *rebuilt = 1 (else 0; rebuilt may be NULL).
+ * Arguments, outputs, the one wait on `stream` and the errors as fmm_field;
+ * with unchanged x and p the result equals fmm_field's bit for bit. */
+int fmm_field_reuse(fmm_plan_t plan, const double* x, const double* p, const double* q, void* E, void* B,
+                    void* stream, int* rebuilt);
+
+/* Relativistic Boris push over one time step (not in the paper; the particle
+ * pusher a tracking code runs between field evaluations).  With u = p (the
+ * momentum gamma beta), a_j = q_j dt / (2 mass c0) and gamma(u) = sqrt(1+|u|^2):
+ *   u-  = u + a E,   t = (a c0 / gamma(u-)) B,   s = 2 t / (1 + |t|^2),
+ *   u+  = u- + (u- + u- x t) x s,   u' = u+ + a E,   x' = x + c0 dt u' / gamma(u'),
+ * E, B the fields at x (V/m, T).  x, p: device [N,3] float64, updated in place
+ * (p then lives at the half step); q: device [N] float64 (coulomb); E, B: device
+ * [N,3] in the precision field_precision (FMM_FP32: float, FMM_FP64: double), as
+ * fmm_field writes them; mass in kg > 0, dt in s.  Asynchronous on `stream`.
+ * FMM_EINVAL for NULL pointers, N < 1, a bad precision, mass <= 0 or a
+ * non-finite mass or dt. */
+int fmm_boris_push(double* x, double* p, const double* q, int64_t N, const void* E, const void* B,
+                   int field_precision, double mass, double dt, void* stream);
+
 /* Adjoint of the forward pass of the same plan (not in the paper).  For the
  * loss L = sum_i wE_i . E_i + wB_i . B_i it returns dL/dx [N,3], dL/dp [N,3]
  * and dL/dq [N] (device float64), the exact derivative of the FMM operator

@@ -35,6 +35,7 @@ enum : unsigned {
   kErrOvfP2P = 4u,
   kErrOvfM2L = 8u,
   kErrBounds = 16u,
+  kErrStale = 32u,  // field with reuse: an M2L pair is no longer admissible
 };
 
 // Device-resident counters of one call (first bytes of the workspace).
@@ -328,6 +329,51 @@ inline void particle_shape(int64_t leaf, int kpt, int* NT, int* groups, int* chu
   *chunks = (int)((leaf + (int64_t)kpt * *NT - 1) / ((int64_t)kpt * *NT));
 }
 
+// Admissibility of the cluster pair (t, u) (Alg. 8 with Algs. 6-7):
+// max(r_t, r_u) / d < eta in FP64 with the operations in a fixed order and
+// no contraction, d the stretched centre distance; d = 0 gives inf or NaN,
+// not admissible.  The traversal and the tracking refresh share it, so both
+// take the same decision to the last bit.
+__device__ __forceinline__ bool pair_admissible(const double* __restrict__ ndiam, const double* __restrict__ ncen,
+                                                double gbar, int64_t t, int64_t u, double eta) {
+  const double s[3] = {1.0, 1.0, gbar};
+  const double rt = ndiam[t], ru = ndiam[u];
+  double v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = __dmul_rn(s[k], __dsub_rn(ncen[3 * t + k], ncen[3 * u + k]));
+  const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
+                                        __dmul_rn(v[2], v[2])));
+  const double ratio = __ddiv_rn(rt >= ru ? rt : ru, d);
+  return ratio < eta;
+}
+
+// Centre offset s o (c_a - c_b) / ell of a list pair in stretched, scaled
+// units, stored as hi + lo floats (FP32 plans) or a double4 (FP64 plans).
+template <bool kFP32>
+__device__ __forceinline__ void store_pair_offset(const double* __restrict__ ncen, const double* __restrict__ scal,
+                                                  int64_t a, int64_t b, void* dc, int64_t dst) {
+  const double s3[3] = {1.0, 1.0, scal[0]};
+  const double inv = scal[3];
+  const double* ca = ncen + 3 * a;
+  const double* cb = ncen + 3 * b;
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = __dmul_rn(__dmul_rn(s3[k], __dsub_rn(ca[k], cb[k])), inv);
+  if (kFP32) {
+    float h[3], l[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      h[k] = (float)d[k];
+      l[k] = (float)(d[k] - (double)h[k]);
+    }
+    float4* o = static_cast<float4*>(dc);
+    o[2 * dst] = make_float4(h[0], h[1], h[2], 0.f);
+    o[2 * dst + 1] = make_float4(l[0], l[1], l[2], 0.f);
+  } else {
+    static_cast<double4*>(dc)[dst] = make_double4(d[0], d[1], d[2], 0.0);
+  }
+}
+
 // Node of a breadth-first tree level containing slot `pos`: binary search in
 // the first slots of the 2^level nodes [first, first + count).
 __device__ __forceinline__ int64_t find_node(const int64_t* __restrict__ nstart, int64_t first,
@@ -360,6 +406,11 @@ int record_stage(fmm_plan_s* P, int k, cudaStream_t s);
 // synchronises the stream, FMM_EBOUNDS on any violation
 int run_bounds_check(fmm_plan_s* P, bool source_major, cudaStream_t s);
 int run_m2l(fmm_plan_s* P, cudaStream_t s);
+// field with reuse (track.cu): the boxes of the kept tree membership at the
+// new positions, then the lists' centre offsets and the admissibility of
+// every M2L pair under them (kErrStale on failure)
+int run_refresh(fmm_plan_s* P, const double* x, cudaStream_t s);
+int run_refresh_lists(fmm_plan_s* P, cudaStream_t s);
 // FP32 M2L with a kernel specialised on the points per axis (reads the
 // multipoles directly); otherwise the generic kernel reads the source table
 bool m2l_specialised(const fmm_plan_s* P);

@@ -340,10 +340,18 @@ int fmm_plan_set_workspace(fmm_plan_t P, void* dev, size_t bytes) {
   return FMM_OK;
 }
 
-int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, void* E, void* B, void* stream) {
-  if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
-  if (!P->ws) return FMM_ENOWORKSPACE;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace fmm {
+namespace {
+// Alg. 12.  With reuse the tree's membership and the lists of the last
+// forward stay: the boxes, gbar and everything after them are recomputed,
+// and kStaleLists is returned (E, B unwritten) if an M2L pair is no longer
+// admissible.
+constexpr int kStaleLists = -1;
+
+int forward(fmm_plan_s* P, const double* x, const double* p, const double* q, void* E, void* B, cudaStream_t s,
+            bool reuse) {
   P->have_forward = false;
   P->last_stream = s;
   int rc;
@@ -353,7 +361,7 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   if ((rc = record(P, 0, s)) != FMM_OK) return rc;
   if ((rc = run_setup(P, x, p, q, s)) != FMM_OK) return rc;
   if ((rc = record(P, 1, s)) != FMM_OK) return rc;
-  if ((rc = run_tree(P, x, s)) != FMM_OK) return rc;
+  if ((rc = reuse ? run_refresh(P, x, s) : run_tree(P, x, s)) != FMM_OK) return rc;
   if ((rc = run_prep(P, x, p, q, s)) != FMM_OK) return rc;
   if ((rc = record(P, 2, s)) != FMM_OK) return rc;
   // The upward pass and the traversal are independent, but the traversal is
@@ -361,7 +369,7 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   // (measured: a side-stream upward pass then waits for it), so they run in turn.
   if ((rc = run_upward(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 17, s)) != FMM_OK) return rc;
-  if ((rc = run_traverse(P, s)) != FMM_OK) return rc;
+  if ((rc = reuse ? run_refresh_lists(P, s) : run_traverse(P, s)) != FMM_OK) return rc;
   if ((rc = record(P, 3, s)) != FMM_OK) return rc;
   // The list sizes, error flags and scalars go to pinned host memory right
   // after the traversal, and M2L, L2L and P2P are queued at once: the host
@@ -381,10 +389,13 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   FMM_CUDA_TRY(cudaEventRecord(P->trav_ev, s));
   auto read_back = [&]() -> int {
     FMM_CUDA_TRY(cudaEventSynchronize(P->trav_ev));
-    P->p2p_count = (int64_t)hc->p2p_count;
-    P->m2l_count = (int64_t)hc->m2l_count;
-    P->p2p_work = (double)hc->p2p_work;
+    if (!reuse) {  // with reuse the lists, their sizes and pair counts stay those of the last forward
+      P->p2p_count = (int64_t)hc->p2p_count;
+      P->m2l_count = (int64_t)hc->m2l_count;
+      P->p2p_work = (double)hc->p2p_work;
+    }
     if (hc->err & kErrNonFinite) return FMM_ENONFINITE;
+    if (hc->err & kErrStale) return kStaleLists;
     if ((hc->err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || P->p2p_count > P->cap_p2p ||
         P->m2l_count > P->cap_m2l)
       return FMM_EOVERFLOW;
@@ -441,6 +452,31 @@ int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, v
   P->transposed_valid = false;
   P->locals_valid = true;
   return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+extern "C" {
+
+int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, void* E, void* B, void* stream) {
+  if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
+  if (!P->ws) return FMM_ENOWORKSPACE;
+  return forward(P, x, p, q, E, B, static_cast<cudaStream_t>(stream), false);
+}
+
+int fmm_field_reuse(fmm_plan_t P, const double* x, const double* p, const double* q, void* E, void* B, void* stream,
+                    int* rebuilt) {
+  if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
+  if (!P->ws) return FMM_ENOWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rebuilt) *rebuilt = 0;
+  if (P->have_forward) {
+    const int rc = forward(P, x, p, q, E, B, s, true);
+    if (rc != kStaleLists) return rc;
+  }
+  if (rebuilt) *rebuilt = 1;
+  return forward(P, x, p, q, E, B, s, false);
 }
 
 int fmm_field_adjoint(fmm_plan_t P, const double* x, const double* p, const double* q, const void* wE,

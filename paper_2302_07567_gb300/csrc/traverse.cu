@@ -220,8 +220,6 @@ __device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = gtid >> 5, nwarps = gstride >> 5;
   const uint64_t mask = ((uint64_t)1 << a.shift) - 1;
-  const double s3[3] = {1.0, 1.0, a.scal[0]};
-  const double inv = a.scal[3];
   for (int64_t w = gw; w < 2 * M; w += nwarps) {
     const int j = w >= M ? 1 : 0;
     const int64_t t = w - j * M;
@@ -241,24 +239,7 @@ __device__ void order_lists(cg::grid_group& grid, const ListArgs& a) {
       for (int q = 0; q < n; ++q) r += (staged ? stage[wib][q] : __ldcg(seg + q)) < ki ? 1 : 0;
       const int64_t dst = lo + r;
       J.out[dst] = ki;
-      const double* ca = a.ncen + 3 * (ki >> a.shift);
-      const double* cb = a.ncen + 3 * (ki & mask);
-      double dc[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) dc[d] = (s3[d] * (ca[d] - cb[d])) * inv;
-      if (kFP32) {
-        float h[3], l[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          h[d] = (float)dc[d];
-          l[d] = (float)(dc[d] - (double)h[d]);
-        }
-        float4* o = static_cast<float4*>(J.dc);
-        o[2 * dst] = make_float4(h[0], h[1], h[2], 0.f);
-        o[2 * dst + 1] = make_float4(l[0], l[1], l[2], 0.f);
-      } else {
-        static_cast<double4*>(J.dc)[dst] = make_double4(dc[0], dc[1], dc[2], 0.0);
-      }
+      store_pair_offset<kFP32>(a.ncen, a.scal, (int64_t)(ki >> a.shift), (int64_t)(ki & mask), J.dc, dst);
     }
     __syncwarp();
   }
@@ -301,13 +282,7 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs a) {
         continue;
       }
       const double rt = a.ndiam[t], ru = a.ndiam[u];
-      double v[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) v[k] = __dmul_rn(s[k], __dsub_rn(ncen[3 * t + k], ncen[3 * u + k]));
-      const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
-                                            __dmul_rn(v[2], v[2])));
-      const double ratio = __ddiv_rn(rt >= ru ? rt : ru, d);
-      if (ratio < a.eta) {
+      if (pair_admissible(a.ndiam, ncen, s[2], t, u, a.eta)) {
         if (a.m2sub > 0 && a.ncount[t] * a.ncount[u] < a.m2sub) {
           // fewer particle pairs than proxy-point pairs: every leaf pair under
           // (t, u) goes to P2P instead (all leaves sit at depth kappa)

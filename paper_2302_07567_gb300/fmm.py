@@ -81,6 +81,8 @@ def lib():
         "fmm_kernel_launches": (I64, []),
         "fmm_gamma_bar_noalloc": (I32, [P, I64, P, P]),
         "fmm_fp32_fma_rate": (I32, [P, SZ, I32, ctypes.POINTER(D), P]),
+        "fmm_field_reuse": (I32, [P, P, P, P, P, P, P, ctypes.POINTER(I32)]),
+        "fmm_boris_push": (I32, [P, P, P, I64, P, P, I32, D, D, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -131,6 +133,7 @@ class Plan:
         self._h = h
         self._ws = None
         self.generation = 0  # bumped by every field() call
+        self.last_rebuilt = True
         if capacity is not None:
             self.set_capacity(*capacity)
         self._attach()
@@ -161,11 +164,14 @@ class Plan:
         self._attach()
 
     # -- compute
-    def field(self, x, p, q, E=None, B=None, max_retries: int = 10):
+    def field(self, x, p, q, E=None, B=None, max_retries: int = 10, reuse: bool = False):
         """E, B [N,3] (float32 for fp32 plans, float64 for fp64) of the particles.
 
         On an interaction-list overflow the capacities grow (x4, or to 1.25x
         the counts seen) and the call is repeated, up to ``max_retries`` times.
+        With ``reuse`` (a tracking step, fmm_field_reuse) the tree membership
+        and the interaction lists of the last call stay while they remain
+        admissible; ``last_rebuilt`` tells whether this call built them anew.
         """
         N, dev = self.N, self.device
         _check_in(x, "x", (N, 3), torch.float64, dev)
@@ -177,9 +183,14 @@ class Plan:
             B = torch.empty((N, 3), dtype=self.out_dtype, device=dev)
         _check_in(E, "E", (N, 3), self.out_dtype, dev)
         _check_in(B, "B", (N, 3), self.out_dtype, dev)
+        rebuilt = ctypes.c_int(1)
         for _ in range(max_retries + 1):
             with torch.cuda.device(dev):
-                rc = lib().fmm_field(self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(E), _ptr(B), _stream(dev))
+                if reuse:
+                    rc = lib().fmm_field_reuse(self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(E), _ptr(B), _stream(dev),
+                                               ctypes.byref(rebuilt))
+                else:
+                    rc = lib().fmm_field(self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(E), _ptr(B), _stream(dev))
             if rc != FMM_EOVERFLOW:
                 break
             st = self.stats()
@@ -187,8 +198,9 @@ class Plan:
                               max(4 * st["cap_m2l"], int(1.25 * st["m2l_pairs"]) + 1024),
                               4 * st["cap_frontier"])
         if rc != FMM_OK:
-            raise FMMError(rc, "fmm_field")
+            raise FMMError(rc, "fmm_field_reuse" if reuse else "fmm_field")
         self.generation += 1
+        self.last_rebuilt = bool(rebuilt.value)
         return E, B
 
     def adjoint(self, x, p, q, wE, wB):
@@ -245,6 +257,38 @@ class Plan:
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().fmm_kernel_launches())
+
+
+def boris_push(x, p, q, E, B, mass: float, dt: float):
+    """One relativistic Boris step (fmm_boris_push): x, p updated in place."""
+    dev = x.device
+    N = x.shape[0]
+    _check_in(x, "x", (N, 3), torch.float64, dev)
+    _check_in(p, "p", (N, 3), torch.float64, dev)
+    _check_in(q, "q", (N,), torch.float64, dev)
+    if E.dtype not in (torch.float32, torch.float64) or B.dtype != E.dtype:
+        raise TypeError("E and B must both be float32 or both float64")
+    _check_in(E, "E", (N, 3), E.dtype, dev)
+    _check_in(B, "B", (N, 3), E.dtype, dev)
+    prec = FMM_FP32 if E.dtype == torch.float32 else FMM_FP64
+    with torch.cuda.device(dev):
+        rc = lib().fmm_boris_push(_ptr(x), _ptr(p), _ptr(q), N, _ptr(E), _ptr(B), prec, float(mass), float(dt),
+                                  _stream(dev))
+    if rc != FMM_OK:
+        raise FMMError(rc, "fmm_boris_push")
+
+
+def track(plan: "Plan", x, p, q, mass: float, dt: float, steps: int, reuse: bool = True) -> int:
+    """Advance the beam ``steps`` time steps in its own space-charge field:
+    each step the FMM field (with the previous step's tree and lists while
+    they stay admissible, if ``reuse``) and a Boris push; x and p are
+    updated in place.  Returns how many steps built tree and lists anew."""
+    rebuilds = 0
+    for _ in range(int(steps)):
+        E, B = plan.field(x, p, q, reuse=reuse)
+        rebuilds += int(plan.last_rebuilt) if reuse else 1
+        boris_push(x, p, q, E, B, mass, dt)
+    return rebuilds
 
 
 def fp32_fma_rate(paired: bool, device=None) -> float:

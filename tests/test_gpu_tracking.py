@@ -1,0 +1,116 @@
+"""Tracking with the FMM field, through the C ABI (GPU; not in the paper).
+
+fmm_field_reuse keeps the previous step's tree membership and interaction
+lists while every M2L pair stays admissible; fmm_boris_push moves the beam.
+Checked against the oracle's refreshed plan (oracle.tracking.refresh_plan)
+and its Boris step at every step of a short tracking run: FP64 fields within
+1e-12 of the oracle's FMM on the same plan, positions and momenta within
+1e-12; FP32 fields within 1e-5.  With unchanged input the reuse path equals
+fmm_field bit for bit, and when the particles move too far it builds tree
+and lists anew, again equal to fmm_field.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bldtt, metrics, tracking
+from paper_2302_07567_gb300 import fmm
+from paper_2302_07567_gb300.workloads import make_beam, random_beam
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+QM = 1e7                        # macro-particle: 10^7 electrons
+Q, MASS = -1.602176634e-19 * QM, 9.1093837015e-31 * QM
+
+
+def dev(*arrs):
+    return [torch.as_tensor(np.ascontiguousarray(a), device=DEV) for a in arrs]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_reuse_with_unchanged_input_equals_field(prec):
+    x, p, q = make_beam("cylinder64k", N=6000)
+    X, Pm, Qd = dev(x, p, q)
+    plan = fmm.Plan(6000, 6, 128, 0.5, precision=prec)
+    E0, B0 = [t.clone() for t in plan.field(X, Pm, Qd)]
+    E1, B1 = plan.field(X, Pm, Qd, reuse=True)
+    assert not plan.last_rebuilt
+    assert torch.equal(E0, E1) and torch.equal(B0, B1)
+
+
+def test_boris_kernel_matches_oracle():
+    r = np.random.default_rng(11)
+    N = 5000
+    x, p = r.standard_normal((N, 3)), r.standard_normal((N, 3)) * 20
+    q = np.full(N, Q)
+    E, B = 1e6 * r.standard_normal((N, 3)), 0.5 * r.standard_normal((N, 3))
+    X, Pm, Qd, Ed, Bd = dev(x, p, q, E, B)
+    fmm.boris_push(X, Pm, Qd, Ed, Bd, MASS, 2e-12)
+    xo, po = tracking.boris_push(x, p, q, E, B, MASS, 2e-12)
+    np.testing.assert_allclose(X.cpu().numpy(), xo, rtol=1e-15, atol=1e-18)
+    np.testing.assert_allclose(Pm.cpu().numpy(), po, rtol=1e-15, atol=1e-18)
+    # float fields are widened to double before the step
+    X2, P2 = dev(x, p)
+    fmm.boris_push(X2, P2, Qd, Ed.float(), Bd.float(), MASS, 2e-12)
+    xo2, po2 = tracking.boris_push(x, p, q, Ed.float().double().cpu().numpy(), Bd.float().double().cpu().numpy(),
+                                   MASS, 2e-12)
+    np.testing.assert_allclose(P2.cpu().numpy(), po2, rtol=1e-15, atol=1e-18)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_tracking_steps_match_oracle(prec, tol):
+    """Five steps of a gamma = 10 Gaussian bunch: at every step the GPU field
+    (kept tree and lists) against the oracle's FMM on its refreshed plan, and
+    the pushed particles against the oracle's push of the same fields."""
+    N, n, leaf, eta, dt = 3000, 4, 64, 0.5, 2e-12
+    x, p, _ = random_beam(N, seed=21, gamma=10.0, spread=0.01, angle=1e-3)
+    q = np.full(N, Q)
+    X, Pm, Qd = dev(x, p, q)
+    plan = fmm.Plan(N, n, leaf, eta, precision=prec)
+    oplan = None
+    xo, po = x.copy(), p.copy()
+    for step in range(5):
+        E, B = plan.field(X, Pm, Qd, reuse=True)
+        assert plan.last_rebuilt == (step == 0)
+        if oplan is None:
+            oplan = bldtt.build_plan(xo, po, n, leaf, eta)
+        else:
+            oplan, valid = tracking.refresh_plan(oplan, xo, po)
+            assert valid
+        Er, Br = bldtt.fmm_fields(xo, po, q, n, leaf, eta, plan=oplan)
+        Eg, Bg = E.double().cpu().numpy(), B.double().cpu().numpy()
+        assert metrics.field_error(Eg, Bg, Er.numpy(), Br.numpy()) < tol
+        fmm.boris_push(X, Pm, Qd, E, B, MASS, dt)
+        xo, po = tracking.boris_push(xo, po, q, Eg, Bg, MASS, dt)
+        np.testing.assert_allclose(X.cpu().numpy(), xo, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(Pm.cpu().numpy(), po, rtol=1e-12, atol=1e-12)
+    # the bunch has moved c dt per step along z
+    assert np.mean(xo[:, 2] - x[:, 2]) > 0.9 * 5 * dt * 2.99e8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_reuse_rebuilds_when_lists_go_stale(prec):
+    x, p, q = random_beam(4000, seed=22, gamma=10.0)
+    X, Pm, Qd = dev(x, p, q)
+    plan = fmm.Plan(4000, 4, 64, 0.5, precision=prec)
+    plan.field(X, Pm, Qd)
+    # scatter the particles: the kept boxes overlap their M2L partners
+    x2 = x[np.random.default_rng(3).permutation(4000)]
+    oplan = bldtt.build_plan(x, p, 4, 64, 0.5)
+    _, valid = tracking.refresh_plan(oplan, x2, p)
+    assert not valid
+    X2 = dev(x2)[0]
+    E1, B1 = [t.clone() for t in plan.field(X2, Pm, Qd, reuse=True)]
+    assert plan.last_rebuilt
+    E2, B2 = fmm.Plan(4000, 4, 64, 0.5, precision=prec).field(X2, Pm, Qd)
+    assert torch.equal(E1, E2) and torch.equal(B1, B2)
+
+
+def test_track_helper_counts_rebuilds():
+    x, p, _ = random_beam(2000, seed=23, gamma=10.0)
+    q = np.full(2000, Q)
+    X, Pm, Qd = dev(x, p, q)
+    plan = fmm.Plan(2000, 4, 64, 0.5, precision="fp32")
+    rebuilds = fmm.track(plan, X, Pm, Qd, MASS, 1e-12, steps=4)
+    assert rebuilds == 1  # the first step only
+    assert torch.isfinite(X).all() and torch.isfinite(Pm).all()
