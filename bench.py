@@ -67,6 +67,7 @@ CONCURRENT_FP32_FWD = ("p2p_l2p", "m2l")  # FP32 forward: near-field P2P beside 
 # data each stage must move once, FP32 plans; the bytes of the tree follow
 # the passes of its algorithm, see hbm_bytes below)
 HBM_FALLBACK_GBS = 6800.0  # only if the driver's measured peaks are absent
+ELECTRON_MASS = 9.1093837015e-31  # kg (CODATA 2018), the tracking leg's particle mass
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -490,6 +491,28 @@ def run_extras(args, fmm, torch, dev, w, N, eta, x, p, q, X, Pm, Q, WE, WB, adj,
         ap.close()
         del ap
         torch.cuda.empty_cache()
+
+    # tracking: per step the forward field and a Boris push (electron
+    # charge and mass per particle, dt = 1 ps), with the tree and lists kept
+    # while admissible (fmm_field_reuse) and built anew every step (fmm_field)
+    track = {"dt_s": 1e-12, "steps": 3}
+    for reuse in (True, False):
+        Xt, Pt = X.clone(), Pm.clone()
+        tp = fmm.Plan(N, w.n, w.leaf, eta, precision=args.precision, flags=flags & ~fmm.FMM_RECOMPUTE)
+        fmm.track(tp, Xt, Pt, Q, ELECTRON_MASS, 1e-12, 1, reuse)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rebuilt = fmm.track(tp, Xt, Pt, Q, ELECTRON_MASS, 1e-12, track["steps"], reuse)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / track["steps"]
+        track["reuse" if reuse else "rebuild"] = {"value": N / (ms / 1e3), "unit": "particles/s", "ms_per_step": ms,
+                                                   "tree_and_lists_built": rebuilt}
+        tp.close()
+        del tp, Xt, Pt
+        torch.cuda.empty_cache()
+    out["tracking"] = track
 
     # FP64 GPU FMM against FP32 on a 2^20 draw of the same beam (the FP64
     # forward at 2^24 would take minutes)
