@@ -166,7 +166,11 @@ int fmm_field(fmm_plan_t plan, const double* x, const double* p, const double* q
  * error bound (Section 4), though it may differ from fmm_field on the same
  * input, whose traversal can choose other pairs.  Otherwise, or with no
  * earlier forward on the plan, the call builds tree and lists anew exactly as
- * fmm_field does and sets *rebuilt = 1 (else 0; rebuilt may be NULL).
+ * fmm_field does and sets *rebuilt = 1 (else 0; rebuilt may be NULL).  A call
+ * that follows a stale attempt builds at once without trying the kept lists
+ * (the next call tries again): on large beams the particles' relative motion
+ * carries some of the millions of M2L pairs across the admissibility bound
+ * every step, and the wasted attempts then cost every second step only.
  * Arguments, outputs, the one wait on `stream` and the errors as fmm_field;
  * with unchanged x and p the result equals fmm_field's bit for bit. */
 int fmm_field_reuse(fmm_plan_t plan, const double* x, const double* p, const double* q, void* E, void* B,

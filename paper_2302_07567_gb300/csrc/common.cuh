@@ -141,6 +141,7 @@ struct fmm_plan_s {
   double stage_ms[18] = {};
   bool overlap = true;     // independent branches on two streams (no FMM_SERIAL)
   bool split_fwd = false;  // the last forward ran the FP32 near field and L2P as kernels of their own
+  bool reuse_stale = false;  // the last fmm_field_reuse found the kept lists stale
   bool adj_timed = false;  // the last adjoint recorded its stage events
   bool adj_chain = false;  // ... and had a far-field chain (kappa > 0)
   bool adj_overlap = false;  // the running adjoint has its two branches on two streams
@@ -199,6 +200,14 @@ __device__ __forceinline__ float rsqrt_normal(float x) {
 }
 template <>
 __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_normal(x); }
+// 1/x by the hardware approximation (rcp.approx) for a normal positive
+// float, on the transcendental unit instead of the FMA pipe: r^-3 as
+// rsqrt(d) rcp(d) takes one FMA-pipe multiply instead of two.
+__device__ __forceinline__ float rcp_normal(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 

@@ -210,9 +210,13 @@ void make_tables(fmm_plan_s* P) {
   }
 }
 
+// Default list capacities (cluster pairs): 128 P2P partners per leaf and 64
+// M2L pairs per cluster (the 2^24 core-halo beam at gamma 200 needs 114 and
+// 24; the gamma-50 cylinder 12 and 1).  A list that overflows is grown by
+// the caller (fmm_plan_set_capacity) and the call repeated.
 void default_caps(fmm_plan_s* P) {
-  if (P->cap_p2p <= 0) P->cap_p2p = 64 * P->nleaves + 1024;
-  if (P->cap_m2l <= 0) P->cap_m2l = 128 * P->C + 1024;
+  if (P->cap_p2p <= 0) P->cap_p2p = 128 * P->nleaves + 1024;
+  if (P->cap_m2l <= 0) P->cap_m2l = 64 * P->C + 1024;
   if (P->cap_frontier <= 0) P->cap_frontier = P->cap_p2p + P->cap_m2l;
 }
 
@@ -462,6 +466,7 @@ extern "C" {
 int fmm_field(fmm_plan_t P, const double* x, const double* p, const double* q, void* E, void* B, void* stream) {
   if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
   if (!P->ws) return FMM_ENOWORKSPACE;
+  P->reuse_stale = false;
   return forward(P, x, p, q, E, B, static_cast<cudaStream_t>(stream), false);
 }
 
@@ -471,9 +476,15 @@ int fmm_field_reuse(fmm_plan_t P, const double* x, const double* p, const double
   if (!P->ws) return FMM_ENOWORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (rebuilt) *rebuilt = 0;
-  if (P->have_forward) {
+  // A call right after a stale attempt builds at once instead of trying
+  // again: where the kept lists go stale every step the wasted attempts are
+  // then every second step only.
+  const bool attempt = P->have_forward && !P->reuse_stale;
+  P->reuse_stale = false;
+  if (attempt) {
     const int rc = forward(P, x, p, q, E, B, s, true);
     if (rc != kStaleLists) return rc;
+    P->reuse_stale = true;
   }
   if (rebuilt) *rebuilt = 1;
   return forward(P, x, p, q, E, B, s, false);

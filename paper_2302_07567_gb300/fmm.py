@@ -193,10 +193,17 @@ class Plan:
                     rc = lib().fmm_field(self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(E), _ptr(B), _stream(dev))
             if rc != FMM_EOVERFLOW:
                 break
+            # the traversal counts every pair it finds, also past a full list:
+            # a list that overflowed grows to 1.25 times its count (at least
+            # doubling); with both lists within their capacities it was the
+            # traversal frontier that overflowed, which grows fourfold
             st = self.stats()
-            self.set_capacity(max(4 * st["cap_p2p"], int(1.25 * st["p2p_pairs"]) + 1024),
-                              max(4 * st["cap_m2l"], int(1.25 * st["m2l_pairs"]) + 1024),
-                              4 * st["cap_frontier"])
+            p2p_over = st["p2p_pairs"] > st["cap_p2p"]
+            m2l_over = st["m2l_pairs"] > st["cap_m2l"]
+            grow = lambda cap, cnt: max(2 * cap, int(1.25 * cnt) + 1024)  # noqa: E731
+            self.set_capacity(grow(st["cap_p2p"], st["p2p_pairs"]) if p2p_over else 0,
+                              grow(st["cap_m2l"], st["m2l_pairs"]) if m2l_over else 0,
+                              0 if (p2p_over or m2l_over) else 4 * st["cap_frontier"])
         if rc != FMM_OK:
             raise FMMError(rc, "fmm_field_reuse" if reuse else "fmm_field")
         self.generation += 1

@@ -104,6 +104,13 @@ def test_reuse_rebuilds_when_lists_go_stale(prec):
     assert plan.last_rebuilt
     E2, B2 = fmm.Plan(4000, 4, 64, 0.5, precision=prec).field(X2, Pm, Qd)
     assert torch.equal(E1, E2) and torch.equal(B1, B2)
+    # right after a stale attempt the next call builds without trying; the
+    # call after that tries again and, the particles unchanged, keeps the lists
+    plan.field(X2, Pm, Qd, reuse=True)
+    assert plan.last_rebuilt
+    E3, B3 = plan.field(X2, Pm, Qd, reuse=True)
+    assert not plan.last_rebuilt
+    assert torch.equal(E3, E2) and torch.equal(B3, B2)
 
 
 def test_track_helper_counts_rebuilds():
