@@ -931,7 +931,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
 // local) is added as in k_adj_target.  Output per particle (leaf order):
 // g1 = (dL/dx' (3), dL/da'), g2 = (dL/db~' (3), 0); the source-side far field
 // and the chain rule follow in k_adj_source.
-__global__ void __launch_bounds__(128, 5) k_adj_near(
+template <int KPT>
+__global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, const uint64_t* __restrict__ skeys,
     const int32_t* __restrict__ soff, int shift, const int64_t* __restrict__ nstart,
     const int64_t* __restrict__ ncount, int kappa, const NodeGeo* __restrict__ geo, const float4* __restrict__ px,
@@ -950,14 +951,15 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
   constexpr int NC = 7;    // dL/dx' (3), dL/da', dL/db~' (3)
   extern __shared__ unsigned char smem_raw[];
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
-  float* sl = reinterpret_cast<float*>(smem_raw + stage_bytes<float>(kRow, 1, 2 * NC, groups, NT));  // [6][m]
+  float* sl = reinterpret_cast<float*>(smem_raw + stage_bytes<float>(kRow, KPT, 2 * NC, groups, NT));  // [6][m]
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int np1 = ch.np1;
+  const int64_t per_chunk = (int64_t)KPT * NT;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
   __syncthreads();  // the previous item's readers of the stage and sl are done
   const int64_t L = ((int64_t)1 << kappa) + item / chunks;
-  const int64_t c0 = (int64_t)(item % chunks) * NT;
-  const int64_t st = nstart[L], cnt = min64(ncount[L], c0 + NT);
+  const int64_t c0 = (int64_t)(item % chunks) * per_chunk;
+  const int64_t st = nstart[L], cnt = min64(ncount[L], c0 + per_chunk);
   if (c0 >= cnt) continue;  // the leaf is smaller than this chunk
   const NodeGeo gt = geo[L];
   float invh[3];
@@ -970,17 +972,26 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
     const float* Lt = Lcum + (size_t)L * 6 * m;
     for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
   }
-  const int64_t j0 = c0 + lt;
-  const bool valid = j0 < cnt;
-  const int64_t jj = st + (valid ? j0 : 0);
-  const float4 u0 = px[jj], b0 = pb[jj], l0 = pl[jj], e0 = wle[jj], w0 = wlb[jj];
-  float acc[NC], cmp[NC];
+  bool valid[KPT];
+  int64_t jj[KPT];
+  float4 u0[KPT], l0[KPT];
+  float2 WE0[KPT], WE1[KPT], WE2[KPT], WB0[KPT], WB1[KPT], WB2[KPT], NA[KPT], B0[KPT], B1[KPT], B2[KPT];
+  float acc[KPT][NC], cmp[KPT][NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
-  const float2 WE0 = make_float2(e0.x, e0.x), WE1 = make_float2(e0.y, e0.y), WE2 = make_float2(e0.z, e0.z);
-  const float2 WB0 = make_float2(w0.x, w0.x), WB1 = make_float2(w0.y, w0.y), WB2 = make_float2(w0.z, w0.z);
-  const float2 NA = make_float2(-u0.w, -u0.w);
-  const float2 B0 = make_float2(b0.x, b0.x), B1 = make_float2(b0.y, b0.y), B2 = make_float2(b0.z, b0.z);
+  for (int k = 0; k < KPT; ++k) {
+    const int64_t j0 = c0 + lt + (int64_t)k * NT;
+    valid[k] = j0 < cnt;
+    jj[k] = st + (valid[k] ? j0 : 0);
+    u0[k] = px[jj[k]];
+    l0[k] = pl[jj[k]];
+    const float4 b0 = pb[jj[k]], e0 = wle[jj[k]], w0 = wlb[jj[k]];
+    WE0[k] = make_float2(e0.x, e0.x); WE1[k] = make_float2(e0.y, e0.y); WE2[k] = make_float2(e0.z, e0.z);
+    WB0[k] = make_float2(w0.x, w0.x); WB1[k] = make_float2(w0.y, w0.y); WB2[k] = make_float2(w0.z, w0.z);
+    NA[k] = make_float2(-u0[k].w, -u0[k].w);
+    B0[k] = make_float2(b0.x, b0.x); B1[k] = make_float2(b0.y, b0.y); B2[k] = make_float2(b0.z, b0.z);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[k][c] = cmp[k][c] = 0.f;
+  }
   const float2 m3 = make_float2(-3.f, -3.f);
   int it1 = off[L], it2 = soff[L];
   const int e1 = off[L + 1], e2 = soff[L + 1];
@@ -993,10 +1004,12 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
     const float4 dh = tgt ? pdc[2 * it1] : sdc[2 * it2], dl = tgt ? pdc[2 * it1 + 1] : sdc[2 * it2 + 1];
     if (tgt) ++it1;
     if (src) ++it2;
-    float X[3], XL[3];  // x_i in P's frame, hi + lo
-    {
-      const float ri[3] = {u0.x, u0.y, u0.z}, rl[3] = {l0.x, l0.y, l0.z};
+    float2 X0[KPT], X1[KPT], X2[KPT], L0[KPT], L1[KPT], L2[KPT];  // x_i in P's frame, hi + lo
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const float ri[3] = {u0[k].x, u0[k].y, u0[k].z}, rl[3] = {l0[k].x, l0[k].y, l0[k].z};
       const float dch[3] = {dh.x, dh.y, dh.z}, dcl[3] = {dl.x, dl.y, dl.z};
+      float X[3], XL[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         float hs, he;
@@ -1005,13 +1018,15 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
         X[d] = hs + lo;
         XL[d] = lo - (X[d] - hs);
       }
+      X0[k] = make_float2(X[0], X[0]); X1[k] = make_float2(X[1], X[1]); X2[k] = make_float2(X[2], X[2]);
+      L0[k] = make_float2(XL[0], XL[0]); L1[k] = make_float2(XL[1], XL[1]); L2[k] = make_float2(XL[2], XL[2]);
     }
-    const float2 X0 = make_float2(X[0], X[0]), X1 = make_float2(X[1], X[1]), X2 = make_float2(X[2], X[2]);
-    const float2 L0 = make_float2(XL[0], XL[0]), L1 = make_float2(XL[1], XL[1]), L2 = make_float2(XL[2], XL[2]);
     const int64_t sst = nstart[P], scnt = ncount[P];
-    float2 pp[NC];
+    float2 pp[KPT][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) pp[c] = make_float2(0.f, 0.f);
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pp[k][c] = make_float2(0.f, 0.f);
     for (int64_t base = 0; base < scnt; base += blockDim.x) {
       __syncthreads();
       const int64_t j = base + threadIdx.x;
@@ -1041,89 +1056,93 @@ __global__ void __launch_bounds__(128, 5) k_adj_near(
       for (int qq = grp * share2; qq < q1; ++qq) {
         const float4* s4 = reinterpret_cast<const float4*>(smem_raw) + (kPairStride / 4) * qq;
         const float4 S0 = s4[0], S1 = s4[1], S2 = s4[2], S3 = s4[3], S4 = s4[4], S5 = s4[5];
-        const float2 rx = __fadd2_rn(__fadd2_rn(X0, make_float2(S0.x, S0.y)), __fadd2_rn(L0, make_float2(S1.z, S1.w)));
-        const float2 ry = __fadd2_rn(__fadd2_rn(X1, make_float2(S0.z, S0.w)), __fadd2_rn(L1, make_float2(S2.x, S2.y)));
-        const float2 rz = __fadd2_rn(__fadd2_rn(X2, make_float2(S1.x, S1.y)), __fadd2_rn(L2, make_float2(S2.z, S2.w)));
-        const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
-        float2 inv;
-        inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
-        inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
-        const float2 inv2 = __fmul2_rn(inv, inv);
-        const float2 r3 = __fmul2_rn(inv2, inv);
-        // K = R / |R|^3 serves both roles
-        const float2 kx = __fmul2_rn(r3, rx), ky = __fmul2_rn(r3, ry), kz = __fmul2_rn(r3, rz);
+        const float4 S6 = s4[6], S7 = s4[7], S8 = s4[8], S9 = s4[9], S10 = s4[10];
         const float2 aj = make_float2(S3.x, S3.y);
         const float2 bx = make_float2(S3.z, S3.w), by = make_float2(S4.x, S4.y), bz = make_float2(S4.z, S4.w);
         const float2 nbx = make_float2(S5.x, S5.y), nby = make_float2(S5.z, S5.w);
-        const float4 S6 = s4[6], S7 = s4[7], S8 = s4[8], S9 = s4[9], S10 = s4[10];
         const float2 nbz = make_float2(S6.x, S6.y);
         const float2 ex = make_float2(S6.z, S6.w), ey = make_float2(S7.x, S7.y), ez = make_float2(S7.z, S7.w);
         const float2 wx = make_float2(S8.x, S8.y), wy = make_float2(S8.z, S8.w), wz = make_float2(S9.x, S9.y);
         const float2 nwx = make_float2(S9.z, S9.w), nwy = make_float2(S10.x, S10.y), nwz = make_float2(S10.z, S10.w);
-        // v = u_ij - u_ji = a_j w^E_i + w^B_i x b_j - a_i w^E_j + b_i x w^B_j
-        const float2 vx = __ffma2_rn(aj, WE0, __ffma2_rn(WB1, bz, __ffma2_rn(WB2, nby,
-                          __ffma2_rn(NA, ex, __ffma2_rn(B1, wz, __fmul2_rn(B2, nwy))))));
-        const float2 vy = __ffma2_rn(aj, WE1, __ffma2_rn(WB2, bx, __ffma2_rn(WB0, nbz,
-                          __ffma2_rn(NA, ey, __ffma2_rn(B2, wx, __fmul2_rn(B0, nwz))))));
-        const float2 vz = __ffma2_rn(aj, WE2, __ffma2_rn(WB0, by, __ffma2_rn(WB1, nbx,
-                          __ffma2_rn(NA, ez, __ffma2_rn(B0, wy, __fmul2_rn(B1, nwx))))));
-        // J v = r3 v - 3 r5 (R . v) R = r3 v + c K with c = -3 r^-2 (R . v)
-        const float2 rv = __ffma2_rn(rz, vz, __ffma2_rn(ry, vy, __fmul2_rn(rx, vx)));
-        const float2 c = __fmul2_rn(__fmul2_rn(inv2, m3), rv);
-        pp[0] = __ffma2_rn(c, kx, __ffma2_rn(r3, vx, pp[0]));
-        pp[1] = __ffma2_rn(c, ky, __ffma2_rn(r3, vy, pp[1]));
-        pp[2] = __ffma2_rn(c, kz, __ffma2_rn(r3, vz, pp[2]));
-        // source role, summed with the sign flipped at the end: K . w^E_j, K x w^B_j
-        pp[3] = __ffma2_rn(kz, ez, __ffma2_rn(ky, ey, __ffma2_rn(kx, ex, pp[3])));
-        pp[4] = __ffma2_rn(ky, wz, __ffma2_rn(kz, nwy, pp[4]));
-        pp[5] = __ffma2_rn(kz, wx, __ffma2_rn(kx, nwz, pp[5]));
-        pp[6] = __ffma2_rn(kx, wy, __ffma2_rn(ky, nwx, pp[6]));
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          const float2 rx = __fadd2_rn(__fadd2_rn(X0[k], make_float2(S0.x, S0.y)), __fadd2_rn(L0[k], make_float2(S1.z, S1.w)));
+          const float2 ry = __fadd2_rn(__fadd2_rn(X1[k], make_float2(S0.z, S0.w)), __fadd2_rn(L1[k], make_float2(S2.x, S2.y)));
+          const float2 rz = __fadd2_rn(__fadd2_rn(X2[k], make_float2(S1.x, S1.y)), __fadd2_rn(L2[k], make_float2(S2.z, S2.w)));
+          const float2 d = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+          float2 inv;
+          inv.x = d.x > tiny_sep2<float>() ? rsqrt_t<float>(d.x) : 0.f;
+          inv.y = d.y > tiny_sep2<float>() ? rsqrt_t<float>(d.y) : 0.f;
+          const float2 inv2 = __fmul2_rn(inv, inv);
+          const float2 r3 = __fmul2_rn(inv2, inv);
+          // K = R / |R|^3 serves both roles
+          const float2 kx = __fmul2_rn(r3, rx), ky = __fmul2_rn(r3, ry), kz = __fmul2_rn(r3, rz);
+          // v = u_ij - u_ji = a_j w^E_i + w^B_i x b_j - a_i w^E_j + b_i x w^B_j
+          const float2 vx = __ffma2_rn(aj, WE0[k], __ffma2_rn(WB1[k], bz, __ffma2_rn(WB2[k], nby,
+                            __ffma2_rn(NA[k], ex, __ffma2_rn(B1[k], wz, __fmul2_rn(B2[k], nwy))))));
+          const float2 vy = __ffma2_rn(aj, WE1[k], __ffma2_rn(WB2[k], bx, __ffma2_rn(WB0[k], nbz,
+                            __ffma2_rn(NA[k], ey, __ffma2_rn(B2[k], wx, __fmul2_rn(B0[k], nwz))))));
+          const float2 vz = __ffma2_rn(aj, WE2[k], __ffma2_rn(WB0[k], by, __ffma2_rn(WB1[k], nbx,
+                            __ffma2_rn(NA[k], ez, __ffma2_rn(B0[k], wy, __fmul2_rn(B1[k], nwx))))));
+          // J v = r3 v - 3 r5 (R . v) R = r3 v + c K with c = -3 r^-2 (R . v)
+          const float2 rv = __ffma2_rn(rz, vz, __ffma2_rn(ry, vy, __fmul2_rn(rx, vx)));
+          const float2 c = __fmul2_rn(__fmul2_rn(inv2, m3), rv);
+          pp[k][0] = __ffma2_rn(c, kx, __ffma2_rn(r3, vx, pp[k][0]));
+          pp[k][1] = __ffma2_rn(c, ky, __ffma2_rn(r3, vy, pp[k][1]));
+          pp[k][2] = __ffma2_rn(c, kz, __ffma2_rn(r3, vz, pp[k][2]));
+          // source role, summed with the sign flipped at the end: K . w^E_j, K x w^B_j
+          pp[k][3] = __ffma2_rn(kz, ez, __ffma2_rn(ky, ey, __ffma2_rn(kx, ex, pp[k][3])));
+          pp[k][4] = __ffma2_rn(ky, wz, __ffma2_rn(kz, nwy, pp[k][4]));
+          pp[k][5] = __ffma2_rn(kz, wx, __ffma2_rn(kx, nwz, pp[k][5]));
+          pp[k][6] = __ffma2_rn(kx, wy, __ffma2_rn(ky, nwx, pp[k][6]));
+        }
       }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) kahan_add(acc[c], cmp[c], pp[c].x + pp[c].y);
+    for (int k = 0; k < KPT; ++k) {
 #pragma unroll
-    for (int c = 3; c < NC; ++c) kahan_add(acc[c], cmp[c], -(pp[c].x + pp[c].y));
+      for (int c = 0; c < 3; ++c) kahan_add(acc[k][c], cmp[k][c], pp[k][c].x + pp[k][c].y);
+#pragma unroll
+      for (int c = 3; c < NC; ++c) kahan_add(acc[k][c], cmp[k][c], -(pp[k][c].x + pp[k][c].y));
+    }
   }
   __syncthreads();
   const int a3share = (np1 + groups - 1) / groups;
   const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
-  if (valid && kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
-    float lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
-    basis_deriv<float>((u0.x + l0.x) * invh[0], deg[0], ch, cd, lx, dx);
-    basis_deriv<float>((u0.y + l0.y) * invh[1], deg[1], ch, cd, ly, dy);
-    basis_deriv<float>((u0.z + l0.z) * invh[2], deg[2], ch, cd, lz, dz);
-    float G[3] = {0.f, 0.f, 0.f};
-    int mu = a3b * np1 * np1;
-    for (int a3 = a3b; a3 < a3e; ++a3) {
-      for (int a2 = 0; a2 < np1; ++a2) {
-        float s0 = 0.f, sx = 0.f;
-        for (int a1 = 0; a1 < np1; ++a1, ++mu) {
-          const float phi = e0.x * sl[mu] + e0.y * sl[m + mu] + e0.z * sl[2 * m + mu] +
-                            w0.x * sl[3 * m + mu] + w0.y * sl[4 * m + mu] + w0.z * sl[5 * m + mu];
-          s0 += lx[a1] * phi;
-          sx += dx[a1] * phi;
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    if (valid[k] && kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
+      const float4 e0 = wle[jj[k]], w0 = wlb[jj[k]];
+      float lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
+      basis_deriv<float>((u0[k].x + l0[k].x) * invh[0], deg[0], ch, cd, lx, dx);
+      basis_deriv<float>((u0[k].y + l0[k].y) * invh[1], deg[1], ch, cd, ly, dy);
+      basis_deriv<float>((u0[k].z + l0[k].z) * invh[2], deg[2], ch, cd, lz, dz);
+      float G[3] = {0.f, 0.f, 0.f};
+      int mu = a3b * np1 * np1;
+      for (int a3 = a3b; a3 < a3e; ++a3) {
+        for (int a2 = 0; a2 < np1; ++a2) {
+          float s0 = 0.f, sx = 0.f;
+          for (int a1 = 0; a1 < np1; ++a1, ++mu) {
+            const float phi = e0.x * sl[mu] + e0.y * sl[m + mu] + e0.z * sl[2 * m + mu] +
+                              w0.x * sl[3 * m + mu] + w0.y * sl[4 * m + mu] + w0.z * sl[5 * m + mu];
+            s0 += lx[a1] * phi;
+            sx += dx[a1] * phi;
+          }
+          G[0] += ly[a2] * lz[a3] * sx;
+          G[1] += dy[a2] * lz[a3] * s0;
+          G[2] += ly[a2] * dz[a3] * s0;
         }
-        G[0] += ly[a2] * lz[a3] * sx;
-        G[1] += dy[a2] * lz[a3] * s0;
-        G[2] += ly[a2] * dz[a3] * s0;
       }
-    }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) kahan_add(acc[d], cmp[d], G[d] * invh[d]);
+      for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], G[d] * invh[d]);
+    }
   }
-  {
-    float a2[1][NC], c2[1][NC];
+  combine_groups<float, KPT, NC>(acc, cmp, reinterpret_cast<float*>(smem_raw), groups, grp, NT, lt);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      a2[0][c] = acc[c];
-      c2[0][c] = cmp[c];
-    }
-    combine_groups<float, 1, NC>(a2, c2, reinterpret_cast<float*>(smem_raw), groups, grp, NT, lt);
-    if (grp == 0 && valid) {
-      const int64_t pos = st + j0;
-      g1[pos] = make_float4(a2[0][0], a2[0][1], a2[0][2], a2[0][3]);
-      g2[pos] = make_float4(a2[0][4], a2[0][5], a2[0][6], 0.f);
+  for (int k = 0; k < KPT; ++k) {
+    if (grp == 0 && valid[k]) {
+      g1[jj[k]] = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+      g2[jj[k]] = make_float4(acc[k][4], acc[k][5], acc[k][6], 0.f);
     }
   }
   }  // items
@@ -1762,23 +1781,24 @@ int adj_source(fmm_plan_s* P, const double* p, const double* q, double* dx, doub
 // FP32 near field of both roles (k_adj_near), on the caller's stream beside
 // the source side's far field; like the target side it keeps to part of the
 // SMs' block slots.
-int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
+template <int KPT>
+int launch_adj_near_k(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
   int NT, groups, chunks;
-  particle_shape(P->leaf, 1, &NT, &groups, &chunks);  // as the forward P2P
+  particle_shape(P->leaf, KPT, &NT, &groups, &chunks);  // as the forward P2P
   const int nt = groups * NT;
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
-  const size_t smem = stage_bytes<float>(7, 1, 14, groups, NT) + sizeof(float) * 6 * P->m;  // kRow 7
-  if (int rc = set_smem(k_adj_near, smem)) return rc;
+  const size_t smem = stage_bytes<float>(7, KPT, 14, groups, NT) + sizeof(float) * 6 * P->m;  // kRow 7
+  if (int rc = set_smem(k_adj_near<KPT>, smem)) return rc;
   if (P->kappa > 0 && P->adj_overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;
     if (int rc = device_sms(&sms)) return rc;
     grid = (unsigned)std::min<int64_t>(items, (int64_t)3 * sms);
-  } else if (int rc = resident_blocks(k_adj_near, nt, smem, items, &grid)) {  // alone: every resident slot
+  } else if (int rc = resident_blocks(k_adj_near<KPT>, nt, smem, items, &grid)) {  // alone: every resident slot
     return rc;
   }
-  k_adj_near<<<grid, nt, smem, s>>>(
+  k_adj_near<KPT><<<grid, nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), ws_ptr<uint64_t>(P, L.p2p_src),
       ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount),
       P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb),
@@ -1787,6 +1807,13 @@ int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
       ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
+}
+
+// Two targets per thread on leaves of 256 or more, as the forward P2P: each
+// staged partner pair feeds two independent chains (2^24 core-halo beam,
+// N0 = 256: alone 1124 -> 1079 ms; at N0 = 128 the 2^16 cylinder is slower).
+int launch_adj_near(fmm_plan_s* P, cudaStream_t s) {
+  return P->leaf >= 256 ? launch_adj_near_k<2>(P, s) : launch_adj_near_k<1>(P, s);
 }
 
 // dL/dgbar into scal[9], scal[10] (after the target side and M2L^T).
