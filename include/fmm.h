@@ -69,13 +69,17 @@ typedef enum fmm_flags {
                             (with FMM_GBAR_TERM, whose M2L^T reads M, Lambda keeps a
                             buffer of its own), so fmm_plan_workspace_bytes shrinks
                             by about 7.5 (n+1)^3 x (number of clusters) bytes
-                            (FP32).  The adjoint's near field, which reads the leaf
-                            locals, runs before the far-field chain that overwrites
-                            them, on the caller's stream (no second stream).  A
-                            further adjoint call without a new fmm_field recomputes
-                            the upward pass, M2L and L2L first; fmm_plan_export of
-                            multipoles or locals after an adjoint returns
-                            FMM_ESTATE                                               */
+                            (FP32).  The target-side far field, which reads the
+                            leaf locals, runs before the far-field chain that
+                            overwrites them: in FP32 without FMM_GBAR_TERM as a
+                            kernel of its own, after which the near field and the
+                            chain run side by side as without the flag; in FP64 and
+                            with FMM_GBAR_TERM inside the near-field kernel, which
+                            then runs first, on the caller's stream (no second
+                            stream).  A further adjoint call without a new fmm_field
+                            recomputes the upward pass, M2L and L2L first;
+                            fmm_plan_export of multipoles or locals after an
+                            adjoint returns FMM_ESTATE                               */
   FMM_BOUNDS_CHECK = 2u, /* after the traversal (and the adjoint's source-major lists)
                             check on the device: node tables, the leaf order is a
                             permutation, list pairs in range, sorted and matching

@@ -26,8 +26,9 @@
 //
 // Buffers: W and Lambda have their own, so the forward's multipoles and
 // cumulative locals survive the adjoint (a second adjoint call reuses them),
-// and the near field (FP32: both roles of every pair in k_adj_near; FP64 and
-// the gbar term: the target side in k_adj_target) runs on the caller's
+// and the near field (FP32: both roles of every pair in k_adj_near, after
+// k_adj_far has taken the target-side far field from the leaf locals; FP64
+// and the gbar term: the target side in k_adj_target) runs on the caller's
 // stream while the source side's far field (L2P^T, L2L^T, M2L^T, M2M^T) runs
 // on the plan's side stream.  After both, k_adj_final (FP32) or k_adj_source
 // adds the source-side far field and applies the chain rule.
@@ -437,19 +438,21 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_adj_m2l_fast(const uint64_
   }  // work items
 }
 
-// FP32 M2L^T with paired arithmetic and regrouped x sums, the counterpart of
-// k_m2l_pair: a thread owns two source points of the cluster, nu_a = P and
-// nu_b = P + H, and evaluates both against each target point mu with paired
-// FP32 instructions.  In the mu1 loop R_x = t_x[mu1] - X is the only varying
-// component (R = xi_S,mu - xi_s,nu), and the sums that carry R_x are split:
-// sum w r3 R_x = sum (w t_x) r3 - X sum w r3, with the products w t_x of the
-// node weights and the x offset of their point staged once per target
-// cluster.  A point pair then costs 12 FMA-pipe operations (|R|^2 1, r^-3 2,
-// nine sums) instead of 15.  Staged per target point, duplicated for the two
-// lanes: (WEx, ., WEy, .), (WEz, ., WBx, .), (WBy, ., WBz, .),
-// (WEx t_x, ., WBy t_x, .), (WBz t_x, ., 0, 0).
+// FP32 M2L^T with paired arithmetic, the counterpart of k_m2l_pair: a thread
+// owns two source points of the cluster, nu_a = P and nu_b = P + H, and
+// evaluates both against each target point mu with paired FP32 instructions.
+// In the mu1 loop R_x = t_x[mu1] - X is the only varying component
+// (R = xi_S,mu - xi_s,nu, its x part held per mu1 in registers), so the sums
+// are taken in r3 and r3 R_x and multiplied by R_y, R_z after the loop: of
+// Lambda's sums only W^E_x, W^B_y and W^B_z meet R_x, and a point pair costs
+// 12 FMA-pipe operations (|R|^2 1, r^-3 2, r3 R_x 1, eight sums) on three
+// staged float4 per target point, duplicated for the two lanes:
+// (WEx, ., WEy, .), (WEz, ., WBx, .), (WBy, ., WBz, .).  Splitting the R_x
+// sums as sum w r3 R_x = sum (w t_x) r3 - X sum w r3 takes as many
+// operations on five staged float4 (2^24 core-halo beam, n = 8: 960 ms
+// against 853 ms for this form at 3 blocks per SM, 823 ms at 4).
 template <int NP1, int NT>
-__global__ void __launch_bounds__(NT, 3) k_adj_m2l_pair(const uint64_t* __restrict__ keys,
+__global__ void __launch_bounds__(NT, 4) k_adj_m2l_pair(const uint64_t* __restrict__ keys,
                                                        const int32_t* __restrict__ off, int shift,
                                                        const int32_t* __restrict__ order, int64_t nitems,
                                                        unsigned int* __restrict__ work,
@@ -460,8 +463,8 @@ __global__ void __launch_bounds__(NT, 3) k_adj_m2l_pair(const uint64_t* __restri
   constexpr int H = (m + 1) / 2;
   constexpr int SPLIT = (H + NT - 1) / NT;
   extern __shared__ float4 dsm[];
-  float4* sw = dsm;                                        // [m][5] staged target points
-  float2* sacc = reinterpret_cast<float2*>(dsm + 5 * m);   // [8][NT] Kahan sums, compensations
+  float4* sw = dsm;                                        // [m][3] staged target points
+  float2* sacc = reinterpret_cast<float2*>(dsm + 3 * m);   // [8][NT] Kahan sums, compensations
   __shared__ float sxyz[3][NP1];                           // target point offsets per axis
   __shared__ int64_t s_item;
   const int tid = threadIdx.x;
@@ -494,13 +497,9 @@ __global__ void __launch_bounds__(NT, 3) k_adj_m2l_pair(const uint64_t* __restri
       for (int o = tid; o < m; o += NT) {
         const float ex = Ws[o], ey = Ws[m + o], ez = Ws[2 * m + o];
         const float bx = Ws[3 * m + o], by = Ws[4 * m + o], bz = Ws[5 * m + o];
-        const float tx = (float)(gS.h[0] * ch.t[o % NP1]);
-        const float vx = ex * tx, vy = by * tx, vz = bz * tx;
-        sw[5 * o] = make_float4(ex, ex, ey, ey);
-        sw[5 * o + 1] = make_float4(ez, ez, bx, bx);
-        sw[5 * o + 2] = make_float4(by, by, bz, bz);
-        sw[5 * o + 3] = make_float4(vx, vx, vy, vy);
-        sw[5 * o + 4] = make_float4(vz, vz, 0.f, 0.f);
+        sw[3 * o] = make_float4(ex, ex, ey, ey);
+        sw[3 * o + 1] = make_float4(ez, ez, bx, bx);
+        sw[3 * o + 2] = make_float4(by, by, bz, bz);
       }
       if (tid < 3 * NP1) {
         const int d = tid / NP1, k = tid - d * NP1;
@@ -522,45 +521,43 @@ __global__ void __launch_bounds__(NT, 3) k_adj_m2l_pair(const uint64_t* __restri
         const float2 rz = __fadd2_rn(make_float2(sxyz[2][m3], sxyz[2][m3]), __fmul2_rn(Z, neg1));
         const float2 nrz = __fmul2_rn(rz, neg1);
         const float2 dz = __fmul2_rn(rz, rz);
-        const float4* row = sw + 5 * m3 * NP1 * NP1;
+        const float4* row = sw + 3 * m3 * NP1 * NP1;
 #pragma unroll
         for (int m2 = 0; m2 < NP1; ++m2) {
           const float2 ry = __fadd2_rn(make_float2(sxyz[1][m2], sxyz[1][m2]), __fmul2_rn(Y, neg1));
           const float2 dyz = __ffma2_rn(ry, ry, dz);
           const float2 z0 = make_float2(0.f, 0.f);
-          float2 T1 = z0, T2 = z0, T3 = z0, T4 = z0, T5 = z0, T6 = z0, V1 = z0, V5 = z0, V6 = z0;
+          float2 T2 = z0, T3 = z0, T4 = z0, T5 = z0, T6 = z0, U1 = z0, U5 = z0, U6 = z0;
 #pragma unroll
           for (int m1 = 0; m1 < NP1; ++m1) {
-            const float4* q = row + 5 * (m2 * NP1 + m1);
-            const float4 A = q[0], Bq = q[1], C = q[2], D = q[3], F = q[4];
+            const float4* q = row + 3 * (m2 * NP1 + m1);
+            const float4 A = q[0], Bq = q[1], C = q[2];
             float2 d = __ffma2_rn(Rx[m1], Rx[m1], dyz);
             d.x = fmaxf(d.x, tiny_sep2<float>());
             d.y = fmaxf(d.y, tiny_sep2<float>());
             const float2 inv = make_float2(rsqrt_normal(d.x), rsqrt_normal(d.y));
             const float2 r3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
-            T1 = __ffma2_rn(make_float2(A.x, A.y), r3, T1);
+            const float2 rr = __fmul2_rn(r3, Rx[m1]);
+            U1 = __ffma2_rn(make_float2(A.x, A.y), rr, U1);
             T2 = __ffma2_rn(make_float2(A.z, A.w), r3, T2);
             T3 = __ffma2_rn(make_float2(Bq.x, Bq.y), r3, T3);
             T4 = __ffma2_rn(make_float2(Bq.z, Bq.w), r3, T4);
             T5 = __ffma2_rn(make_float2(C.x, C.y), r3, T5);
             T6 = __ffma2_rn(make_float2(C.z, C.w), r3, T6);
-            V1 = __ffma2_rn(make_float2(D.x, D.y), r3, V1);
-            V5 = __ffma2_rn(make_float2(D.z, D.w), r3, V5);
-            V6 = __ffma2_rn(make_float2(F.x, F.y), r3, V6);
+            U5 = __ffma2_rn(make_float2(C.x, C.y), rr, U5);
+            U6 = __ffma2_rn(make_float2(C.z, C.w), rr, U6);
           }
-          // sum w r3 R_x = sum (w t_x) r3 - X sum w r3
-          const float2 T1R = __ffma2_rn(nX, T1, V1), T5R = __ffma2_rn(nX, T5, V5), T6R = __ffma2_rn(nX, T6, V6);
-          // Lambda^a += sum r3 W^E_x R_x + R_y sum r3 W^E_y + R_z sum r3 W^E_z
-          // Lambda^b += (R_y sum r3 W^B_z - R_z sum r3 W^B_y, R_z sum r3 W^B_x - sum r3 W^B_z R_x,
-          //              sum r3 W^B_y R_x - R_y sum r3 W^B_x)
-          part[0] = __fadd2_rn(part[0], T1R);
+          // Lambda^a += sum r3 R_x W^E_x + R_y sum r3 W^E_y + R_z sum r3 W^E_z
+          // Lambda^b += (R_y sum r3 W^B_z - R_z sum r3 W^B_y, R_z sum r3 W^B_x - sum r3 R_x W^B_z,
+          //              sum r3 R_x W^B_y - R_y sum r3 W^B_x)
+          part[0] = __fadd2_rn(part[0], U1);
           part[0] = __ffma2_rn(ry, T2, part[0]);
           part[0] = __ffma2_rn(rz, T3, part[0]);
           part[1] = __ffma2_rn(ry, T6, part[1]);
           part[1] = __ffma2_rn(nrz, T5, part[1]);
           part[2] = __ffma2_rn(rz, T4, part[2]);
-          part[2] = __ffma2_rn(T6R, neg1, part[2]);
-          part[3] = __fadd2_rn(part[3], T5R);
+          part[2] = __ffma2_rn(U6, neg1, part[2]);
+          part[3] = __fadd2_rn(part[3], U5);
           part[3] = __ffma2_rn(__fmul2_rn(ry, neg1), T4, part[3]);
         }
       }
@@ -588,7 +585,7 @@ template <int NP1, int NT>
 int launch_adj_m2l_pair(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
   constexpr int m = NP1 * NP1 * NP1, H = (m + 1) / 2, SPLIT = (H + NT - 1) / NT;
-  const size_t smem = sizeof(float4) * 5 * m + sizeof(float2) * 8 * NT;
+  const size_t smem = sizeof(float4) * 3 * m + sizeof(float2) * 8 * NT;
   if (int rc = smem_limit(k_adj_m2l_pair<NP1, NT>, (int)smem)) return rc;
   unsigned grid = 0;
   if (int rc = resident_blocks(k_adj_m2l_pair<NP1, NT>, NT, smem, P->C * SPLIT, &grid)) return rc;
@@ -927,18 +924,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_adj_target(
 // by staging its masses (no target role) or its weights (no source role) as
 // zero.  Partners are staged in pairs as in k_adj_target and evaluated with
 // paired FP32 arithmetic; per partner leaf the two lanes are added and
-// Kahan-summed.  The target-side far field (grad of the forward's cumulative
-// local) is added as in k_adj_target.  Output per particle (leaf order):
-// g1 = (dL/dx' (3), dL/da'), g2 = (dL/db~' (3), 0); the source-side far field
-// and the chain rule follow in k_adj_source.
+// Kahan-summed.  With a far field (kappa > 0) the target-side far field that
+// k_adj_far left in g1 is added last, so this kernel reads no expansion and
+// may run while the far-field chain overwrites the leaf locals.  Output per
+// particle (leaf order): g1 = (dL/dx' (3), dL/da'), g2 = (dL/db~' (3), 0);
+// the source-side far field and the chain rule follow in k_adj_final.
 template <int KPT>
 __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, const uint64_t* __restrict__ skeys,
     const int32_t* __restrict__ soff, int shift, const int64_t* __restrict__ nstart,
-    const int64_t* __restrict__ ncount, int kappa, const NodeGeo* __restrict__ geo, const float4* __restrict__ px,
-    const float4* __restrict__ pb, const float4* __restrict__ pl, const float4* __restrict__ pdc,
-    const float4* __restrict__ sdc, const float4* __restrict__ wle, const float4* __restrict__ wlb,
-    const float* __restrict__ Lcum, Cheb ch, ChebD cd, int m, int groups, int chunks, int64_t nitems,
+    const int64_t* __restrict__ ncount, int kappa, const float4* __restrict__ px, const float4* __restrict__ pb,
+    const float4* __restrict__ pl, const float4* __restrict__ pdc, const float4* __restrict__ sdc,
+    const float4* __restrict__ wle, const float4* __restrict__ wlb, int groups, int chunks, int64_t nitems,
     float4* __restrict__ g1, float4* __restrict__ g2) {
   // staged partner pairs: 12 float4 (48 floats) at a 13-float4 stride, 24
   // components as (partner 2q, partner 2q+1): -x_hi (3), -x_lo (3), a, b~ (3),
@@ -947,31 +944,17 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
   // stride the scattered staging stores of a warp fall into 2 ways of the
   // shared-memory banks instead of 8 (48 = 16 mod 32)
   constexpr int kPairStride = 52;
-  constexpr int kRow = 7;  // float4 per staged partner, rounded up (6.5)
   constexpr int NC = 7;    // dL/dx' (3), dL/da', dL/db~' (3)
   extern __shared__ unsigned char smem_raw[];
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
-  float* sl = reinterpret_cast<float*>(smem_raw + stage_bytes<float>(kRow, KPT, 2 * NC, groups, NT));  // [6][m]
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
-  const int np1 = ch.np1;
   const int64_t per_chunk = (int64_t)KPT * NT;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
-  __syncthreads();  // the previous item's readers of the stage and sl are done
+  __syncthreads();  // the previous item's readers of the stage are done
   const int64_t L = ((int64_t)1 << kappa) + item / chunks;
   const int64_t c0 = (int64_t)(item % chunks) * per_chunk;
   const int64_t st = nstart[L], cnt = min64(ncount[L], c0 + per_chunk);
   if (c0 >= cnt) continue;  // the leaf is smaller than this chunk
-  const NodeGeo gt = geo[L];
-  float invh[3];
-  bool deg[3];
-  for (int d = 0; d < 3; ++d) {
-    deg[d] = !(gt.h[d] > 0.0);
-    invh[d] = deg[d] ? 0.f : (float)(1.0 / gt.h[d]);
-  }
-  if (kappa > 0) {
-    const float* Lt = Lcum + (size_t)L * 6 * m;
-    for (int o = threadIdx.x; o < 6 * m; o += blockDim.x) sl[o] = Lt[o];
-  }
   bool valid[KPT];
   int64_t jj[KPT];
   float4 u0[KPT], l0[KPT];
@@ -1107,40 +1090,16 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
     }
   }
   __syncthreads();
-  const int a3share = (np1 + groups - 1) / groups;
-  const int a3b = min(np1, grp * a3share), a3e = min(np1, a3b + a3share);
-#pragma unroll
-  for (int k = 0; k < KPT; ++k) {
-    if (valid[k] && kappa > 0) {  // far field at the target: grad of sum_mu l_mu(x) (w^ . Lc_mu)
-      const float4 e0 = wle[jj[k]], w0 = wlb[jj[k]];
-      float lx[kMaxNp1], ly[kMaxNp1], lz[kMaxNp1], dx[kMaxNp1], dy[kMaxNp1], dz[kMaxNp1];
-      basis_deriv<float>((u0[k].x + l0[k].x) * invh[0], deg[0], ch, cd, lx, dx);
-      basis_deriv<float>((u0[k].y + l0[k].y) * invh[1], deg[1], ch, cd, ly, dy);
-      basis_deriv<float>((u0[k].z + l0[k].z) * invh[2], deg[2], ch, cd, lz, dz);
-      float G[3] = {0.f, 0.f, 0.f};
-      int mu = a3b * np1 * np1;
-      for (int a3 = a3b; a3 < a3e; ++a3) {
-        for (int a2 = 0; a2 < np1; ++a2) {
-          float s0 = 0.f, sx = 0.f;
-          for (int a1 = 0; a1 < np1; ++a1, ++mu) {
-            const float phi = e0.x * sl[mu] + e0.y * sl[m + mu] + e0.z * sl[2 * m + mu] +
-                              w0.x * sl[3 * m + mu] + w0.y * sl[4 * m + mu] + w0.z * sl[5 * m + mu];
-            s0 += lx[a1] * phi;
-            sx += dx[a1] * phi;
-          }
-          G[0] += ly[a2] * lz[a3] * sx;
-          G[1] += dy[a2] * lz[a3] * s0;
-          G[2] += ly[a2] * dz[a3] * s0;
-        }
-      }
-#pragma unroll
-      for (int d = 0; d < 3; ++d) kahan_add(acc[k][d], cmp[k][d], G[d] * invh[d]);
-    }
-  }
   combine_groups<float, KPT, NC>(acc, cmp, reinterpret_cast<float*>(smem_raw), groups, grp, NT, lt);
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     if (grp == 0 && valid[k]) {
+      if (kappa > 0) {  // the target-side far field of k_adj_far
+        const float4 f = g1[jj[k]];
+        kahan_add(acc[k][0], cmp[k][0], f.x);
+        kahan_add(acc[k][1], cmp[k][1], f.y);
+        kahan_add(acc[k][2], cmp[k][2], f.z);
+      }
       g1[jj[k]] = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
       g2[jj[k]] = make_float4(acc[k][4], acc[k][5], acc[k][6], 0.f);
     }
@@ -1605,6 +1564,76 @@ __global__ void __launch_bounds__(kFinalThreads) k_adj_final(
   dx_out[3 * i + 2] = dX[2];
 }
 
+// FP32 target-side far field of the adjoint (FP64 and the gbar term take it
+// in k_adj_target): per particle i of leaf L, in internal units,
+//   dL/dx'_i = sum_mu grad l_mu(x_i) (w^_i . Lc_mu),
+// the L2P of Alg. 14 (Eq. 2.8) differentiated in x_i, with Lc the forward's
+// cumulative local of L.  One thread per particle of a leaf chunk of 128,
+// the six components of Lc staged side by side as in the forward's L2P.
+// Written to g1 as (dL/dx', 0) before the near field, which adds it, so the
+// far-field chain may overwrite the locals (FMM_RECOMPUTE) while the near
+// field runs.
+template <int NP1>  // 0: points per axis from ch at run time
+__global__ void __launch_bounds__(kFinalThreads) k_adj_far(
+    const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
+    const NodeGeo* __restrict__ geo, const float4* __restrict__ px, const float4* __restrict__ pl,
+    const float4* __restrict__ wle, const float4* __restrict__ wlb, const float* __restrict__ Lcum, Cheb ch,
+    ChebD cd, int m, int chunks, float4* __restrict__ g1) {
+  extern __shared__ float4 slc[];  // [m][2]: (L0, L1, L2, L3), (L4, L5, 0, 0)
+  const int64_t t = ((int64_t)1 << kappa) + blockIdx.x / chunks;
+  const int64_t c0 = (int64_t)(blockIdx.x % chunks) * kFinalThreads;
+  const int64_t st = nstart[t], cnt = ncount[t];
+  if (c0 >= cnt) return;  // the leaf is smaller than this chunk
+  const float* Lt = Lcum + (size_t)t * 6 * m;
+  for (int o = threadIdx.x; o < m; o += blockDim.x) {
+    slc[2 * o] = make_float4(Lt[o], Lt[m + o], Lt[2 * m + o], Lt[3 * m + o]);
+    slc[2 * o + 1] = make_float4(Lt[4 * m + o], Lt[5 * m + o], 0.f, 0.f);
+  }
+  __syncthreads();
+  const int64_t j = c0 + threadIdx.x;
+  if (j >= cnt) return;
+  const int64_t pos = st + j;
+  const float4 u = px[pos], l = pl[pos], e = wle[pos], w = wlb[pos];
+  const NodeGeo g = geo[t];
+  float invh[3];
+  bool deg[3];
+  for (int d = 0; d < 3; ++d) {
+    deg[d] = !(g.h[d] > 0.0);
+    invh[d] = deg[d] ? 0.f : (float)(1.0 / g.h[d]);
+  }
+  constexpr int K = NP1 > 0 ? NP1 : kMaxNp1;
+  const int np1 = NP1 > 0 ? NP1 : ch.np1;
+  float lx[K], ly[K], lz[K], dx[K], dy[K], dz[K];
+  if constexpr (NP1 > 0) {
+    basis_deriv_n<K>((u.x + l.x) * invh[0], deg[0], ch, cd, lx, dx);
+    basis_deriv_n<K>((u.y + l.y) * invh[1], deg[1], ch, cd, ly, dy);
+    basis_deriv_n<K>((u.z + l.z) * invh[2], deg[2], ch, cd, lz, dz);
+  } else {
+    basis_deriv<float>((u.x + l.x) * invh[0], deg[0], ch, cd, lx, dx);
+    basis_deriv<float>((u.y + l.y) * invh[1], deg[1], ch, cd, ly, dy);
+    basis_deriv<float>((u.z + l.z) * invh[2], deg[2], ch, cd, lz, dz);
+  }
+  float G[3] = {0.f, 0.f, 0.f};
+  int mu = 0;
+  for (int a3 = 0; a3 < np1; ++a3) {
+#pragma unroll
+    for (int a2 = 0; a2 < (NP1 > 0 ? NP1 : np1); ++a2) {
+      float s0 = 0.f, sx = 0.f;
+#pragma unroll
+      for (int a1 = 0; a1 < (NP1 > 0 ? NP1 : np1); ++a1, ++mu) {
+        const float4 A = slc[2 * mu], Bv = slc[2 * mu + 1];
+        const float phi = e.x * A.x + e.y * A.y + e.z * A.z + w.x * A.w + w.y * Bv.x + w.z * Bv.y;
+        s0 += lx[a1] * phi;
+        sx += dx[a1] * phi;
+      }
+      G[0] += ly[a2] * lz[a3] * sx;
+      G[1] += dy[a2] * lz[a3] * s0;
+      G[2] += ly[a2] * dz[a3] * s0;
+    }
+  }
+  g1[pos] = make_float4(G[0] * invh[0], G[1] * invh[1], G[2] * invh[2], 0.f);
+}
+
 // ---------------------------------------------------------------- launchers
 // Raise the kernel's dynamic shared-memory limit to what this launch needs.
 template <typename K>
@@ -1730,6 +1759,29 @@ int launch_adj_target(fmm_plan_s* P, cudaStream_t s) {
   return FMM_OK;
 }
 
+// FP32 before the near field: the target-side far field (k_adj_far) into g1.
+int launch_adj_far(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  const int64_t most = *std::max_element(P->node_count.begin() + P->nleaves, P->node_count.end());
+  const int chunks = (int)div_up(most, kFinalThreads);
+  const size_t smem = sizeof(float4) * 2 * P->m;
+  auto kern = k_adj_far<0>;
+  switch (P->np1) {
+    case 3: kern = k_adj_far<3>; break;
+    case 5: kern = k_adj_far<5>; break;
+    case 7: kern = k_adj_far<7>; break;
+    case 9: kern = k_adj_far<9>; break;
+    default: break;
+  }
+  if (int rc = smem_limit(kern, (int)smem)) return rc;
+  kern<<<(unsigned)(P->nleaves * chunks), kFinalThreads, smem, s>>>(
+      ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount), P->kappa, ws_ptr<NodeGeo>(P, L.ngeo),
+      ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pl), ws_ptr<float4>(P, L.wle), ws_ptr<float4>(P, L.wlb),
+      ws_ptr<float>(P, L.local), P->cheb, P->chebd, P->m, chunks, ws_ptr<float4>(P, L.adj_part));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
 // FP32 after k_adj_near: source-side far field and chain rule.
 int launch_adj_final(fmm_plan_s* P, const double* p, const double* q, double* dx, double* dp, double* dq,
                      cudaStream_t s) {
@@ -1789,7 +1841,7 @@ int launch_adj_near_k(fmm_plan_s* P, cudaStream_t s) {
   const int nt = groups * NT;
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
-  const size_t smem = stage_bytes<float>(7, KPT, 14, groups, NT) + sizeof(float) * 6 * P->m;  // kRow 7
+  const size_t smem = stage_bytes<float>(7, KPT, 14, groups, NT);  // 7 float4 per thread: half a 52-float pair
   if (int rc = set_smem(k_adj_near<KPT>, smem)) return rc;
   if (P->kappa > 0 && P->adj_overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;
@@ -1801,10 +1853,9 @@ int launch_adj_near_k(fmm_plan_s* P, cudaStream_t s) {
   k_adj_near<KPT><<<grid, nt, smem, s>>>(
       ws_ptr<uint64_t>(P, L.p2p), ws_ptr<int32_t>(P, L.p2p_off), ws_ptr<uint64_t>(P, L.p2p_src),
       ws_ptr<int32_t>(P, L.p2p_soff), P->kappa + 1, ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount),
-      P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb),
-      ws_ptr<float4>(P, L.pl), ws_ptr<float4>(P, L.p2p_dc), ws_ptr<float4>(P, L.p2p_sdc), ws_ptr<float4>(P, L.wle),
-      ws_ptr<float4>(P, L.wlb), ws_ptr<float>(P, L.local), P->cheb, P->chebd, P->m, groups, chunks, items,
-      ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2));
+      P->kappa, ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb), ws_ptr<float4>(P, L.pl),
+      ws_ptr<float4>(P, L.p2p_dc), ws_ptr<float4>(P, L.p2p_sdc), ws_ptr<float4>(P, L.wle), ws_ptr<float4>(P, L.wlb),
+      groups, chunks, items, ws_ptr<float4>(P, L.adj_part), ws_ptr<float4>(P, L.adj_part2));
   FMM_LAUNCH_CHECK();
   return FMM_OK;
 }
@@ -1858,21 +1909,25 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
                                     ws_ptr<int32_t>(P, L.perm), ws_ptr<double>(P, L.scal), ws_ptr<V4>(P, L.wle),
                                     ws_ptr<V4>(P, L.wlb));
   FMM_LAUNCH_CHECK();
-  if ((rc = record(P, 16, s)) != FMM_OK) return rc;
   // Two independent branches from here: the far field of the source side
   // (L2P^T, L2L^T, M2L^T, M2M^T, mostly latency-bound transfers) on the
   // plan's side stream, the near-field particle kernel (ALU-bound) on the
-  // caller's stream.  They share no buffer that either writes: W and Lambda
-  // have their own, the near field reads the forward's leaf locals.
-  // With FMM_SERIAL the chain runs first on the caller's stream; with
-  // FMM_RECOMPUTE W is written over the locals, so the near field runs
-  // first and the chain after it, on the caller's stream.
+  // caller's stream.  They share no buffer that either writes, and only
+  // the target-side far field reads the forward's leaf locals: in FP32
+  // without the gbar term k_adj_far takes it before the branches, so
+  // FMM_RECOMPUTE may write W over the locals beside the near field; where
+  // the near-field kernel itself reads them (k_adj_target) FMM_RECOMPUTE
+  // runs it first and the chain after it, on the caller's stream.  With
+  // FMM_SERIAL the chain runs first on the caller's stream.
   const bool chain = P->kappa > 0;
   const bool gb = (P->flags & FMM_GBAR_TERM) != 0;
   const bool rec = (P->flags & FMM_RECOMPUTE) != 0;
-  const bool ov = chain && P->overlap && !rec;
-  P->adj_overlap = ov;
   const bool fused = std::is_same<T, float>::value && !gb;  // FP32 without the gbar term: both roles in one kernel
+  const bool near_first = rec && !fused;
+  const bool ov = chain && P->overlap && !near_first;
+  P->adj_overlap = ov;
+  if (fused && chain && (rc = launch_adj_far(P, s)) != FMM_OK) return rc;
+  if ((rc = record(P, 16, s)) != FMM_OK) return rc;
   auto near = [&]() -> int {
     int r;
     if (fused) r = launch_adj_near(P, s);
@@ -1881,7 +1936,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if (r != FMM_OK) return r;
     return record(P, 10, s);
   };
-  if (rec && (rc = near()) != FMM_OK) return rc;
+  if (near_first && (rc = near()) != FMM_OK) return rc;
   if (chain) {
     cudaStream_t t = s;
     if (ov) {
@@ -1903,7 +1958,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
     if (ov) FMM_CUDA_TRY(cudaEventRecord(P->join_ev, t));
     if (rec) P->locals_valid = false;  // W and Lambda now hold what L and M held
   }
-  if (!rec && (rc = near()) != FMM_OK) return rc;
+  if (!near_first && (rc = near()) != FMM_OK) return rc;
   if (ov) FMM_CUDA_TRY(cudaStreamWaitEvent(s, P->join_ev, 0));
   if (gb && (rc = gbar_sum<T>(P, chain, s)) != FMM_OK) return rc;
   if ((rc = adj_source<T>(P, p, q, dx, dp, dq, gb, fused, s)) != FMM_OK) return rc;
@@ -1911,7 +1966,7 @@ int adjoint_t(fmm_plan_s* P, const double* x, const double* p, const double* q, 
   (void)x;
   P->adj_timed = (P->flags & FMM_TIMING) != 0;
   P->adj_chain = chain;
-  P->adj_order = ov ? 0 : (rec ? 2 : 1);
+  P->adj_order = ov ? 0 : (near_first ? 2 : 1);
   return FMM_OK;
 }
 

@@ -270,23 +270,22 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* _
 //   point with paired FP32 instructions (__fadd2_rn, __fmul2_rn,
 //   __ffma2_rn: two lanes per instruction), so one instruction stream serves
 //   two point pairs.
-// - In the nu1 loop R_x = X - s_x[nu1] is the only varying component, and
-//   the sums that carry R_x are split: sum q r3 R_x = X sum q r3 - sum
-//   (q s_x) r3.  The products q s_x of the source's effective masses with
-//   the x offset of their point are staged once per source cluster, so a
-//   point pair costs 10 FMA-pipe operations (|R|^2 1, r^-3 2, seven sums)
-//   instead of 13.  The split loses no more than a few units of the last
-//   place relative to the pair's field: |X| and |s_x| are at most |R| plus
-//   the two boxes' half widths, and admissible boxes are at least their
-//   radii apart.
+// - In the nu1 loop R_x = X - s_x[nu1] is the only varying component (held
+//   per nu1 in registers), so the sums are taken in r3 and r3 R_x and
+//   multiplied by R_y, R_z after the loop: a point pair costs 11 FMA-pipe
+//   operations (|R|^2 1, r^-3 2, r3 R_x 1, seven sums) on two staged float4.
+//   Splitting the R_x sums instead (sum q r3 R_x = X sum q r3 - sum (q s_x)
+//   r3, with q s_x staged) saves the r3 R_x product but doubles the shared
+//   loads; measured on the 2^24 core-halo beam (n = 8) at 4 blocks per SM
+//   this form takes 743 ms against the split form's 791 ms at 3 blocks.
 // Staged per source point, every value duplicated for the two lanes:
-// (a, a, b~x, b~x), (b~y, b~y, b~z, b~z), (-a s_x, ., -b~y s_x, .),
-// (-b~z s_x, ., 0, 0).  The running sums across sources are Kahan-compensated
-// in shared memory, in the same per-source groups as the other M2L kernels.
+// (a, a, b~x, b~x), (b~y, b~y, b~z, b~z).  The running sums across sources
+// are Kahan-compensated in shared memory, in the same per-source groups as
+// the other M2L kernels.
 // Items are (target, chunk of NT point pairs), fetched from the work counter
 // in the work order (longest source lists first).
 template <int NP1, int NT>
-__global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
+__global__ void __launch_bounds__(NT, 4) k_m2l_pair(const uint64_t* __restrict__ keys, const int32_t* __restrict__ off,
                                                    int shift, const unsigned int* __restrict__ err,
                                                    const int32_t* __restrict__ order, int64_t nitems,
                                                    unsigned int* __restrict__ work, const NodeGeo* __restrict__ geo,
@@ -296,8 +295,8 @@ __global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__
   constexpr int H = (m + 1) / 2;               // point pairs per cluster
   constexpr int SPLIT = (H + NT - 1) / NT;     // items per cluster
   extern __shared__ float4 dsm[];
-  float4* sm = dsm;                                           // [m][4] staged source points
-  float2* sacc = reinterpret_cast<float2*>(dsm + 4 * m);      // [12][NT] Kahan sums, compensations
+  float4* sm = dsm;                                           // [m][2] staged source points
+  float2* sacc = reinterpret_cast<float2*>(dsm + 2 * m);      // [12][NT] Kahan sums, compensations
   __shared__ float sxyz[3][NP1];               // source point offsets per axis
   __shared__ int64_t s_item;
   if (*err) return;  // the traversal failed: the lists are incomplete
@@ -331,12 +330,8 @@ __global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__
       const float* Ms = M + (size_t)s * 4 * m;
       for (int o = tid; o < m; o += NT) {
         const float a = Ms[o], bx = Ms[m + o], by = Ms[2 * m + o], bz = Ms[3 * m + o];
-        const float sx = (float)(gs.h[0] * ch.t[o % NP1]);
-        const float ua = -a * sx, uy = -by * sx, uz = -bz * sx;
-        sm[4 * o] = make_float4(a, a, bx, bx);
-        sm[4 * o + 1] = make_float4(by, by, bz, bz);
-        sm[4 * o + 2] = make_float4(ua, ua, uy, uy);
-        sm[4 * o + 3] = make_float4(uz, uz, 0.f, 0.f);
+        sm[2 * o] = make_float4(a, a, bx, bx);
+        sm[2 * o + 1] = make_float4(by, by, bz, bz);
       }
       if (tid < 3 * NP1) {
         const int d = tid / NP1, k = tid - d * NP1;
@@ -357,7 +352,7 @@ __global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__
         const float2 rz = __fadd2_rn(Z, make_float2(-sxyz[2][n3], -sxyz[2][n3]));
         const float2 nrz = __fmul2_rn(rz, neg1);
         const float2 dz = __fmul2_rn(rz, rz);
-        const float4* row = sm + 4 * n3 * NP1 * NP1;
+        const float4* row = sm + 2 * n3 * NP1 * NP1;
 #pragma unroll
         for (int n2 = 0; n2 < NP1; ++n2) {
           const float2 ry = __fadd2_rn(Y, make_float2(-sxyz[1][n2], -sxyz[1][n2]));
@@ -366,8 +361,8 @@ __global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__
           float2 Ta = z0, Ua = z0, Tbx = z0, Tby = z0, Uby = z0, Tbz = z0, Ubz = z0;
 #pragma unroll
           for (int n1 = 0; n1 < NP1; ++n1) {
-            const float4* q = row + 4 * (n2 * NP1 + n1);
-            const float4 A = q[0], Bq = q[1], C = q[2], D = q[3];
+            const float4* q = row + 2 * (n2 * NP1 + n1);
+            const float4 A = q[0], Bq = q[1];
             float2 d = __ffma2_rn(Rx[n1], Rx[n1], dyz);
             d.x = fmaxf(d.x, tiny_sep2<float>());
             d.y = fmaxf(d.y, tiny_sep2<float>());
@@ -377,12 +372,12 @@ __global__ void __launch_bounds__(NT, 3) k_m2l_pair(const uint64_t* __restrict__
             Tbx = __ffma2_rn(make_float2(A.z, A.w), r3, Tbx);
             Tby = __ffma2_rn(make_float2(Bq.x, Bq.y), r3, Tby);
             Tbz = __ffma2_rn(make_float2(Bq.z, Bq.w), r3, Tbz);
-            Ua = __ffma2_rn(make_float2(C.x, C.y), r3, Ua);
-            Uby = __ffma2_rn(make_float2(C.z, C.w), r3, Uby);
-            Ubz = __ffma2_rn(make_float2(D.x, D.y), r3, Ubz);
+            const float2 rr = __fmul2_rn(r3, Rx[n1]);
+            Ua = __ffma2_rn(make_float2(A.x, A.y), rr, Ua);
+            Uby = __ffma2_rn(make_float2(Bq.x, Bq.y), rr, Uby);
+            Ubz = __ffma2_rn(make_float2(Bq.z, Bq.w), rr, Ubz);
           }
-          // sum q r3 R_x = X sum q r3 - sum (q s_x) r3
-          const float2 TaR = __ffma2_rn(X, Ta, Ua), TbyR = __ffma2_rn(X, Tby, Uby), TbzR = __ffma2_rn(X, Tbz, Ubz);
+          const float2 TaR = Ua, TbyR = Uby, TbzR = Ubz;
           // E += (sum a r3 R_x, R_y sum a r3, R_z sum a r3)
           // B += (R_z sum b~y r3 - R_y sum b~z r3, sum b~z r3 R_x - R_z sum b~x r3,
           //       R_y sum b~x r3 - sum b~y r3 R_x)
@@ -421,7 +416,7 @@ template <int NP1, int NT>
 int launch_pair(fmm_plan_s* P, cudaStream_t s) {
   const Layout& L = P->lay;
   constexpr int m = NP1 * NP1 * NP1, H = (m + 1) / 2, SPLIT = (H + NT - 1) / NT;
-  const size_t smem = sizeof(float4) * 4 * m + sizeof(float2) * 12 * NT;
+  const size_t smem = sizeof(float4) * 2 * m + sizeof(float2) * 12 * NT;
   if (int rc = smem_limit(k_m2l_pair<NP1, NT>, (int)smem)) return rc;
   unsigned grid = 0;
   if (int rc = resident_blocks(k_m2l_pair<NP1, NT>, NT, smem, P->C * SPLIT, &grid)) return rc;

@@ -42,7 +42,7 @@ namespace {
 constexpr int kP2PPairLeaf = 256;  // near-field P2P with two targets per thread from this leaf size
 
 template <typename T, int KPT, bool POLY>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (KPT == 1 ? 8 : 4) : 1) k_p2p_l2p(
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (KPT == 1 ? 8 : 5) : 1) k_p2p_l2p(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ off, int shift, const unsigned int* __restrict__ err,
     const int64_t* __restrict__ nstart, const int64_t* __restrict__ ncount, int kappa,
     const NodeGeo* __restrict__ geo, const typename Vec4<T>::type* __restrict__ px,

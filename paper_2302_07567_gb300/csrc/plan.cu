@@ -552,8 +552,9 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
     if (P->adj_timed) {
       // the near-field kernel runs on the caller's stream from event 16 while
       // L2P^T .. M2M^T run on the side stream (order 0), after them (order
-      // 1, FMM_SERIAL) or before them (order 2, FMM_RECOMPUTE); the source
-      // side starts when both have finished
+      // 1, FMM_SERIAL) or before them (order 2, FMM_RECOMPUTE where the
+      // near-field kernel reads the leaf locals: FP64, the gbar term); the
+      // source side starts when both have finished
       const int ord = P->adj_chain ? P->adj_order : 2;
       P->stage_ms[11] = ord == 1 ? el(13, 10) : el(16, 10);  // near-field particle kernel
       if (P->adj_chain) {
@@ -565,7 +566,7 @@ int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
         P->stage_ms[12] = el(10, 14);
       }
       P->stage_ms[14] = el(15, 14);  // whole adjoint call
-      P->stage_ms[15] = el(15, 16);  // source-major lists, recompute if asked, weights
+      P->stage_ms[15] = el(15, 16);  // source-major lists, recompute if asked, weights, FP32 target-side far field
     }
     for (int k = 0; k < 18; ++k) out->stage_ms[k] = P->stage_ms[k];
   }

@@ -116,8 +116,11 @@ def test_second_adjoint_recomputes_and_matches(case):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
 def test_recompute_mode_matches_oracle_and_default(case, prec, tol):
     """FMM_RECOMPUTE keeps one set of expansions: W and Lambda overwrite the
-    locals and multipoles, the near field runs before the far-field chain,
-    and a second adjoint recomputes the upward pass, M2L and L2L.  Its
+    locals and multipoles, the target-side far field reads the locals before
+    the far-field chain (FP32: in a kernel of its own, after which the near
+    field runs beside the chain; FP64: inside the near-field kernel, which
+    runs first), and a second adjoint recomputes the upward pass, M2L and
+    L2L.  Its
     gradients equal those of the default plan bit for bit (every sum keeps
     its order) and so match the oracle's frozen-plan gradient."""
     plan, dx, dp, dq = gpu_grad(case, prec, flags=fmm.FMM_RECOMPUTE)
