@@ -947,6 +947,11 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
   constexpr int NC = 7;    // dL/dx' (3), dL/da', dL/db~' (3)
   extern __shared__ unsigned char smem_raw[];
   const int NT = blockDim.x / groups, grp = threadIdx.x / NT, lt = threadIdx.x - grp * NT;
+  // per thread and owned particle the running sums and their compensations,
+  // [KPT][2 NC][threads]: touched once per partner leaf, so they stay out of
+  // the registers of the pair loop
+  float* sK = reinterpret_cast<float*>(smem_raw + stage_bytes<float>(7, KPT, 2 * NC, groups, NT)) + threadIdx.x;
+  const int kstride = blockDim.x;
   const uint64_t mask = ((uint64_t)1 << shift) - 1;
   const int64_t per_chunk = (int64_t)KPT * NT;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {  // (leaf, chunk) items
@@ -959,7 +964,6 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
   int64_t jj[KPT];
   float4 u0[KPT], l0[KPT];
   float2 WE0[KPT], WE1[KPT], WE2[KPT], WB0[KPT], WB1[KPT], WB2[KPT], NA[KPT], B0[KPT], B1[KPT], B2[KPT];
-  float acc[KPT][NC], cmp[KPT][NC];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int64_t j0 = c0 + lt + (int64_t)k * NT;
@@ -973,7 +977,7 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
     NA[k] = make_float2(-u0[k].w, -u0[k].w);
     B0[k] = make_float2(b0.x, b0.x); B1[k] = make_float2(b0.y, b0.y); B2[k] = make_float2(b0.z, b0.z);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[k][c] = cmp[k][c] = 0.f;
+    for (int c = 0; c < 2 * NC; ++c) sK[(k * 2 * NC + c) * kstride] = 0.f;
   }
   const float2 m3 = make_float2(-3.f, -3.f);
   int it1 = off[L], it2 = soff[L];
@@ -1082,13 +1086,24 @@ __global__ void __launch_bounds__(128, KPT == 1 ? 5 : 3) k_adj_near(
       }
     }
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
+    for (int k = 0; k < KPT; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) kahan_add(acc[k][c], cmp[k][c], pp[k][c].x + pp[k][c].y);
-#pragma unroll
-      for (int c = 3; c < NC; ++c) kahan_add(acc[k][c], cmp[k][c], -(pp[k][c].x + pp[k][c].y));
-    }
+      for (int c = 0; c < NC; ++c) {
+        float* a = sK + (k * 2 * NC + c) * kstride;
+        float sum = a[0], comp = a[NC * kstride];
+        kahan_add(sum, comp, c < 3 ? pp[k][c].x + pp[k][c].y : -(pp[k][c].x + pp[k][c].y));
+        a[0] = sum;
+        a[NC * kstride] = comp;
+      }
   }
+  float acc[KPT][NC], cmp[KPT][NC];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      acc[k][c] = sK[(k * 2 * NC + c) * kstride];
+      cmp[k][c] = sK[(k * 2 * NC + NC + c) * kstride];
+    }
   __syncthreads();
   combine_groups<float, KPT, NC>(acc, cmp, reinterpret_cast<float*>(smem_raw), groups, grp, NT, lt);
 #pragma unroll
@@ -1841,7 +1856,8 @@ int launch_adj_near_k(fmm_plan_s* P, cudaStream_t s) {
   const int nt = groups * NT;
   const int64_t items = P->nleaves * chunks;
   unsigned grid = (unsigned)items;
-  const size_t smem = stage_bytes<float>(7, KPT, 14, groups, NT);  // 7 float4 per thread: half a 52-float pair
+  const size_t smem = stage_bytes<float>(7, KPT, 14, groups, NT)  // 7 float4 per thread: half a 52-float pair
+                      + sizeof(float) * KPT * 14 * nt;            // running sums and compensations
   if (int rc = set_smem(k_adj_near<KPT>, smem)) return rc;
   if (P->kappa > 0 && P->adj_overlap) {  // 3 per SM measured best at 2^9 leaves (4: +0.4%, one per item: +2%, 5: +4%)
     int sms = 0;
