@@ -416,6 +416,12 @@ def run_ours(args, rank, world, local):
                               "adjoint near field 84 per particle pair for both roles in one kernel (FP32), "
                               "else 46 (target side) and 67 (source side)",
                 "kernels": kernels}
+        # the whole step: every hot kernel's algorithmic flop over the timed
+        # step (branches that share the GPU counted once, by their flop)
+        step_flop = sum(kd["flop"] for kd in kernels.values())
+        step_s = t_max / args.steps  # one rank's step (replicas: every rank runs the same work)
+        roof["step"] = {"flop": step_flop, "ms": step_s * 1e3, "tflops": step_flop / step_s / 1e12,
+                        "frac": step_flop / step_s / 1e12 / peak32["tflops"] if peak32 else None}
 
     # HBM-bound stages of the forward (tree with its presort, P2M, L2P)
     hpk, hbasis = hbm_peak()

@@ -45,7 +45,7 @@ __device__ __forceinline__ void basis_deriv(T t, bool deg, const Cheb& ch, const
   const int np1 = ch.np1;
   for (int k = 0; k < np1; ++k) {
     T s = T(0);
-    for (int mm = 0; mm < np1; ++mm) s += l[mm] * (T)cd.D[mm * np1 + k];
+    for (int mm = 0; mm < np1; ++mm) s += l[mm] * cheb_diff<T>(cd, mm * np1 + k);
     dl[k] = deg ? T(0) : s;
   }
 }
@@ -1482,7 +1482,7 @@ __device__ __forceinline__ void basis_deriv_n(float t, bool deg, const Cheb& ch,
   for (int k = 0; k < NP1; ++k) {
     float acc = 0.f;
 #pragma unroll
-    for (int mm = 0; mm < NP1; ++mm) acc += l[mm] * (float)cd.D[mm * NP1 + k];
+    for (int mm = 0; mm < NP1; ++mm) acc += l[mm] * cd.Df[mm * NP1 + k];
     dl[k] = deg ? 0.f : acc;
   }
 }
@@ -1533,7 +1533,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_adj_final(
     }
     int nu = 0;
     for (int a3 = 0; a3 < np1; ++a3) {
-      for (int a2 = 0; a2 < np1; ++a2) {
+#pragma unroll
+      for (int a2 = 0; a2 < (NP1 > 0 ? NP1 : np1); ++a2) {
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, s0 = 0.f, sx = 0.f;
 #pragma unroll
         for (int a1 = 0; a1 < (NP1 > 0 ? NP1 : np1); ++a1, ++nu) {

@@ -69,6 +69,11 @@ struct Cheb {
   int np1;
   double t[kMaxNp1];
   double w[kMaxNp1];
+  // the same nodes and weights rounded to FP32 on the host: the FP32
+  // kernels read them as they are (a conversion from FP64 runs on the FP64
+  // unit, a small fraction of the FP32 rate)
+  float tf[kMaxNp1];
+  float wf[kMaxNp1];
 };
 
 // Differentiation matrix of the Lagrange basis on the Chebyshev points:
@@ -76,7 +81,28 @@ struct Cheb {
 // degree n - 1 and is reproduced by the interpolation, Theorem 1).
 struct ChebD {
   double D[kMaxNp1 * kMaxNp1];
+  float Df[kMaxNp1 * kMaxNp1];  // D rounded to FP32 on the host
 };
+
+// The tables in the arithmetic's precision.
+template <typename T>
+__device__ __forceinline__ T cheb_node(const Cheb& ch, int k);
+template <>
+__device__ __forceinline__ float cheb_node<float>(const Cheb& ch, int k) { return ch.tf[k]; }
+template <>
+__device__ __forceinline__ double cheb_node<double>(const Cheb& ch, int k) { return ch.t[k]; }
+template <typename T>
+__device__ __forceinline__ T cheb_weight(const Cheb& ch, int k);
+template <>
+__device__ __forceinline__ float cheb_weight<float>(const Cheb& ch, int k) { return ch.wf[k]; }
+template <>
+__device__ __forceinline__ double cheb_weight<double>(const Cheb& ch, int k) { return ch.w[k]; }
+template <typename T>
+__device__ __forceinline__ T cheb_diff(const ChebD& cd, int i);
+template <>
+__device__ __forceinline__ float cheb_diff<float>(const ChebD& cd, int i) { return cd.Df[i]; }
+template <>
+__device__ __forceinline__ double cheb_diff<double>(const ChebD& cd, int i) { return cd.D[i]; }
 
 // Per-node geometry in stretched, scaled coordinates (FP64).
 struct NodeGeo {
@@ -233,7 +259,7 @@ __device__ __forceinline__ void bary_basis(T t, bool degenerate, const Cheb& ch,
   int hit = degenerate ? 0 : -1;
   if (!degenerate) {
     for (int k = 0; k < np1; ++k) {
-      T d = t - T(ch.t[k]);
+      T d = t - cheb_node<T>(ch, k);
       if (hit < 0 && fabs(d) <= tiny) hit = k;
     }
   }
@@ -243,7 +269,7 @@ __device__ __forceinline__ void bary_basis(T t, bool degenerate, const Cheb& ch,
   }
   T s = T(0);
   for (int k = 0; k < np1; ++k) {
-    T v = T(ch.w[k]) / (t - T(ch.t[k]));
+    T v = cheb_weight<T>(ch, k) / (t - cheb_node<T>(ch, k));
     out[k] = v;
     s += v;
   }
@@ -259,7 +285,7 @@ __device__ __forceinline__ void bary_basis_n(float t, bool degenerate, const Che
   if (!degenerate) {
 #pragma unroll
     for (int k = 0; k < NP1; ++k)
-      if (hit < 0 && fabsf(t - (float)ch.t[k]) <= 1e-30f) hit = k;
+      if (hit < 0 && fabsf(t - ch.tf[k]) <= 1e-30f) hit = k;
   }
   if (hit >= 0) {
 #pragma unroll
@@ -269,7 +295,7 @@ __device__ __forceinline__ void bary_basis_n(float t, bool degenerate, const Che
   float sum = 0.f;
 #pragma unroll
   for (int k = 0; k < NP1; ++k) {
-    out[k] = (float)ch.w[k] / (t - (float)ch.t[k]);
+    out[k] = ch.wf[k] / (t - ch.tf[k]);
     sum += out[k];
   }
   const float inv = 1.f / sum;

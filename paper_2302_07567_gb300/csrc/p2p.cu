@@ -397,7 +397,8 @@ __global__ void __launch_bounds__(kFarThreads) k_l2p_far(
     }
     int mu = 0;
     for (int a3 = 0; a3 < np1; ++a3) {
-      for (int a2 = 0; a2 < np1; ++a2) {
+#pragma unroll
+      for (int a2 = 0; a2 < (NP1 > 0 ? NP1 : np1); ++a2) {
         const float w = lz[a3] * ly[a2];
         float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;
 #pragma unroll

@@ -208,6 +208,11 @@ void make_tables(fmm_plan_s* P) {
     }
     cd.D[a * np1 + a] = diag;
   }
+  for (int k = 0; k < np1; ++k) {
+    ch.tf[k] = (float)ch.t[k];
+    ch.wf[k] = (float)ch.w[k];
+  }
+  for (int k = 0; k < np1 * np1; ++k) cd.Df[k] = (float)cd.D[k];
 }
 
 // Default list capacities (cluster pairs): 128 P2P partners per leaf and 64

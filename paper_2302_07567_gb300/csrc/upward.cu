@@ -5,6 +5,8 @@
 // t_k the Chebyshev points of the second kind; the Lagrange basis is
 // evaluated in the barycentric form in the normalised variable t = (x - c)/h.
 // A side of zero width carries the basis l_0 = 1.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fmm {
@@ -181,6 +183,101 @@ __global__ void __launch_bounds__(256) k_p2m(const typename Vec4<T>::type* __res
   }
 }
 
+// FP32 P2M with the tensor structure of the basis,
+//   M_nu = sum_j l_nu1(x_j) l_nu2(y_j) l_nu3(z_j) m_j   (Alg. 3):
+// one block per leaf; a thread owns one (nu2, nu3) and all NP1 values of
+// nu1, so per staged particle it forms t_c = l_nu2(y) l_nu3(z) m_c once and
+// adds l_nu1(x) t_c for every nu1 (5 multiplies and 4 NP1 FMAs, against 6
+// NP1 operations and 4 NP1 shared loads of the point-per-thread form).  The
+// particles' 1-D bases and masses are staged a block-width at a time; sums
+// over runs of 32 particles are plain and Kahan-compensated across runs, as
+// in k_p2m.
+constexpr int kP2MSepThreads = 96;
+template <int NP1>
+__global__ void __launch_bounds__(kP2MSepThreads) k_p2m_sep(const float4* __restrict__ px,
+                                                          const float4* __restrict__ pb,
+                                                          const int64_t* __restrict__ nstart,
+                                                          const int64_t* __restrict__ ncount, int kappa,
+                                                          const NodeGeo* __restrict__ geo, Cheb ch,
+                                                          float* __restrict__ M) {
+  constexpr int m = NP1 * NP1 * NP1;
+  constexpr int boff = (3 * NP1 + 3) & ~3;  // (a, b~) at a 16-byte offset
+  constexpr int stride = boff + 4;
+  static_assert(NP1 * NP1 <= kP2MSepThreads, "one thread per (nu2, nu3)");
+  __shared__ __align__(16) float srow[kP2MSepThreads * stride];
+  const int64_t leaf = ((int64_t)1 << kappa) + blockIdx.x;
+  const int64_t st = nstart[leaf], cnt = ncount[leaf];
+  const NodeGeo g = geo[leaf];
+  float invh[3];
+  bool deg[3];
+  for (int k = 0; k < 3; ++k) {
+    deg[k] = !(g.h[k] > 0.0);
+    invh[k] = deg[k] ? 0.f : (float)(1.0 / g.h[k]);
+  }
+  const int tid = threadIdx.x;
+  const bool own = tid < NP1 * NP1;
+  const int nu2 = tid % NP1, nu3 = own ? tid / NP1 : 0;
+  float acc[NP1][4], cmp[NP1][4];
+#pragma unroll
+  for (int a = 0; a < NP1; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = cmp[a][c] = 0.f;
+  for (int64_t base = 0; base < cnt; base += kP2MSepThreads) {
+    const int64_t j = base + tid;
+    if (j < cnt) {
+      const float4 u = px[st + j], w = pb[st + j];
+      float* row = srow + tid * stride;
+      float l[NP1];
+      bary_basis_n<NP1>(u.x * invh[0], deg[0], ch, l);
+#pragma unroll
+      for (int k = 0; k < NP1; ++k) row[k] = l[k];
+      bary_basis_n<NP1>(u.y * invh[1], deg[1], ch, l);
+#pragma unroll
+      for (int k = 0; k < NP1; ++k) row[NP1 + k] = l[k];
+      bary_basis_n<NP1>(u.z * invh[2], deg[2], ch, l);
+#pragma unroll
+      for (int k = 0; k < NP1; ++k) row[2 * NP1 + k] = l[k];
+      *reinterpret_cast<float4*>(row + boff) = make_float4(u.w, w.x, w.y, w.z);
+    }
+    __syncthreads();
+    const int nj = (int)min64(kP2MSepThreads, cnt - base);
+    if (own) {
+      for (int j0 = 0; j0 < nj; j0 += 32) {
+        float part[NP1][4];
+#pragma unroll
+        for (int a = 0; a < NP1; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) part[a][c] = 0.f;
+        const int j1 = min(nj, j0 + 32);
+        for (int jj = j0; jj < j1; ++jj) {
+          const float* r = srow + jj * stride;
+          const float t = r[NP1 + nu2] * r[2 * NP1 + nu3];
+          const float4 ms = *reinterpret_cast<const float4*>(r + boff);
+          const float tc[4] = {t * ms.x, t * ms.y, t * ms.z, t * ms.w};
+#pragma unroll
+          for (int a = 0; a < NP1; ++a) {
+            const float lx = r[a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[a][c] = fmaf(lx, tc[c], part[a][c]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NP1; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) kahan_add(acc[a][c], cmp[a][c], part[a][c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (!own) return;
+#pragma unroll
+  for (int a = 0; a < NP1; ++a) {
+    const int nu = a + NP1 * (nu2 + NP1 * nu3);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) M[((size_t)leaf * 4 + c) * m + nu] = acc[a][c];
+  }
+}
+
 // M2L source table: per node and proxy point, (Y, a) and (b~, 0) with
 // Y = h o t_nu the point's offset from the box centre.
 template <typename T>
@@ -222,21 +319,45 @@ int launch_p2m(fmm_plan_s* P, cudaStream_t s) {
   return FMM_OK;
 }
 
+template <int NP1>
+int launch_p2m_sep(fmm_plan_s* P, cudaStream_t s) {
+  const Layout& L = P->lay;
+  k_p2m_sep<NP1><<<(unsigned)P->nleaves, kP2MSepThreads, 0, s>>>(
+      ws_ptr<float4>(P, L.px), ws_ptr<float4>(P, L.pb), ws_ptr<int64_t>(P, L.nstart), ws_ptr<int64_t>(P, L.ncount),
+      P->kappa, ws_ptr<NodeGeo>(P, L.ngeo), P->cheb, ws_ptr<float>(P, L.mpole));
+  FMM_LAUNCH_CHECK();
+  return FMM_OK;
+}
+
+// FP32 with 3, 5, 7 or 9 points per axis: the separable kernel; otherwise
+// (FP64, other degrees) the point-per-thread one.
+template <typename T>
+int launch_p2m_any(fmm_plan_s* P, cudaStream_t s) {
+  if (std::is_same<T, float>::value) {
+    switch (P->np1) {
+      case 3: return launch_p2m_sep<3>(P, s);
+      case 5: return launch_p2m_sep<5>(P, s);
+      case 7: return launch_p2m_sep<7>(P, s);
+      case 9: return launch_p2m_sep<9>(P, s);
+      default: break;
+    }
+  }
+  switch (div_up(P->m, 256)) {
+    case 1: return launch_p2m<T, 1>(P, s);
+    case 2: return launch_p2m<T, 2>(P, s);
+    case 3: return launch_p2m<T, 3>(P, s);
+    case 4: return launch_p2m<T, 4>(P, s);
+    case 5: return launch_p2m<T, 5>(P, s);
+    case 6: return launch_p2m<T, 6>(P, s);
+    case 7: return launch_p2m<T, 7>(P, s);
+    case 8: return launch_p2m<T, 8>(P, s);
+    default: return launch_p2m<T, 9>(P, s);
+  }
+}
+
 template <typename T>
 int upward_t(fmm_plan_s* P, cudaStream_t s, int xfer_cap, bool per_level) {
-  const int nv = (int)div_up(P->m, 256);
-  int rc;
-  switch (nv) {
-    case 1: rc = launch_p2m<T, 1>(P, s); break;
-    case 2: rc = launch_p2m<T, 2>(P, s); break;
-    case 3: rc = launch_p2m<T, 3>(P, s); break;
-    case 4: rc = launch_p2m<T, 4>(P, s); break;
-    case 5: rc = launch_p2m<T, 5>(P, s); break;
-    case 6: rc = launch_p2m<T, 6>(P, s); break;
-    case 7: rc = launch_p2m<T, 7>(P, s); break;
-    case 8: rc = launch_p2m<T, 8>(P, s); break;
-    default: rc = launch_p2m<T, 9>(P, s); break;
-  }
+  int rc = launch_p2m_any<T>(P, s);
   if (rc != FMM_OK) return rc;
   // P2M done (stage event of the forward call, not of a recomputation)
   if (!P->have_forward && (rc = record_stage(P, 9, s)) != FMM_OK) return rc;
