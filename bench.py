@@ -94,7 +94,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 GPU FMM side measurement")
     ap.add_argument("--sweep", action="store_true",
-                    help="the paper's uniform-cube experiments (Figs. 2, 3, Section 11) instead of the bench line")
+                    help="the paper's uniform-cube experiments (Figs. 2-4, Section 11) instead of the bench line")
+    ap.add_argument("--sweep-part", default="all", choices=["all", "fig2", "fig3", "fig4", "sec11"],
+                    help="with --sweep: one experiment only")
     ap.add_argument("--size-aware", action="store_true",
                     help="admissible pairs with fewer particle pairs than proxy-point pairs go to P2P (not in the paper)")
     ap.add_argument("--gbar-term", action="store_true",
@@ -649,7 +651,9 @@ def run_sweep(args):
 
     Fig. 2: forward time against the error of Eq. 5.1 for eta in {0.3, 0.4, 0.5} and
     n in {2, 4, 6, 8, 10} with N0 = (n+1)^3, N = 1.28e6.  Fig. 3: forward time against N
-    for n = 4, N0 = 125, eta = 0.5.  Section 11 (Fig. 7): N = 2.56e7 with the same
+    for n = 4, N0 = 125, eta = 0.5.  Fig. 4: the stage times (each stage alone) and the
+    interaction counts at, just above and halfway past the transitions N_t = 2^kappa N0
+    of the same case.  Section 11 (Fig. 7): N = 2.56e7 with the same
     parameters.  Times are CUDA-event medians of the whole fmm_field call (inputs in HBM);
     errors are max over E, B of the relative L2 error on 4096 sampled targets against the
     FP64 brute force.  One JSON line per point.
@@ -660,10 +664,11 @@ def run_sweep(args):
 
     dev = torch.device("cuda", 0)
 
-    def point(N, n, N0, eta, prec, reps=3, err=True, exp=""):
+    def point(N, n, N0, eta, prec, reps=3, err=True, exp="", stages=False):
         x, p, q = make_beam("cube", N=N)
         X, Pm, Q = (torch.as_tensor(a, device=dev) for a in (x, p, q))
-        plan = fmm.Plan(N, n, N0, eta, precision=prec)
+        # stages: every stage alone (FMM_SERIAL) with its own events
+        plan = fmm.Plan(N, n, N0, eta, precision=prec, flags=(fmm.FMM_TIMING | fmm.FMM_SERIAL) if stages else 0)
         for _ in range(2):
             plan.field(X, Pm, Q)
         times = []
@@ -677,6 +682,13 @@ def run_sweep(args):
             times.append(e0.elapsed_time(e1))
         out = {"sweep": exp, "N": N, "n": n, "N0": N0, "eta": eta, "precision": prec,
                "ms": statistics.median(times), "particles_per_s": N / (statistics.median(times) / 1e3)}
+        if stages:
+            st = plan.stats()
+            out["kappa"] = st["kappa"]
+            out["stage_ms"] = {k: round(st["stage_ms"][k], 4) for k in ("tree", "p2m", "upward", "traversal", "m2l",
+                                                                         "l2l", "p2p_l2p", "l2p")}
+            out["p2p_interactions"], out["m2l_interactions"] = st["p2p_interactions"], st["m2l_interactions"]
+            out["p2p_pairs"], out["m2l_pairs"] = st["p2p_pairs"], st["m2l_pairs"]
         if err:
             st = plan.stats()
             tg = torch.as_tensor(sample_targets(N, 4096, tag=9), device=dev)
@@ -688,17 +700,29 @@ def run_sweep(args):
         del plan
         torch.cuda.empty_cache()
 
-    for eta in (0.3, 0.4, 0.5):
-        for n in (2, 4, 6, 8, 10):
-            point(1_280_000, n, (n + 1) ** 3, eta, "fp32", exp="fig2")
-    for eta in (0.5,):
-        for n in (2, 4, 6):
-            point(1_280_000, n, (n + 1) ** 3, eta, "fp64", exp="fig2")
-    for N in (10_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000, 4_000_000, 8_000_000,
-              16_000_000):
-        point(N, 4, 125, 0.5, "fp32", err=False, exp="fig3")
-    point(25_600_000, 4, 125, 0.5, "fp32", exp="sec11")
-    point(25_600_000, 4, 125, 0.5, "fp64", reps=1, err=False, exp="sec11")
+    part = args.sweep_part
+    if part in ("all", "fig2"):
+        for eta in (0.3, 0.4, 0.5):
+            for n in (2, 4, 6, 8, 10):
+                point(1_280_000, n, (n + 1) ** 3, eta, "fp32", exp="fig2")
+        for eta in (0.5,):
+            for n in (2, 4, 6):
+                point(1_280_000, n, (n + 1) ** 3, eta, "fp64", exp="fig2")
+    if part in ("all", "fig3"):
+        for N in (10_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000, 2_000_000, 4_000_000, 8_000_000,
+                  16_000_000):
+            point(N, 4, 125, 0.5, "fp32", err=False, exp="fig3")
+    if part in ("all", "fig4"):
+        # the stages against N across the transitions N_t = 2^kappa N0, where
+        # the tree gains a level (Section 5's model: P2P work halves, M2L work
+        # doubles just above N_t)
+        for kappa in (10, 11, 12, 13):
+            Nt = (1 << kappa) * 125
+            for N in (Nt, Nt + 1, (3 * Nt) // 2):
+                point(N, 4, 125, 0.5, "fp32", err=False, exp="fig4", stages=True)
+    if part in ("all", "sec11"):
+        point(25_600_000, 4, 125, 0.5, "fp32", exp="sec11")
+        point(25_600_000, 4, 125, 0.5, "fp64", reps=1, err=False, exp="sec11")
 
 
 def main():
