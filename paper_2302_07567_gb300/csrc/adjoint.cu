@@ -1559,22 +1559,27 @@ __global__ void __launch_bounds__(kFinalThreads) k_adj_final(
     }
   }
   const float4 h1 = g1[pos], h2 = g2[pos];
-  const double gbar = scal[0], mu_u = scal[1], ell = scal[2];
+  // mu and ell are powers of two: their reciprocals (scal[11], scal[3]) are
+  // exact and a product by one equals the quotient; FP64 division runs on
+  // the FP64 unit at a small fraction of the FP32 rate
+  const double gbar = scal[0], imu = scal[11], iell = scal[3];
   // internal (a', b~', x') -> physical (a, b, x)
-  const double dA = ((double)h1.w + (double)F[0]) / mu_u;
-  const double dB[3] = {((double)h2.x + (double)F[1]) / (gbar * mu_u), ((double)h2.y + (double)F[2]) / (gbar * mu_u),
-                        ((double)h2.z + (double)F[3]) / mu_u};
-  const double dX[3] = {((double)h1.x + (double)(G[0] * invh[0])) / ell, ((double)h1.y + (double)(G[1] * invh[1])) / ell,
-                        gbar * ((double)h1.z + (double)(G[2] * invh[2])) / ell};
+  const double dA = ((double)h1.w + (double)F[0]) * imu;
+  const double dB[3] = {((double)h2.x + (double)F[1]) * imu / gbar, ((double)h2.y + (double)F[2]) * imu / gbar,
+                        ((double)h2.z + (double)F[3]) * imu};
+  const double dX[3] = {((double)h1.x + (double)(G[0] * invh[0])) * iell,
+                        ((double)h1.y + (double)(G[1] * invh[1])) * iell,
+                        gbar * ((double)h1.z + (double)(G[2] * invh[2])) * iell};
   const int64_t i = perm[pos];
   const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2], qi = q[i];
   const double gam = sqrt(1.0 + ((p0 * p0 + p1 * p1) + p2 * p2));
+  const double qa = qi * dA / gam;
   // a = q gamma, b = q p:  dL/dq = gamma dL/da + p . dL/db,
   //                        dL/dp = q (p/gamma) dL/da + q dL/db
   dq_out[i] = gam * dA + (p0 * dB[0] + p1 * dB[1] + p2 * dB[2]);
-  dp_out[3 * i + 0] = qi * (p0 / gam) * dA + qi * dB[0];
-  dp_out[3 * i + 1] = qi * (p1 / gam) * dA + qi * dB[1];
-  dp_out[3 * i + 2] = qi * (p2 / gam) * dA + qi * dB[2];
+  dp_out[3 * i + 0] = p0 * qa + qi * dB[0];
+  dp_out[3 * i + 1] = p1 * qa + qi * dB[1];
+  dp_out[3 * i + 2] = p2 * qa + qi * dB[2];
   dx_out[3 * i + 0] = dX[0];
   dx_out[3 * i + 1] = dX[1];
   dx_out[3 * i + 2] = dX[2];

@@ -97,8 +97,11 @@ struct ScatterSmem {
   uint32_t wcnt[kSortWarps][256];  // per warp and digit: keys of the current round
   uint32_t run[256];               // per digit: keys of the tile placed so far
   uint32_t gbase[256];             // per digit: first output slot of this tile
-  uint32_t cnt[256];
+  uint32_t cnt[256];               // per digit: keys of this tile
+  uint32_t loff[256];              // per digit: first slot of its run in the tile, reordered
   uint32_t wt[33];
+  uint64_t skey[kSortTile];        // the tile in digit order (stable)
+  uint32_t sval[kSortTile];
 };
 
 // The tile's keys (and values) in registers, thread-strided within each round.
@@ -118,10 +121,10 @@ __device__ __forceinline__ void load_tile(const uint64_t* keys, const uint32_t* 
   }
 }
 
-// Digit counts of the tile into S.cnt (valid after the call).
+// Digit counts of the tile into cnt[256] (valid after the call).
 __device__ __forceinline__ void tile_histogram(const uint64_t (&kk)[kSortRounds], int64_t base, int64_t n,
-                                               int shift, ScatterSmem& S) {
-  S.cnt[threadIdx.x] = 0;
+                                               int shift, uint32_t* cnt) {
+  cnt[threadIdx.x] = 0;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
@@ -129,21 +132,27 @@ __device__ __forceinline__ void tile_histogram(const uint64_t (&kk)[kSortRounds]
     const bool valid = i < n;
     const unsigned d = valid ? (unsigned)((kk[r] >> shift) & 0xffu) : 0x100u + (threadIdx.x & 31);
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&S.cnt[d], (uint32_t)__popc(peers));
+    if (valid && (peers & lanemask_lt()) == 0u) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
 }
 
 // Stable scatter of the tile by its digit; S.gbase holds the tile's first
-// output slot of every digit.  Rounds go in input order, warps in order
-// inside a round and lanes in order inside a warp.
+// output slot of every digit and S.cnt its count of every digit.  Rounds go
+// in input order, warps in order inside a round and lanes in order inside a
+// warp.  The tile is first reordered by digit in shared memory, then written
+// out in that order, so that consecutive threads write consecutive slots of
+// one digit's run (coalesced) instead of slots of up to 32 different runs.
 __device__ __forceinline__ void tile_scatter(const uint64_t (&kk)[kSortRounds], const uint32_t (&vv)[kSortRounds],
                                              int64_t base, int64_t n, int shift, bool with_vals, ScatterSmem& S,
                                              uint64_t* keys_out, uint32_t* vals_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = 0; w < kSortWarps; ++w) S.wcnt[w][threadIdx.x] = 0;
   S.run[threadIdx.x] = 0;
-  __syncthreads();
+  {
+    uint32_t tot;
+    S.loff[threadIdx.x] = block_exclusive_scan(S.cnt[threadIdx.x], S.wt, tot);  // synchronises
+  }
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
@@ -156,9 +165,9 @@ __device__ __forceinline__ void tile_scatter(const uint64_t (&kk)[kSortRounds], 
     if (valid) {
       uint32_t pre = S.run[d];
       for (int w = 0; w < warp; ++w) pre += S.wcnt[w][d];
-      const uint32_t pos = S.gbase[d] + pre + wr;
-      keys_out[pos] = kk[r];
-      if (with_vals) vals_out[pos] = vv[r];
+      const uint32_t lpos = S.loff[d] + pre + wr;
+      S.skey[lpos] = kk[r];
+      S.sval[lpos] = vv[r];
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -169,21 +178,29 @@ __device__ __forceinline__ void tile_scatter(const uint64_t (&kk)[kSortRounds], 
     S.run[threadIdx.x] += tot;
     __syncthreads();
   }
+  const int nv = (int)(n - base < kSortTile ? n - base : kSortTile);
+  for (int e = threadIdx.x; e < nv; e += kSortThreads) {
+    const uint64_t key = S.skey[e];
+    const unsigned d = (unsigned)((key >> shift) & 0xffu);
+    const uint32_t pos = S.gbase[d] + ((uint32_t)e - S.loff[d]);
+    keys_out[pos] = key;
+    if (with_vals) vals_out[pos] = S.sval[e];
+  }
 }
 
 // Digit histogram of one tile of one batch: hist[batch][digit][tile].
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint64_t* __restrict__ keys, int64_t stride,
                                                                int64_t n, int shift, int64_t ntiles,
                                                                uint32_t* __restrict__ hist) {
-  __shared__ ScatterSmem S;
+  __shared__ uint32_t cnt[256];
   keys += blockIdx.y * stride;
   hist += (int64_t)blockIdx.y * 256 * ntiles;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   uint64_t kk[kSortRounds];
   uint32_t vv[kSortRounds];
   load_tile<false>(keys, nullptr, base, n, kk, vv);
-  tile_histogram(kk, base, n, shift, S);
-  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = S.cnt[threadIdx.x];
+  tile_histogram(kk, base, n, shift, cnt);
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
 // Stable scatter of one tile by its digit; `hist` holds the exclusive scan
@@ -205,7 +222,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(
   uint64_t kk[kSortRounds];
   uint32_t vv[kSortRounds];
   load_tile<false>(keys, vals, base, n, kk, vv);
-  S.gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  // hist is the exclusive scan over (digit, tile), digit-major: the next
+  // entry (the next tile, or the next digit's first tile) ends this one
+  const int64_t f = (int64_t)threadIdx.x * ntiles + blockIdx.x;
+  const uint32_t g0 = hist[f];
+  S.gbase[threadIdx.x] = g0;
+  S.cnt[threadIdx.x] = (f + 1 < 256 * ntiles ? hist[f + 1] : (uint32_t)n) - g0;
   tile_scatter(kk, vv, base, n, shift, vals != nullptr, S, keys_out, vals_out);
 }
 
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_coop(uint64_t* keys, uin
       uint64_t kk[kSortRounds];
       uint32_t vv[kSortRounds];
       load_tile<true>(kin + batch * stride, nullptr, base, n, kk, vv);
-      tile_histogram(kk, base, n, shift, S);
+      tile_histogram(kk, base, n, shift, S.cnt);
       hist[it * 256 + threadIdx.x] = S.cnt[threadIdx.x];
     }
     grid.sync();
@@ -255,6 +277,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_coop(uint64_t* keys, uin
       }
       uint32_t all;
       S.gbase[threadIdx.x] = block_exclusive_scan(tot, S.wt, all) + before;
+      S.cnt[threadIdx.x] = __ldcg(h + tile * 256);
       tile_scatter(kk, vv, base, n, shift, with_vals, S, kout + batch * stride,
                    with_vals ? vout + batch * stride : nullptr);
     }

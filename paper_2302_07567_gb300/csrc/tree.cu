@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pairwise(const double* __restri
 }
 
 // Last level (at most 2048 partials per component), max |q| and
-// scal[0] = gbar, scal[1] = mass unit mu (power of two near max|q|),
+// scal[0] = gbar, scal[1] = mass unit mu (power of two near max|q|), scal[11] = 1/mu,
 // scal[6..8] = pbar (for the adjoint's gbar term).
 __global__ void __launch_bounds__(kRedThreads) k_setup_final(const double* __restrict__ part, int64_t n,
                                                             int64_t comp_step, int64_t N,
@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(kRedThreads) k_setup_final(const double* __res
   const double px = __ddiv_rn(sum[0], dn), py = __ddiv_rn(sum[1], dn), pz = __ddiv_rn(sum[2], dn);
   const double pp = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
   scal[0] = __dsqrt_rn(__dadd_rn(1.0, pp));
-  scal[1] = (m > 0.0 && isfinite(m)) ? ldexp(1.0, (int)rint(log2(m))) : 1.0;
+  const int me = (m > 0.0 && isfinite(m)) ? (int)rint(log2(m)) : 0;
+  scal[1] = ldexp(1.0, me);
+  scal[11] = ldexp(1.0, -me);  // 1/mu, exact
   scal[6] = px;
   scal[7] = py;
   scal[8] = pz;

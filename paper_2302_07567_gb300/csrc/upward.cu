@@ -72,7 +72,7 @@ __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ 
                        const double* __restrict__ scal, typename Vec4<T>::type* __restrict__ px,
                        typename Vec4<T>::type* __restrict__ pb, typename Vec4<T>::type* __restrict__ pl) {
   const int64_t first = (int64_t)1 << kappa;
-  const double gbar = scal[0], imu = 1.0 / scal[1], inv = scal[3];
+  const double gbar = scal[0], imu = scal[11], inv = scal[3];
   for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < N;
        pos += (int64_t)gridDim.x * blockDim.x) {
     const int64_t leaf = find_node(nstart, first, first, pos);
