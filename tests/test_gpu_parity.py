@@ -126,6 +126,23 @@ def test_multipoles_and_locals_fp64(case, gpu64):
         assert err.max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("n", [2, 3, 4, 6, 8])
+def test_multipoles_fp32(n):
+    """FP32 multipoles (Alg. 3 at the leaves, the separable kernel for 3, 5,
+    7 and 9 points per axis, the point-per-thread one for 4; Alg. 5 above)
+    node by node within FP32 rounding of the oracle's."""
+    x, p, q = make_beam("gauss4k", N=3000)
+    leaf = 64
+    rp = bldtt.build_plan(x, p, n, leaf, 0.5)
+    ref = bldtt.fmm_stages(x, p, q, rp)
+    plan, _, _ = run(x, p, q, n, leaf, 0.5, "fp32")
+    C = rp.tree.C
+    Mref = np.stack([ref["M"][i].numpy().T for i in range(1, C + 1)])
+    Mg = plan.export("multipole").astype(np.float64)
+    assert Mg.shape == Mref.shape
+    assert _node_rel(Mg, Mref).max() < 2e-6
+
+
 def test_fields_fp64_match_oracle_fmm(case, gpu64):
     _, E, B = gpu64
     ref = case["ref"]
