@@ -513,6 +513,29 @@ def run_extras(args, fmm, torch, dev, w, N, eta, x, p, q, X, Pm, Q, WE, WB, adj,
         del ap
         torch.cuda.empty_cache()
 
+    # the step recorded as CUDA graphs (fmm_step_graph_*) and replayed: the
+    # same kernels in the same order, without a host launch for each; timed
+    # on the host per replay, which waits for its forward's list check and
+    # for its end
+    gp = fmm.Plan(N, w.n, w.leaf, eta, precision=args.precision, flags=flags)
+    Xg, Pg, Qg = X.clone(), Pm.clone(), Q.clone()
+    gout = gp.record_step(Xg, Pg, Qg, *((WE, WB) if adj else ()))
+    greps = 5 if N <= (1 << 22) else 2
+    gp.replay()
+    torch.cuda.synchronize()
+    k0 = fmm.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(greps):
+        gp.replay()
+    gms = (time.perf_counter() - t0) * 1e3 / greps
+    out["graph"] = {"value": N / (gms / 1e3), "unit": "particles/s", "ms_per_step": gms, "steps": greps,
+                    "kernels_per_step": (fmm.kernel_launches() - k0) / greps,
+                    "timing": "host clock per replay (each replay waits for its end)"}
+    del gout
+    gp.close()
+    del gp, Xg, Pg, Qg
+    torch.cuda.empty_cache()
+
     # tracking: per step the forward field and a Boris push (electron
     # charge and mass per particle, dt = 1 ps), with the tree and lists kept
     # while admissible (fmm_field_reuse) and built anew every step (fmm_field)

@@ -208,6 +208,39 @@ int fmm_field_adjoint(fmm_plan_t plan, const double* x, const double* p, const d
                       const void* wE, const void* wB, double* dx, double* dp, double* dq,
                       void* stream);
 
+/* A recorded step (not in the paper): fmm_field and, with wE != NULL,
+ * fmm_field_adjoint on these arguments, kept by the plan as two CUDA graphs
+ * (the forward, the adjoint) and replayed by fmm_step_graph_launch.  A replay
+ * runs the kernels of the calls it recorded in the same order, so on the same
+ * input its results equal theirs bit for bit; it spares the host the launch of
+ * every kernel (about 300 per forward and adjoint), which bounds the step of a
+ * small beam.  The graphs hold the pointers: x, p, q, wE, wB, E, B, dx, dp, dq
+ * must stay allocated at these addresses while the graphs exist, and a replay
+ * reads what they hold then (a tracking or optimisation loop updates x, p, q,
+ * wE, wB in place).  The call first runs the step once as usual, so it
+ * returns that step's errors (after FMM_EOVERFLOW the caller grows the
+ * capacities and calls again), then records it.  Arguments as fmm_field and
+ * fmm_field_adjoint (dx, dp, dq may be NULL when wE is NULL).  FMM_EINVAL for
+ * NULL arguments, a legacy default stream (NULL, cudaStreamLegacy or
+ * cudaStreamPerThread, which cannot be recorded), FMM_TIMING or
+ * FMM_BOUNDS_CHECK (they time or wait on the host); FMM_ECUDA, and no graphs,
+ * if recording fails.  fmm_plan_set_capacity, fmm_plan_set_workspace and
+ * fmm_plan_destroy drop the graphs. */
+int fmm_step_graph_create(fmm_plan_t plan, const double* x, const double* p, const double* q, const void* wE,
+                          const void* wB, void* E, void* B, double* dx, double* dp, double* dq, void* stream);
+
+/* Replays the recorded step on `stream` and waits for it: the forward, a read
+ * of its list sizes and device error flags, then (if recorded) the adjoint.
+ * Returns what fmm_field would return on the arrays' current contents; on
+ * FMM_EOVERFLOW or FMM_ENONFINITE the adjoint is not replayed and nothing is
+ * written to E, B, dx, dp, dq (the graphs stay; after growing the capacities,
+ * which drops them, the caller records anew).  FMM_ESTATE without a recorded
+ * step. */
+int fmm_step_graph_launch(fmm_plan_t plan, void* stream);
+
+/* Drops the recorded step, if any. */
+int fmm_step_graph_destroy(fmm_plan_t plan);
+
 typedef struct fmm_stats {
   int64_t N, nodes, leaves;
   int32_t degree, leaf_size, kappa, precision;

@@ -173,6 +173,11 @@ struct fmm_plan_s {
   bool adj_overlap = false;  // the running adjoint has its two branches on two streams
   int adj_order = 0;       // stage order of the last adjoint: 0 branches overlapped, 1 chain then
                            // near field (FMM_SERIAL), 2 near field then chain (FMM_RECOMPUTE)
+  // a recorded step (fmm_step_graph_*): the forward and, if recorded, the adjoint
+  cudaGraphExec_t graph_fwd = nullptr, graph_adj = nullptr;
+  long long graph_fwd_kernels = 0, graph_adj_kernels = 0;  // kernel launches of one replay
+  bool graph_locals_valid = false;  // locals_valid after a replayed step
+  bool capturing = false;           // forward / adjoint are being recorded: no host waits
 };
 
 namespace fmm {

@@ -234,6 +234,14 @@ int ensure_events(fmm_plan_s* P) {
 
 int record(fmm_plan_s* P, int k, cudaStream_t s) { return record_stage(P, k, s); }
 
+// Drops the recorded step (fmm_step_graph_*).
+void drop_graphs(fmm_plan_s* P) {
+  if (P->graph_fwd) cudaGraphExecDestroy(P->graph_fwd);
+  if (P->graph_adj) cudaGraphExecDestroy(P->graph_adj);
+  P->graph_fwd = P->graph_adj = nullptr;
+  P->graph_fwd_kernels = P->graph_adj_kernels = 0;
+}
+
 }  // namespace
 
 int record_stage(fmm_plan_s* P, int k, cudaStream_t s) {
@@ -324,6 +332,7 @@ int fmm_plan_set_capacity(fmm_plan_t P, int64_t p2p_pairs, int64_t m2l_pairs, in
   if (frontier_pairs > 0) P->cap_frontier = frontier_pairs;
   default_caps(P);
   make_layout(P);
+  drop_graphs(P);  // they record the old workspace's addresses
   P->ws = nullptr;
   P->ws_bytes = 0;
   P->have_forward = false;
@@ -339,6 +348,7 @@ int fmm_plan_workspace_bytes(fmm_plan_t P, size_t* bytes) {
 int fmm_plan_set_workspace(fmm_plan_t P, void* dev, size_t bytes) {
   if (!P || !dev) return FMM_EINVAL;
   if (bytes < P->lay.total || ((uintptr_t)dev & 255u)) return FMM_ENOWORKSPACE;
+  drop_graphs(P);  // they record the old workspace's addresses
   P->ws = static_cast<char*>(dev);
   P->ws_bytes = bytes;
   P->have_forward = false;
@@ -358,6 +368,27 @@ namespace {
 // and kStaleLists is returned (E, B unwritten) if an M2L pair is no longer
 // admissible.
 constexpr int kStaleLists = -1;
+
+// The list sizes, device error flags and scalars a forward copied to the
+// pinned slot after its traversal (the copy must have completed).
+int check_counters(fmm_plan_s* P, bool reuse) {
+  const Counters* hc = static_cast<const Counters*>(P->hpin);
+  const double* hs = reinterpret_cast<const double*>(static_cast<const char*>(P->hpin) + 256);
+  if (!reuse) {  // with reuse the lists, their sizes and pair counts stay those of the last forward
+    P->p2p_count = (int64_t)hc->p2p_count;
+    P->m2l_count = (int64_t)hc->m2l_count;
+    P->p2p_work = (double)hc->p2p_work;
+  }
+  if (hc->err & kErrNonFinite) return FMM_ENONFINITE;
+  if (hc->err & kErrStale) return kStaleLists;
+  if ((hc->err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || P->p2p_count > P->cap_p2p ||
+      P->m2l_count > P->cap_m2l)
+    return FMM_EOVERFLOW;
+  P->gbar = hs[0];
+  P->munit = hs[1];
+  P->lunit = hs[2];
+  return FMM_OK;
+}
 
 int forward(fmm_plan_s* P, const double* x, const double* p, const double* q, void* E, void* B, cudaStream_t s,
             bool reuse) {
@@ -395,23 +426,12 @@ int forward(fmm_plan_s* P, const double* x, const double* p, const double* q, vo
   static_assert(sizeof(Counters) <= 256, "counters fit the pinned slot");
   FMM_CUDA_TRY(cudaMemcpyAsync(hc, P->ws + P->lay.counters, sizeof(Counters), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaMemcpyAsync(hs, P->ws + P->lay.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  FMM_CUDA_TRY(cudaEventRecord(P->trav_ev, s));
+  // (not while recording: an event recorded into a graph cannot be waited on
+  // afterwards, and the replay is waited on as a whole)
+  if (!P->capturing) FMM_CUDA_TRY(cudaEventRecord(P->trav_ev, s));
   auto read_back = [&]() -> int {
     FMM_CUDA_TRY(cudaEventSynchronize(P->trav_ev));
-    if (!reuse) {  // with reuse the lists, their sizes and pair counts stay those of the last forward
-      P->p2p_count = (int64_t)hc->p2p_count;
-      P->m2l_count = (int64_t)hc->m2l_count;
-      P->p2p_work = (double)hc->p2p_work;
-    }
-    if (hc->err & kErrNonFinite) return FMM_ENONFINITE;
-    if (hc->err & kErrStale) return kStaleLists;
-    if ((hc->err & (kErrOvfFrontier | kErrOvfP2P | kErrOvfM2L)) || P->p2p_count > P->cap_p2p ||
-        P->m2l_count > P->cap_m2l)
-      return FMM_EOVERFLOW;
-    P->gbar = hs[0];
-    P->munit = hs[1];
-    P->lunit = hs[2];
-    return FMM_OK;
+    return check_counters(P, reuse);
   };
   const bool wait_first = (P->flags & FMM_BOUNDS_CHECK) != 0;
   if (wait_first) {
@@ -456,7 +476,9 @@ int forward(fmm_plan_s* P, const double* x, const double* p, const double* q, vo
     if ((rc = record(P, 8, s)) != FMM_OK) return rc;
   }
   P->split_fwd = split;
-  if (!wait_first && (rc = read_back()) != FMM_OK) return rc;
+  // while recording a step the host waits for nothing: fmm_step_graph_launch
+  // reads the counters after the replay
+  if (!wait_first && !P->capturing && (rc = read_back()) != FMM_OK) return rc;
   P->have_forward = true;
   P->transposed_valid = false;
   P->locals_valid = true;
@@ -502,6 +524,108 @@ int fmm_field_adjoint(fmm_plan_t P, const double* x, const double* p, const doub
   if (!P->have_forward) return FMM_ESTATE;
   if (P->flags & FMM_TEST_POLY_KERNEL) return FMM_EINVAL;  // the adjoint is of the physical kernel only
   return run_adjoint(P, x, p, q, wE, wB, dx, dp, dq, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace fmm {
+namespace {
+// Records what `body` queues on s into an instantiated graph; the kernel
+// launches it counted are taken back off the launch counter (recorded, not
+// run) and returned in *kernels.
+template <typename F>
+int record_graph(fmm_plan_s* P, cudaStream_t s, F body, cudaGraphExec_t* out, long long* kernels) {
+  *out = nullptr;
+  const long long before = g_launches.load();
+  FMM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  P->capturing = true;
+  const int rc = body();
+  P->capturing = false;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s, &g);
+  const long long n = g_launches.load() - before;
+  g_launches.fetch_sub(n);
+  if (rc != FMM_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (rc != FMM_OK) return rc;
+    set_last_cuda_error(ce);
+    return FMM_ECUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *out = nullptr;
+    set_last_cuda_error(ie);
+    return FMM_ECUDA;
+  }
+  *kernels = n;
+  return FMM_OK;
+}
+}  // namespace
+}  // namespace fmm
+
+extern "C" {
+
+int fmm_step_graph_create(fmm_plan_t P, const double* x, const double* p, const double* q, const void* wE,
+                          const void* wB, void* E, void* B, double* dx, double* dp, double* dq, void* stream) {
+  if (!P || !x || !p || !q || !E || !B) return FMM_EINVAL;
+  const bool adj = wE != nullptr;
+  if (adj && (!wB || !dx || !dp || !dq)) return FMM_EINVAL;
+  if (!P->ws) return FMM_ENOWORKSPACE;
+  if (P->flags & (FMM_TIMING | FMM_BOUNDS_CHECK)) return FMM_EINVAL;  // host-side timing or waits
+  if (adj && (P->flags & FMM_TEST_POLY_KERNEL)) return FMM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return FMM_EINVAL;  // not recordable
+  drop_graphs(P);
+  // the step once as usual: it makes the plan's events, side stream and
+  // pinned slot, the per-device launch facts, and returns the step's errors
+  int rc = fmm_field(P, x, p, q, E, B, stream);
+  if (rc == FMM_OK && adj) rc = fmm_field_adjoint(P, x, p, q, wE, wB, dx, dp, dq, stream);
+  if (rc != FMM_OK) return rc;
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  P->reuse_stale = false;
+  rc = record_graph(P, s, [&]() { return forward(P, x, p, q, E, B, s, false); }, &P->graph_fwd,
+                    &P->graph_fwd_kernels);
+  if (rc == FMM_OK && adj)
+    rc = record_graph(P, s, [&]() { return run_adjoint(P, x, p, q, wE, wB, dx, dp, dq, s); }, &P->graph_adj,
+                      &P->graph_adj_kernels);
+  if (rc != FMM_OK) {
+    drop_graphs(P);
+    P->have_forward = false;
+    return rc;
+  }
+  P->graph_locals_valid = P->locals_valid;
+  return FMM_OK;
+}
+
+int fmm_step_graph_launch(fmm_plan_t P, void* stream) {
+  if (!P) return FMM_EINVAL;
+  if (!P->graph_fwd || !P->ws) return FMM_ESTATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  P->have_forward = false;
+  FMM_CUDA_TRY(cudaGraphLaunch(P->graph_fwd, s));
+  g_launches.fetch_add(P->graph_fwd_kernels);
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  P->last_stream = s;
+  int rc = check_counters(P, false);
+  if (rc != FMM_OK) return rc;
+  P->have_forward = true;
+  P->transposed_valid = false;
+  P->locals_valid = true;
+  if (P->graph_adj) {
+    FMM_CUDA_TRY(cudaGraphLaunch(P->graph_adj, s));
+    g_launches.fetch_add(P->graph_adj_kernels);
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    P->transposed_valid = true;
+    P->locals_valid = P->graph_locals_valid;
+  }
+  return FMM_OK;
+}
+
+int fmm_step_graph_destroy(fmm_plan_t P) {
+  if (!P) return FMM_EINVAL;
+  drop_graphs(P);
+  return FMM_OK;
 }
 
 int fmm_plan_stats(fmm_plan_t P, fmm_stats* out) {
@@ -680,6 +804,7 @@ int fmm_plan_export(fmm_plan_t P, int what, void* host, size_t bytes) {
 
 void fmm_plan_destroy(fmm_plan_t P) {
   if (!P) return;
+  drop_graphs(P);
   if (P->ev_made)
     for (auto& e : P->ev) cudaEventDestroy(e);
   if (P->hpin) {
@@ -693,6 +818,7 @@ void fmm_plan_destroy(fmm_plan_t P) {
     cudaEventDestroy(P->fork_ev);
     cudaEventDestroy(P->join_ev);
   }
+  (void)cudaGetLastError();  // the teardown is best effort: leave no error for the next call to report
   delete P;
 }
 

@@ -65,6 +65,9 @@ def lib():
     P, I64, I32, D, U, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_size_t
     sig = {
         "fmm_plan_create": (I32, [ctypes.POINTER(P), I64, I32, I32, D, I32, U]),
+        "fmm_step_graph_create": (I32, [P] * 12),
+        "fmm_step_graph_launch": (I32, [P, P]),
+        "fmm_step_graph_destroy": (I32, [P]),
         "fmm_plan_set_capacity": (I32, [P, I64, I64, I64]),
         "fmm_plan_workspace_bytes": (I32, [P, ctypes.POINTER(SZ)]),
         "fmm_plan_set_workspace": (I32, [P, P, SZ]),
@@ -193,22 +196,80 @@ class Plan:
                     rc = lib().fmm_field(self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(E), _ptr(B), _stream(dev))
             if rc != FMM_EOVERFLOW:
                 break
-            # the traversal counts every pair it finds, also past a full list:
-            # a list that overflowed grows to 1.25 times its count (at least
-            # doubling); with both lists within their capacities it was the
-            # traversal frontier that overflowed, which grows fourfold
-            st = self.stats()
-            p2p_over = st["p2p_pairs"] > st["cap_p2p"]
-            m2l_over = st["m2l_pairs"] > st["cap_m2l"]
-            grow = lambda cap, cnt: max(2 * cap, int(1.25 * cnt) + 1024)  # noqa: E731
-            self.set_capacity(grow(st["cap_p2p"], st["p2p_pairs"]) if p2p_over else 0,
-                              grow(st["cap_m2l"], st["m2l_pairs"]) if m2l_over else 0,
-                              0 if (p2p_over or m2l_over) else 4 * st["cap_frontier"])
+            self._grow()
         if rc != FMM_OK:
             raise FMMError(rc, "fmm_field_reuse" if reuse else "fmm_field")
         self.generation += 1
         self.last_rebuilt = bool(rebuilt.value)
         return E, B
+
+    def _grow(self):
+        # the traversal counts every pair it finds, also past a full list: a
+        # list that overflowed grows to 1.25 times its count (at least
+        # doubling); with both lists within their capacities it was the
+        # traversal frontier that overflowed, which grows fourfold
+        st = self.stats()
+        p2p_over = st["p2p_pairs"] > st["cap_p2p"]
+        m2l_over = st["m2l_pairs"] > st["cap_m2l"]
+        grow = lambda cap, cnt: max(2 * cap, int(1.25 * cnt) + 1024)  # noqa: E731
+        self.set_capacity(grow(st["cap_p2p"], st["p2p_pairs"]) if p2p_over else 0,
+                          grow(st["cap_m2l"], st["m2l_pairs"]) if m2l_over else 0,
+                          0 if (p2p_over or m2l_over) else 4 * st["cap_frontier"])
+
+    # -- recorded steps (CUDA graphs)
+    def record_step(self, x, p, q, wE=None, wB=None, max_retries: int = 10):
+        """Record one step, field() and with wE, wB also adjoint(), on these
+        tensors as CUDA graphs (fmm_step_graph_create); returns the tensors the
+        replays write: (E, B), or (E, B, dx, dp, dq) with the adjoint.
+
+        The graphs hold the tensors' addresses: keep them (the plan keeps a
+        reference) and update their contents in place between replay() calls.
+        The recording runs the step once (growing the capacities on an
+        overflow, as field() does) and uses a stream of the plan's own, since
+        the legacy default stream cannot be recorded.
+        """
+        N, dev = self.N, self.device
+        _check_in(x, "x", (N, 3), torch.float64, dev)
+        _check_in(p, "p", (N, 3), torch.float64, dev)
+        _check_in(q, "q", (N,), torch.float64, dev)
+        adj = wE is not None
+        if adj:
+            _check_in(wE, "wE", (N, 3), self.out_dtype, dev)
+            _check_in(wB, "wB", (N, 3), self.out_dtype, dev)
+        E = torch.empty((N, 3), dtype=self.out_dtype, device=dev)
+        B = torch.empty((N, 3), dtype=self.out_dtype, device=dev)
+        grads = [torch.empty(sh, dtype=torch.float64, device=dev) for sh in ((N, 3), (N, 3), (N,))] if adj else []
+        if getattr(self, "_gstream", None) is None:
+            self._gstream = torch.cuda.Stream(dev)
+        gs = self._gstream
+        nul = ctypes.c_void_p(None)
+        for _ in range(max_retries + 1):
+            gs.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.device(dev):
+                rc = lib().fmm_step_graph_create(
+                    self._h, _ptr(x), _ptr(p), _ptr(q), _ptr(wE) if adj else nul, _ptr(wB) if adj else nul,
+                    _ptr(E), _ptr(B), *([_ptr(g) for g in grads] if adj else [nul, nul, nul]),
+                    ctypes.c_void_p(gs.cuda_stream))
+            if rc != FMM_EOVERFLOW:
+                break
+            self._grow()
+        if rc != FMM_OK:
+            raise FMMError(rc, "fmm_step_graph_create")
+        self._graph_refs = (x, p, q, wE, wB, E, B, *grads)
+        self.generation += 1
+        return (E, B, *grads)
+
+    def replay(self):
+        """Replay the recorded step (fmm_step_graph_launch) after the work
+        queued so far on the current stream, and wait for it.  Raises FMMError
+        on an overflow (grow the capacities and record_step() again)."""
+        dev = self.device
+        self._gstream.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.device(dev):
+            rc = lib().fmm_step_graph_launch(self._h, ctypes.c_void_p(self._gstream.cuda_stream))
+        if rc != FMM_OK:
+            raise FMMError(rc, "fmm_step_graph_launch")
+        self.generation += 1
 
     def adjoint(self, x, p, q, wE, wB):
         """(dL/dx, dL/dp, dL/dq) of L = sum wE.E + wB.B at the last field() call."""
@@ -253,6 +314,7 @@ class Plan:
             _lib.fmm_plan_destroy(self._h)
             self._h = None
         self._ws = None
+        self._graph_refs = None
 
     def __del__(self):  # pragma: no cover - best effort
         try:

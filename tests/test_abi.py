@@ -67,6 +67,16 @@ def test_host_side_argument_checks(libpath):
     lib.fmm_field.argtypes = [ctypes.c_void_p] * 7
     one = ctypes.c_void_p(256)
     assert lib.fmm_field(h, one, one, one, one, one, None) == 2  # no workspace attached
+    # the recorded step: nothing recorded yet, NULL arguments, no workspace
+    lib.fmm_step_graph_create.argtypes = [ctypes.c_void_p] * 12
+    lib.fmm_step_graph_launch.argtypes = [ctypes.c_void_p] * 2
+    lib.fmm_step_graph_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.fmm_step_graph_launch(h, one) == 5
+    assert lib.fmm_step_graph_launch(None, one) == 1
+    assert lib.fmm_step_graph_create(h, None, one, one, None, None, one, one, None, None, None, one) == 1
+    assert lib.fmm_step_graph_create(h, one, one, one, one, None, one, one, one, one, one, one) == 1  # wE without wB
+    assert lib.fmm_step_graph_create(h, one, one, one, None, None, one, one, None, None, None, one) == 2
+    assert lib.fmm_step_graph_destroy(h) == 0
     lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.fmm_plan_destroy(h)
     assert lib.fmm_strerror(3) == b"interaction-list capacity exceeded"
