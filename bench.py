@@ -418,6 +418,19 @@ def run_ours(args, rank, world, local):
                               "adjoint near field 84 per particle pair for both roles in one kernel (FP32), "
                               "else 46 (target side) and 67 (source side)",
                 "kernels": kernels}
+        # kernels that share the GPU in the step (two streams) have no
+        # duration of their own there: report each pair of branches over the
+        # span they share, from the first one's start to the last one's end
+        branches = {}
+        pairs = (("forward", ("m2l", "p2p_l2p"), stage_med.get("p2p_l2p", 0.0)),
+                 ("adjoint", ("adj_near", "adj_m2lt"),
+                  stage_med.get("adj_total", 0.0) - stage_med.get("adj_lists", 0.0) - stage_med.get("adj_source", 0.0)))
+        for name, ks, span in pairs:
+            if all(k in kernels and kernels[k]["shares_gpu_in_step"] for k in ks) and span > 0 and peak32:
+                fl = sum(kernels[k]["flop"] for k in ks)
+                branches[name] = {"kernels": list(ks), "ms_in_step": span, "tflops": fl / (span / 1e3) / 1e12,
+                                  "frac": fl / (span / 1e3) / 1e12 / peak32["tflops"]}
+        roof["branches_in_step"] = branches
         # the whole step: every hot kernel's algorithmic flop over the timed
         # step (branches that share the GPU counted once, by their flop)
         step_flop = sum(kd["flop"] for kd in kernels.values())
