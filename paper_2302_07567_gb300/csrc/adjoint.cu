@@ -1743,6 +1743,7 @@ int adj_m2l(fmm_plan_s* P, bool gbar_term, cudaStream_t s) {
       case 5: return launch_adj_m2l_pair<5, 64>(P, s);
       case 7: return launch_adj_m2l_pair<7, 64>(P, s);
       case 9: return launch_adj_m2l_pair<9, 128>(P, s);
+      case 11: return launch_adj_m2l_pair<11, 128>(P, s);
       default: break;
     }
   }
@@ -1792,6 +1793,7 @@ int launch_adj_far(fmm_plan_s* P, cudaStream_t s) {
     case 5: kern = k_adj_far<5>; break;
     case 7: kern = k_adj_far<7>; break;
     case 9: kern = k_adj_far<9>; break;
+    case 11: kern = k_adj_far<11>; break;
     default: break;
   }
   if (int rc = smem_limit(kern, (int)smem)) return rc;
@@ -1816,6 +1818,7 @@ int launch_adj_final(fmm_plan_s* P, const double* p, const double* q, double* dx
     case 5: kern = k_adj_final<5>; break;
     case 7: kern = k_adj_final<7>; break;
     case 9: kern = k_adj_final<9>; break;
+    case 11: kern = k_adj_final<11>; break;
     default: break;
   }
   if (int rc = smem_limit(kern, (int)smem)) return rc;

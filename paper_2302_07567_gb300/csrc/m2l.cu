@@ -499,7 +499,7 @@ int m2l_t(fmm_plan_s* P, cudaStream_t s) {
 
 bool m2l_specialised(const fmm_plan_s* P) {
   return P->precision == FMM_FP32 && P->eta <= 0.5 && !(P->flags & FMM_TEST_POLY_KERNEL) &&
-         (P->np1 == 3 || P->np1 == 5 || P->np1 == 7 || P->np1 == 9);
+         (P->np1 == 3 || P->np1 == 5 || P->np1 == 7 || P->np1 == 9 || P->np1 == 11);
 }
 
 int run_m2l(fmm_plan_s* P, cudaStream_t s) {
@@ -509,10 +509,12 @@ int run_m2l(fmm_plan_s* P, cudaStream_t s) {
       // paired kernels, block sizes from sweeps of fwd+adj steps: n = 4 (64
       // threads) 33.2 -> 32.1 ms on the 1.28e6 cube; n = 6 (64) 1.465 ->
       // 1.432 ms at 2^16, 14.9 -> 14.3 ms at 2^18 (192: 14.0, 96: 14.6);
-      // n = 8 (128) with the x sums split 3.91 -> 3.47 s at 2^24
+      // n = 8 (128) with the x sums split 3.91 -> 3.47 s at 2^24; n = 10
+      // (128): M2L 11.4 -> 4.9 ms on the 1.28e6 cube at eta = 0.3
       case 5: return launch_pair<5, 64>(P, s);
       case 7: return launch_pair<7, 64>(P, s);
       case 9: return launch_pair<9, 128>(P, s);
+      case 11: return launch_pair<11, 128>(P, s);
       default: break;
     }
   }

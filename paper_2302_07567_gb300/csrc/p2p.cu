@@ -493,6 +493,7 @@ int run_l2p_far(fmm_plan_s* P, void* E, void* B, cudaStream_t s) {
     case 5: kern = k_l2p_far<5>; break;
     case 7: kern = k_l2p_far<7>; break;
     case 9: kern = k_l2p_far<9>; break;
+    case 11: kern = k_l2p_far<11>; break;
     default: break;
   }
   if (int rc = smem_limit(kern, (int)smem)) return rc;

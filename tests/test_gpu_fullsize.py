@@ -177,10 +177,12 @@ def test_corehalo_shape_fp32_against_fp64_at_1m():
 @pytest.mark.parametrize("eta", [0.3, 0.5])
 def test_paper_sweep_regime_cube_n10(eta):
     """The regime of the paper's Fig. 2 sweep (Section 5): the uniform cube at
-    gamma = 50, degree n = 10 (a degree without specialised kernels) and
-    leaf size N0 = (n + 1)^3 = 1331, on a 16,384-particle draw.  FP64 within
-    1e-12 of the oracle's FMM, FP32 within 1e-5 of it and within the FMM's
-    truncation error + 1e-6 of the brute force."""
+    gamma = 50, degree n = 10 (11 points per axis: the paired FP32 M2L and
+    M2L^T kernels) and leaf size N0 = (n + 1)^3 = 1331, on a 16,384-particle
+    draw.  FP64 within 1e-12 of the oracle's FMM, FP32 within 1e-5 of it and
+    within the FMM's truncation error + 1e-6 of the brute force; at
+    eta = 0.5 the FP32 adjoint within 2e-5 of the oracle's frozen-plan
+    gradient."""
     N, n, leaf = 16384, 10, 1331
     x, p, q = make_beam("cube", N=N)
     ref_plan = bldtt.build_plan(x, p, n, leaf, eta)
@@ -202,3 +204,12 @@ def test_paper_sweep_regime_cube_n10(eta):
     trunc = metrics.field_error(Er[tg], Br[tg], Ed.numpy(), Bd.numpy())
     e32 = metrics.field_error(out["fp32"][0][tg], out["fp32"][1][tg], Ed.numpy(), Bd.numpy())
     assert e32 < trunc + 1e-6, (e32, trunc)
+    if eta == 0.5:
+        wE, wB = make_weights(N)
+        _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, ref_plan)
+        plan = fmm.Plan(N, n, leaf, eta, precision="fp32")
+        plan.field(X, Pm, Q)
+        WE, WB = (torch.as_tensor(a, device=X.device, dtype=torch.float32) for a in (wE, wB))
+        for a, b in zip(plan.adjoint(X, Pm, Q, WE, WB), (gx, gp, gq)):
+            b = b.numpy()
+            assert np.linalg.norm(a.cpu().numpy() - b) / np.linalg.norm(b) < 2e-5
