@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import bldtt, metrics, physics
+from oracle import bldtt, gradient, metrics, physics
 from paper_2302_07567_gb300 import fmm
 from paper_2302_07567_gb300.workloads import make_beam, make_weights, random_beam
 
@@ -230,11 +230,23 @@ def test_edge_cases():
     p = np.zeros((600, 3))
     p[:, 2] = 5.0
     q = np.full(600, -1.6e-19)
-    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
-        _, E, B = run(x, p, q, 3, 16, 0.5, prec)
-        Er, Br = bldtt.fmm_fields(x, p, q, 3, 16, 0.5)
-        assert np.all(np.isfinite(E)) and np.all(np.isfinite(B))
-        assert metrics.field_error(E, B, Er.numpy(), Br.numpy()) < tol
+    for n in (3, 4):  # 4: the separable P2M and the paired M2L kernels on zero-width boxes
+        Er, Br = bldtt.fmm_fields(x, p, q, n, 16, 0.5)
+        for prec, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
+            _, E, B = run(x, p, q, n, 16, 0.5, prec)
+            assert np.all(np.isfinite(E)) and np.all(np.isfinite(B))
+            assert metrics.field_error(E, B, Er.numpy(), Br.numpy()) < tol
+    # and the FP32 adjoint there (the far-field basis derivatives of a zero-width side)
+    wE, wB = make_weights(600)
+    ref_plan = bldtt.build_plan(x, p, 4, 16, 0.5)
+    _, gx, gp, gq = gradient.fmm_gradient(x, p, q, wE, wB, ref_plan)
+    plan = fmm.Plan(600, 4, 16, 0.5, precision="fp32")
+    X, P, Q = dev(x, p, q)
+    plan.field(X, P, Q)
+    WE, WB = (torch.as_tensor(a, device=DEV, dtype=torch.float32) for a in (wE, wB))
+    for a, b in zip(plan.adjoint(X, P, Q, WE, WB), (gx, gp, gq)):
+        a, b = a.cpu().numpy(), b.numpy()
+        assert np.all(np.isfinite(a)) and np.linalg.norm(a - b) / np.linalg.norm(b) < 2e-5
 
 
 def test_nonfinite_input_is_rejected():
