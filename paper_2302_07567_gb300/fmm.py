@@ -264,9 +264,12 @@ class Plan:
         queued so far on the current stream, and wait for it.  Raises FMMError
         on an overflow (grow the capacities and record_step() again)."""
         dev = self.device
-        self._gstream.wait_stream(torch.cuda.current_stream(dev))
+        gs = getattr(self, "_gstream", None)
+        if gs is None:  # nothing recorded: the library reports FMM_ESTATE
+            gs = torch.cuda.current_stream(dev)
+        gs.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.device(dev):
-            rc = lib().fmm_step_graph_launch(self._h, ctypes.c_void_p(self._gstream.cuda_stream))
+            rc = lib().fmm_step_graph_launch(self._h, ctypes.c_void_p(gs.cuda_stream))
         if rc != FMM_OK:
             raise FMMError(rc, "fmm_step_graph_launch")
         self.generation += 1

@@ -95,7 +95,6 @@ def test_forward_only_recording():
 
 def test_replay_without_a_recording_is_a_state_error():
     plan = fmm.Plan(4096, 4, 64, 0.5, precision="fp32")
-    plan._gstream = torch.cuda.Stream(DEV)
     with pytest.raises(fmm.FMMError) as e:
         plan.replay()
     assert e.value.status == fmm.FMM_ESTATE
