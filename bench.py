@@ -317,8 +317,9 @@ def run_ours(args, rank, world, local):
     # memory, all inside the timed region, and the host waits for the results
     # at the end of every step (as a host-side integrator must).  The loss
     # weights go up on a copy stream while the forward runs and E, B come down
-    # on it while the adjoint runs; x, p, q go up before the forward and the
-    # gradients come down after the adjoint, on the compute stream.  The plan
+    # on it while the adjoint runs (copy engine); x, p, q go up before the
+    # forward and the gradients come down after the adjoint, on the compute
+    # stream, by the SMs (fmm.copy_).  The plan
     # is warm from the device-resident timing: one more warm-up step, then up
     # to five timed steps.
     hx, hp, hq = (torch.as_tensor(a).pin_memory() for a in (x, p, q))
@@ -328,13 +329,25 @@ def run_ours(args, rank, world, local):
     o_field = [torch.empty((N, 3), dtype=out_dt, pin_memory=True) for _ in range(2)]
     o_grad = [torch.empty(sh, dtype=torch.float64, pin_memory=True) for sh in ((N, 3), (N, 3), (N,))] if adj else []
     outs = o_grad + o_field
+    Xd, Pd, Qd = (torch.empty(h.shape, dtype=h.dtype, device=dev) for h in (hx, hp, hq))
+
+    def up_or_down(dst, src):
+        # the copies the compute waits for go through the SMs (fmm.copy_),
+        # which the first transfer of a buffer after a step takes faster
+        # than the copy engine; rows of an odd N are not 16-byte multiples
+        if (dst.numel() * dst.element_size()) % 16 == 0:
+            fmm.copy_(dst, src)
+        else:
+            dst.copy_(src, non_blocking=True)
+
     e2e_steps = min(args.steps, 5)
     e2e_ms = []
     for k in range(1 + e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Xd, Pd, Qd = hx.to(dev, non_blocking=True), hp.to(dev, non_blocking=True), hq.to(dev, non_blocking=True)
+        for d_, h_ in zip((Xd, Pd, Qd), (hx, hp, hq)):
+            up_or_down(d_, h_)
         if adj:
             with torch.cuda.stream(cstream):
                 WEd, WBd = hwE.to(dev, non_blocking=True), hwB.to(dev, non_blocking=True)
@@ -348,17 +361,17 @@ def run_ours(args, rank, world, local):
         if adj:
             stream.wait_event(w_ready)
             for o, r in zip(o_grad, plan.adjoint(Xd, Pd, Qd, WEd, WBd)):
-                o.copy_(r, non_blocking=True)
+                up_or_down(o, r)
         torch.cuda.synchronize()
         if k >= 1:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        del Xd, Pd, Qd, E, B
+        del E, B
         if adj:
             del WEd, WBd
     d2h = sum(o.numel() * o.element_size() for o in outs)
     e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world, dev)
     e2e_value = N * world * e2e_steps / e2e_t
-    del outs, o_field, o_grad, hx, hp, hq, hwE, hwB
+    del outs, o_field, o_grad, hx, hp, hq, hwE, hwB, Xd, Pd, Qd
 
     def rel(a, b):
         return float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))

@@ -68,6 +68,7 @@ def lib():
         "fmm_step_graph_create": (I32, [P] * 12),
         "fmm_step_graph_launch": (I32, [P, P]),
         "fmm_step_graph_destroy": (I32, [P]),
+        "fmm_copy": (I32, [P, P, SZ, P]),
         "fmm_plan_set_capacity": (I32, [P, I64, I64, I64]),
         "fmm_plan_workspace_bytes": (I32, [P, ctypes.POINTER(SZ)]),
         "fmm_plan_set_workspace": (I32, [P, P, SZ]),
@@ -324,6 +325,29 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def copy_(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """dst <- src by a kernel on the GPU's SMs (fmm_copy): a CUDA tensor and a
+    pinned CPU tensor, either way, or two CUDA tensors of one device; the
+    same dtype and number of elements, contiguous, 16-byte aligned, a
+    multiple of 16 bytes.  Asynchronous on the CUDA tensor's current stream."""
+    if dst.dtype != src.dtype or dst.numel() != src.numel():
+        raise ValueError("copy_: dst and src differ in dtype or size")
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("copy_: tensors must be contiguous")
+    cuda = [t for t in (dst, src) if t.is_cuda]
+    if not cuda:
+        raise ValueError("copy_: one tensor must be a CUDA tensor")
+    for t in (dst, src):
+        if not t.is_cuda and not t.is_pinned():
+            raise ValueError("copy_: a CPU tensor must be pinned")
+    dev = cuda[0].device
+    with torch.cuda.device(dev):
+        rc = lib().fmm_copy(_ptr(dst), _ptr(src), dst.numel() * dst.element_size(), _stream(dev))
+    if rc != FMM_OK:
+        raise FMMError(rc, "fmm_copy")
+    return dst
 
 
 def kernel_launches() -> int:

@@ -77,6 +77,11 @@ def test_host_side_argument_checks(libpath):
     assert lib.fmm_step_graph_create(h, one, one, one, one, None, one, one, one, one, one, one) == 1  # wE without wB
     assert lib.fmm_step_graph_create(h, one, one, one, None, None, one, one, None, None, None, one) == 2
     assert lib.fmm_step_graph_destroy(h) == 0
+    lib.fmm_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert lib.fmm_copy(None, one, 16, None) == 1
+    assert lib.fmm_copy(one, ctypes.c_void_p(264), 16, None) == 1  # misaligned source
+    assert lib.fmm_copy(one, one, 24, None) == 1  # not a multiple of 16 bytes
+    assert lib.fmm_copy(one, one, 0, None) == 0  # nothing to copy
     lib.fmm_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.fmm_plan_destroy(h)
     assert lib.fmm_strerror(3) == b"interaction-list capacity exceeded"
