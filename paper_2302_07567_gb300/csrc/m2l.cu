@@ -260,8 +260,8 @@ __global__ void __launch_bounds__(NP1 * NP1 * G, 3) k_m2l_fast(const uint64_t* _
   }  // work items
 }
 
-// FP32 M2L with paired arithmetic and regrouped x sums (eta <= 1/2, points
-// per axis NP1 fixed).
+// FP32 M2L with paired arithmetic and the R_x products held per point
+// (eta <= 1/2, points per axis NP1 fixed).
 //
 // Two changes against k_m2l_fast, which issues about 18 instructions per
 // point pair, 14 of them on the FMA pipe:
